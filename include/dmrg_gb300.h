@@ -1,0 +1,189 @@
+/*
+ * dmrg_gb300.h -- C ABI of the GB300 (sm_103a) two-site QC-DMRG hot path.
+ *
+ * Method: J. Brabec et al., "Massively parallel quantum chemical density
+ * matrix renormalization group method" (arXiv:2001.04890).  Section and
+ * equation names below are the paper's.
+ *
+ * The library owns every block operator, task list and Davidson workspace on
+ * the GPU.  Callers pass plain host or device pointers and sizes; nothing in
+ * this interface is a framework type.  All functions return DMRG_OK (0) or a
+ * negative status and then set a thread-local message (dmrg_last_error).  No
+ * function aborts the process or traps the GPU; device-side waits are bounded
+ * and report DMRG_ETIMEOUT.
+ *
+ * Conventions shared by every entry point
+ *   Orbitals (sites) 0..L-1 in lattice order.  Site basis {0, up, dn, updn}
+ *   with |updn> = a+_up a+_dn |0> (Eq. creation_ops read in its stated order).
+ *   Jordan-Wigner order: sites in lattice order, up before dn on a site.
+ *   Hamiltonian (Eq. H2q) in spin-orbital form
+ *       H = sum_pq h_pq a+_ps a_qs + 1/2 sum_pqrs (pq|rs) a+_ps a+_rt a_st a_qs,
+ *   h row-major L*L symmetric, v row-major L^4 chemists' (pq|rs), no core energy.
+ *   Position k (0 <= k <= L-2): left block l = sites 0..k-1, left site k,
+ *   right site k+1, right block r = sites k+2..L-1 (Sec. 2.1, Fig. dmrg_blocks).
+ *   Block sectors: (n_up, n_dn) sorted ascending (Sec. 2.1, U(1) symmetry).
+ *   psi (Eqs. wf, wf_sec): blocks (a, b, c, d) = (left-block sector, left-site
+ *   state, right-site state, right-block sector) with particle numbers adding
+ *   to (N_up, N_dn), ordered lexicographically; each block m_a x m_d row-major.
+ *   Enlarged left block l (x) s (Eq. renorm): sectors sorted; inside a sector
+ *   the (a, b) sub-blocks in lexicographic order, each m_a rows.  Enlarged
+ *   right block s (x) r: (c, d) sub-blocks in lexicographic order, m_d rows.
+ *   A renormalization matrix O is given per enlarged sector E as a row-major
+ *   dim_E x kept_E matrix with orthonormal columns; all sectors concatenated.
+ */
+#ifndef DMRG_GB300_H
+#define DMRG_GB300_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  DMRG_OK = 0,
+  DMRG_EINVAL = -1,   /* bad argument or state-independent precondition   */
+  DMRG_ENOMEM = -2,   /* device or host allocation failed                  */
+  DMRG_ECUDA = -3,    /* a CUDA or library call failed (message has it)     */
+  DMRG_ENOCONV = -4,  /* Davidson hit max_iter before the tolerance          */
+  DMRG_ESTATE = -5,   /* call not valid in the current context state        */
+  DMRG_ETIMEOUT = -6  /* a bounded device-side wait ran out                  */
+};
+
+enum { DMRG_PREC_FP64 = 0, DMRG_PREC_FP32 = 1, DMRG_PREC_BF16X3 = 2 };
+
+typedef struct dmrg_ctx dmrg_ctx; /* opaque, library-owned */
+
+/* Thread-local text of the last error (never NULL; empty if none). */
+const char *dmrg_last_error(void);
+
+/*
+ * dmrg_init -- problem setup (Sec. 2.1, Eq. H2q; Sec. 2.2 task lists).
+ * Copies h (L*L) and v (L^4) from HOST memory.  N electrons, two_sz = N_up - N_dn.
+ * M: bond dimension (kept states per block, Eq. renorm).  precision: DMRG_PREC_*.
+ * cuda_stream: a cudaStream_t (may be NULL for the legacy default stream);
+ * every device operation of this context is ordered on it.
+ * Builds the site operators, the deterministic Aufbau product state (orbitals
+ * 0..N_up-1 carry an up electron, 0..N_dn-1 a dn electron) and all right
+ * blocks of that state, and leaves the context at position 0.
+ * Errors: DMRG_EINVAL for L < 2, N outside [0, 2L], |two_sz| > N, parity of N
+ * and two_sz different, N_up or N_dn > L, M < 1, non-finite h or v, h not
+ * symmetric within 1e-12; DMRG_ENOMEM / DMRG_ECUDA from the device.
+ * *out receives the context (owned by the caller until dmrg_free).
+ */
+int dmrg_init(int L, int N, int two_sz, const double *h, const double *v, int M, int precision,
+              void *cuda_stream, dmrg_ctx **out);
+
+/* Release every device and host resource of the context (NULL is allowed). */
+int dmrg_free(dmrg_ctx *ctx);
+
+/*
+ * dmrg_set_position -- move to two-site position k (0 <= k <= L-2) without
+ * changing any block; direction +1 (forward) or -1 (backward) only records
+ * the sweep direction.  Blocks needed by later calls must already exist.
+ */
+int dmrg_set_position(dmrg_ctx *ctx, int k, int direction);
+
+/* Current position (k) and the left/right block sizes (host ints; any may be NULL). */
+int dmrg_get_position(dmrg_ctx *ctx, int *k, int *direction);
+
+/*
+ * dmrg_psi_layout -- the psi block list of Eq. wf_sec at the current position.
+ * If blocks is non-NULL it must hold 7 * (*nblocks from a previous call) ints:
+ * per block (a, b, c, d, rows m_a, cols m_d, element offset).  *dim = length of psi.
+ * Any output pointer may be NULL.  DMRG_ESTATE if a block is missing.
+ */
+int dmrg_psi_layout(dmrg_ctx *ctx, int *nblocks, int *blocks, long long *dim);
+
+/*
+ * dmrg_block_sectors -- sectors of the left (side 0) or right (side 1) block
+ * at the current position: per sector (n_up, n_dn, dim), 3 ints each.
+ */
+int dmrg_block_sectors(dmrg_ctx *ctx, int side, int *nsec, int *sectors);
+
+/*
+ * dmrg_enlarged_layout -- enlarged sectors of l (x) s_l (direction +1) or
+ * s_r (x) r (direction -1) at the current position: per sector (n_up, n_dn, dim).
+ */
+int dmrg_enlarged_layout(dmrg_ctx *ctx, int direction, int *nsec, int *sectors);
+
+/*
+ * dmrg_hpsi -- sigma = H psi at the current position (Sec. 2.2.1, Eq. dgemm):
+ *   sigma^{s'} = sum_{alpha, s} f(s) A_l^{(alpha,s,s')} psi^s (A_r^{(alpha,s,s')})^T
+ * psi and sigma have the dmrg_psi_layout layout and length dim.  If device_ptrs
+ * is non-zero both are device pointers valid on the context's stream (sigma
+ * is written, not accumulated; psi is not modified; they must not overlap);
+ * otherwise both are host pointers and the call copies in and out.
+ * In DMRG_PREC_FP64 the result is bitwise repeatable run to run.
+ */
+int dmrg_hpsi(dmrg_ctx *ctx, const double *psi, double *sigma, int device_ptrs);
+
+/* Algorithmic FLOPs of one dmrg_hpsi at the current position (host-counted from the task list). */
+int dmrg_hpsi_flops(dmrg_ctx *ctx, double *flops, long long *tasks);
+
+/*
+ * dmrg_set_psi / dmrg_get_psi -- the context's current wave function (host
+ * pointers, dmrg_psi_layout length).  dmrg_set_psi also makes it the
+ * Davidson starting vector.
+ */
+int dmrg_set_psi(dmrg_ctx *ctx, const double *psi);
+int dmrg_get_psi(dmrg_ctx *ctx, double *psi);
+
+/*
+ * dmrg_davidson -- lowest eigenpair of Eq. h_mat at the current position by
+ * Davidson's method (Sec. 2.2.1) in FP64 on the GPU: diagonal preconditioner
+ * (E - diag H)^-1 with |denominator| >= 1e-8, subspace <= 24, thick restart
+ * with 2 vectors, converged when ||H psi - E psi|| <= tol for normalized psi.
+ * Starts from the current psi when one is set, else from a fixed pseudo-random
+ * vector.  *energy, *iters (host; may be NULL).  DMRG_ENOCONV if max_iter is
+ * reached (energy and psi still hold the last Ritz pair).
+ */
+int dmrg_davidson(dmrg_ctx *ctx, double tol, int max_iter, double *energy, int *iters);
+
+/*
+ * dmrg_renormalize -- truncate the enlarged block and renormalize its
+ * operators (Eqs. renorm, renorm_mat; Sec. 2.2.2), then move one position.
+ * direction +1: new left block l' = l (x) s_l, position k -> k+1.
+ * direction -1: new right block r' = s_r (x) r, position k -> k-1.
+ * If O is NULL the basis is the kept eigenvectors of rho^L = psi psi^T
+ * (rho^R = psi^T psi) of the current psi: the M largest eigenvalues over all
+ * sectors, ties broken by (sector order, in-sector order), eigenvalues
+ * <= 1e-13 never kept; kept (may be NULL) receives the per-sector counts.
+ * Otherwise kept (host, one int per enlarged sector) and O (host, layout in
+ * the header comment) define the new basis; the caller guarantees
+ * orthonormal columns.  *discarded_weight (may be NULL) = trace(rho) - kept
+ * eigenvalues (0 when O is given).  After the move the current psi is
+ * transformed into the new position's basis (wave-function prediction) when
+ * O was NULL; otherwise it is cleared.
+ */
+int dmrg_renormalize(dmrg_ctx *ctx, int direction, const int *kept, const double *O,
+                     double *discarded_weight);
+
+/*
+ * dmrg_sweep -- nsweeps two-site sweeps (Sec. 2.1, Fig. dmrg_blocks): forward
+ * over positions 0..L-3 (Davidson then dmrg_renormalize(+1)), backward over
+ * L-2..1 (Davidson then dmrg_renormalize(-1)).  Starts from position 0 in the
+ * forward direction.  energies (host, may be NULL) receives one energy per
+ * Davidson step: nsweeps * 2 * (L - 2) values.
+ */
+int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
+
+/*
+ * dmrg_block_op -- introspection of one stored operator of the left (side 0)
+ * or right (side 1) block at the current position, in its family layout:
+ * for each ket sector a with a bra sector a' in order, the m_a' x m_a block.
+ * kind: 0 H, 1 a+_i, 2 T_i (left blocks), 3 V_i (right blocks), 4 a+_i a+_j,
+ * 5 a+_i a_j (spin-orbital indices 2*site + spin).  out (host) may be NULL to
+ * query *n (element count).  DMRG_EINVAL if the block stores no such operator.
+ */
+int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, long long *n);
+
+/* Planner introspection (host only, no GPU): text dumps of the H pieces at
+ * position k and of the blocking definitions of a new block's operators. */
+int dmrg_debug_pieces(int L, const double *h, const double *v, int k, int l_empty, int r_empty,
+                      int compress, char *buf, long long buflen, long long *needed);
+int dmrg_debug_newops(int L, const double *h, const double *v, int k, int side, int old_empty,
+                      char *buf, long long buflen, long long *needed);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DMRG_GB300_H */

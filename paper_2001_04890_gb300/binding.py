@@ -1,0 +1,221 @@
+"""Thin ctypes binding of the C ABI in include/dmrg_gb300.h (argument marshalling only).
+
+Every step of the hot path runs inside libdmrg_gb300.so (CUDA kernels for
+sm_103a plus its host planner); this module only converts Python / numpy /
+torch arguments to pointers and sizes.  There is no fallback: if the shared
+library is missing the import of the handle fails with an error that says how
+to build it.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libdmrg_gb300.so")
+
+DMRG_OK, DMRG_EINVAL, DMRG_ENOMEM, DMRG_ECUDA, DMRG_ENOCONV, DMRG_ESTATE, DMRG_ETIMEOUT = 0, -1, -2, -3, -4, -5, -6
+PREC_FP64, PREC_FP32, PREC_BF16X3 = 0, 1, 2
+
+_lib = None
+
+
+class DMRGError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"dmrg error {code}: {msg}")
+        self.code = code
+
+
+def lib():
+    """Load libdmrg_gb300.so (built by __graft_entry__.build()); raise if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise ImportError(f"{LIB_PATH} not found: run `python -c 'import __graft_entry__ as g; g.build()'`")
+    L = C.CDLL(LIB_PATH)
+    dp, ip, vp = C.POINTER(C.c_double), C.POINTER(C.c_int), C.c_void_p
+    llp = C.POINTER(C.c_longlong)
+    sig = {
+        "dmrg_last_error": (C.c_char_p, []),
+        "dmrg_init": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, vp, C.POINTER(vp)]),
+        "dmrg_free": (C.c_int, [vp]),
+        "dmrg_set_position": (C.c_int, [vp, C.c_int, C.c_int]),
+        "dmrg_get_position": (C.c_int, [vp, ip, ip]),
+        "dmrg_psi_layout": (C.c_int, [vp, ip, ip, llp]),
+        "dmrg_block_sectors": (C.c_int, [vp, C.c_int, ip, ip]),
+        "dmrg_enlarged_layout": (C.c_int, [vp, C.c_int, ip, ip]),
+        "dmrg_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
+        "dmrg_hpsi_flops": (C.c_int, [vp, dp, llp]),
+        "dmrg_set_psi": (C.c_int, [vp, dp]),
+        "dmrg_get_psi": (C.c_int, [vp, dp]),
+        "dmrg_davidson": (C.c_int, [vp, C.c_double, C.c_int, dp, ip]),
+        "dmrg_renormalize": (C.c_int, [vp, C.c_int, ip, dp, dp]),
+        "dmrg_sweep": (C.c_int, [vp, C.c_int, C.c_double, dp]),
+        "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
+        "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
+                                        C.c_char_p, C.c_longlong, llp]),
+        "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
+                                        C.c_char_p, C.c_longlong, llp]),
+    }
+    for name, (res, args) in sig.items():
+        if not hasattr(L, name):
+            continue  # reported by the export test; calling it raises AttributeError
+        fn = getattr(L, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = L
+    return L
+
+
+def _check(code):
+    if code != DMRG_OK:
+        raise DMRGError(code, lib().dmrg_last_error().decode())
+    return code
+
+
+def _dptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_double))
+
+
+def _iptr(a: np.ndarray):
+    return a.ctypes.data_as(C.POINTER(C.c_int))
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def _dump(fn, *args):
+    need = C.c_longlong(0)
+    _check(fn(*args, None, 0, C.byref(need)))
+    buf = C.create_string_buffer(need.value)
+    _check(fn(*args, buf, need.value, C.byref(need)))
+    return buf.value.decode()
+
+
+def debug_pieces(h, v, k, l_empty, r_empty, compress=True):
+    h, v = _f64(h), _f64(v)
+    return _dump(lib().dmrg_debug_pieces, h.shape[0], _dptr(h), _dptr(v), k, int(l_empty),
+                 int(r_empty), int(compress))
+
+
+def debug_newops(h, v, k, side, old_empty):
+    h, v = _f64(h), _f64(v)
+    return _dump(lib().dmrg_debug_newops, h.shape[0], _dptr(h), _dptr(v), k, side, int(old_empty))
+
+
+class DMRG:
+    """One two-site DMRG problem on the GPU (wraps a dmrg_ctx)."""
+
+    def __init__(self, h, v, N, two_sz, M, precision=PREC_FP64, stream=None):
+        self._h, self._v = _f64(h), _f64(v)
+        self.L = self._h.shape[0]
+        self.N, self.two_sz, self.M = N, two_sz, M
+        ctx = C.c_void_p()
+        s = C.c_void_p(stream) if stream else None
+        _check(lib().dmrg_init(self.L, N, two_sz, _dptr(self._h), _dptr(self._v), M, precision,
+                               s, C.byref(ctx)))
+        self.ctx = ctx
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().dmrg_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_position(self, k, direction=1):
+        _check(lib().dmrg_set_position(self.ctx, k, direction))
+
+    def position(self):
+        k, d = C.c_int(), C.c_int()
+        _check(lib().dmrg_get_position(self.ctx, C.byref(k), C.byref(d)))
+        return k.value, d.value
+
+    def psi_layout(self):
+        n, dim = C.c_int(), C.c_longlong()
+        _check(lib().dmrg_psi_layout(self.ctx, C.byref(n), None, C.byref(dim)))
+        blocks = np.zeros(7 * n.value, dtype=np.int32)
+        _check(lib().dmrg_psi_layout(self.ctx, C.byref(n), _iptr(blocks), C.byref(dim)))
+        return blocks.reshape(n.value, 7), dim.value
+
+    def block_sectors(self, side):
+        n = C.c_int()
+        _check(lib().dmrg_block_sectors(self.ctx, side, C.byref(n), None))
+        out = np.zeros(3 * n.value, dtype=np.int32)
+        _check(lib().dmrg_block_sectors(self.ctx, side, C.byref(n), _iptr(out)))
+        return out.reshape(n.value, 3)
+
+    def enlarged_layout(self, direction):
+        n = C.c_int()
+        _check(lib().dmrg_enlarged_layout(self.ctx, direction, C.byref(n), None))
+        out = np.zeros(3 * n.value, dtype=np.int32)
+        _check(lib().dmrg_enlarged_layout(self.ctx, direction, C.byref(n), _iptr(out)))
+        return out.reshape(n.value, 3)
+
+    def hpsi(self, psi):
+        """sigma = H psi.  psi: numpy float64 (host path) or a CUDA torch tensor (device path)."""
+        if isinstance(psi, np.ndarray):
+            psi = _f64(psi)
+            sigma = np.empty_like(psi)
+            _check(lib().dmrg_hpsi(self.ctx, psi.ctypes.data, sigma.ctypes.data, 0))
+            return sigma
+        import torch  # device path: torch provides the memory only
+        assert psi.is_cuda and psi.dtype == torch.float64 and psi.is_contiguous()
+        sigma = torch.empty_like(psi)
+        _check(lib().dmrg_hpsi(self.ctx, psi.data_ptr(), sigma.data_ptr(), 1))
+        return sigma
+
+    def hpsi_flops(self):
+        f, t = C.c_double(), C.c_longlong()
+        _check(lib().dmrg_hpsi_flops(self.ctx, C.byref(f), C.byref(t)))
+        return f.value, t.value
+
+    def set_psi(self, psi):
+        psi = _f64(psi)
+        _check(lib().dmrg_set_psi(self.ctx, _dptr(psi)))
+
+    def get_psi(self):
+        _, dim = self.psi_layout()
+        out = np.zeros(dim)
+        _check(lib().dmrg_get_psi(self.ctx, _dptr(out)))
+        return out
+
+    def davidson(self, tol=1e-9, max_iter=200, allow_noconv=False):
+        e, it = C.c_double(), C.c_int()
+        code = lib().dmrg_davidson(self.ctx, tol, max_iter, C.byref(e), C.byref(it))
+        if code == DMRG_ENOCONV and allow_noconv:
+            return e.value, it.value
+        _check(code)
+        return e.value, it.value
+
+    def renormalize(self, direction, O=None, kept=None):
+        dw = C.c_double()
+        if O is None:
+            n = len(self.enlarged_layout(direction))
+            kept_out = np.zeros(n, dtype=np.int32)
+            _check(lib().dmrg_renormalize(self.ctx, direction, _iptr(kept_out), None, C.byref(dw)))
+            return dw.value, kept_out
+        O = _f64(O)
+        kept = np.ascontiguousarray(kept, dtype=np.int32)
+        _check(lib().dmrg_renormalize(self.ctx, direction, _iptr(kept), _dptr(O), C.byref(dw)))
+        return dw.value, kept
+
+    def sweep(self, nsweeps, tol=1e-9):
+        e = np.zeros(nsweeps * 2 * (self.L - 2))
+        _check(lib().dmrg_sweep(self.ctx, nsweeps, tol, _dptr(e)))
+        return e
+
+    def block_op(self, side, kind, i=-1, j=-1):
+        n = C.c_longlong()
+        _check(lib().dmrg_block_op(self.ctx, side, kind, i, j, None, C.byref(n)))
+        out = np.zeros(n.value)
+        _check(lib().dmrg_block_op(self.ctx, side, kind, i, j, _dptr(out), C.byref(n)))
+        return out

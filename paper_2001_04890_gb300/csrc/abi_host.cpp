@@ -1,0 +1,78 @@
+// Host-only entry points of the C ABI: error reporting and planner
+// introspection (no CUDA calls; usable on a machine without a GPU).
+#include <cstring>
+#include <string>
+
+#include "../../include/dmrg_gb300.h"
+#include "plan.hpp"
+
+namespace dmrg {
+thread_local std::string g_last_error;
+void set_error(const std::string &s) { g_last_error = s; }
+}  // namespace dmrg
+
+extern "C" const char *dmrg_last_error(void) { return dmrg::g_last_error.c_str(); }
+
+static dmrg::Integrals make_integrals(int L, const double *h, const double *v) {
+  dmrg::Integrals I;
+  I.L = L;
+  I.h.assign(h, h + (size_t)L * L);
+  I.v.assign(v, v + (size_t)L * L * L * L);
+  return I;
+}
+
+static int copy_out(const std::string &s, char *buf, long long buflen, long long *needed) {
+  if (needed) *needed = (long long)s.size() + 1;
+  if (!buf || buflen < (long long)s.size() + 1) {
+    dmrg::set_error("dump buffer too small");
+    return buf ? DMRG_EINVAL : DMRG_OK;
+  }
+  std::memcpy(buf, s.c_str(), s.size() + 1);
+  return DMRG_OK;
+}
+
+extern "C" int dmrg_debug_pieces(int L, const double *h, const double *v, int k, int l_empty,
+                                 int r_empty, int compress, char *buf, long long buflen,
+                                 long long *needed) {
+  try {
+    if (L < 2 || k < 0 || k > L - 2 || !h || !v) {
+      dmrg::set_error("dmrg_debug_pieces: bad arguments");
+      return DMRG_EINVAL;
+    }
+    auto I = make_integrals(L, h, v);
+    auto ps = dmrg::hamiltonian_pieces(I, k, l_empty != 0, r_empty != 0);
+    if (compress) ps = dmrg::compress_pieces(ps);
+    return copy_out(dmrg::dump_pieces(ps), buf, buflen, needed);
+  } catch (const std::exception &e) {
+    dmrg::set_error(e.what());
+    return DMRG_EINVAL;
+  }
+}
+
+extern "C" int dmrg_debug_newops(int L, const double *h, const double *v, int k, int side,
+                                 int old_empty, char *buf, long long buflen, long long *needed) {
+  try {
+    if (L < 2 || k < 0 || k > L - 2 || (side != 0 && side != 1) || !h || !v) {
+      dmrg::set_error("dmrg_debug_newops: bad arguments");
+      return DMRG_EINVAL;
+    }
+    auto I = make_integrals(L, h, v);
+    dmrg::BlockLayout nb;
+    std::vector<int> sites;
+    if (side == 0) for (int s = 0; s <= k; ++s) sites.push_back(s);
+    else for (int s = k + 1; s < L; ++s) sites.push_back(s);
+    dmrg::build_layout(nb, side, L, sites, {{0, 0, 1}});
+    auto ops = dmrg::new_block_ops(I, k, side, nb, old_empty != 0);
+    std::string out;
+    for (auto &o : ops) {
+      const auto &F = nb.fam[o.fam];
+      out += "OP " + std::to_string(F.kind) + " " + std::to_string(F.idx[o.k][0]) + " " +
+             std::to_string(F.idx[o.k][1]) + "\n";
+      out += dmrg::dump_halfop(o.def);
+    }
+    return copy_out(out, buf, buflen, needed);
+  } catch (const std::exception &e) {
+    dmrg::set_error(e.what());
+    return DMRG_EINVAL;
+  }
+}
