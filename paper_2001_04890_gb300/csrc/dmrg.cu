@@ -1,0 +1,1429 @@
+// C ABI implementation: context, block storage, task lists and the FP64 path.
+//
+// Paper: Brabec et al., arXiv:2001.04890.  Sec. 2.1 (sweep, Eqs. renorm,
+// h_mat, wf, wf_sec, renorm_mat, density matrices), Sec. 2.2.1 (H.psi task
+// list, Eq. dgemm), Sec. 2.2.2 (renormalization task list and blocking
+// tables), Sec. 2.2.3 (pre-summed operators, Eq. presum).
+#include <cuda_runtime.h>
+#include <cusolverDn.h>
+
+#include <algorithm>
+#include <cmath>
+#include <functional>
+#include <map>
+#include <cstring>
+#include <memory>
+#include <numeric>
+#include <stdexcept>
+#include <string>
+#include <vector>
+
+#include "../../include/dmrg_gb300.h"
+#include "kernels.cuh"
+#include "plan.hpp"
+
+namespace dmrg {
+void set_error(const std::string &s);
+
+struct Fail {
+  int code;
+  std::string msg;
+};
+
+#define CK(x)                                                                              \
+  do {                                                                                     \
+    cudaError_t _e = (x);                                                                  \
+    if (_e != cudaSuccess)                                                                 \
+      throw Fail{_e == cudaErrorMemoryAllocation ? DMRG_ENOMEM : DMRG_ECUDA,               \
+                 std::string(#x) + ": " + cudaGetErrorString(_e)};                         \
+  } while (0)
+
+#define CKS(x)                                                                             \
+  do {                                                                                     \
+    cusolverStatus_t _s = (x);                                                             \
+    if (_s != CUSOLVER_STATUS_SUCCESS)                                                     \
+      throw Fail{DMRG_ECUDA, std::string(#x) + ": cusolver status " + std::to_string(_s)}; \
+  } while (0)
+
+// ---------------------------------------------------------------- device buffers
+
+template <class T>
+struct DBuf {
+  T *p = nullptr;
+  size_t n = 0;
+  DBuf() = default;
+  DBuf(const DBuf &) = delete;
+  DBuf &operator=(const DBuf &) = delete;
+  ~DBuf() { release(); }
+  void release() {
+    if (p) cudaFree(p);
+    p = nullptr;
+    n = 0;
+  }
+  void alloc(size_t count) {
+    if (count <= n && p) return;
+    release();
+    if (count == 0) return;
+    CK(cudaMalloc(&p, count * sizeof(T)));
+    n = count;
+  }
+  void upload(const std::vector<T> &h, cudaStream_t s) {
+    alloc(h.size());
+    if (!h.empty()) CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
+  }
+};
+
+static uint64_t eaddr(const double *p) { return (uint64_t)(uintptr_t)p / 8; }
+
+// ---------------------------------------------------------------- enlarged layouts
+
+struct ESub {
+  int x, y, roff, m;  // left: (a, b); right: (c, d)
+};
+struct ESector {
+  int nu, nd, dim;
+  std::vector<ESub> sub;
+};
+using Enlarged = std::vector<ESector>;
+
+static Enlarged enlarged(const BlockLayout &b, int direction) {
+  std::map<std::pair<int, int>, std::vector<std::pair<int, int>>> groups;
+  for (int a = 0; a < (int)b.sec.size(); ++a)
+    for (int s = 0; s < 4; ++s) {
+      const std::pair<int, int> E{b.sec[a].nu + SITE_NU[s], b.sec[a].nd + SITE_ND[s]};
+      if (direction > 0) groups[E].push_back({a, s});
+      else groups[E].push_back({s, a});
+    }
+  Enlarged out;
+  for (auto &g : groups) {
+    ESector es;
+    es.nu = g.first.first;
+    es.nd = g.first.second;
+    std::sort(g.second.begin(), g.second.end());
+    int off = 0;
+    for (auto &xy : g.second) {
+      const int m = direction > 0 ? b.sec[xy.first].dim : b.sec[xy.second].dim;
+      es.sub.push_back({xy.first, xy.second, off, m});
+      off += m;
+    }
+    es.dim = off;
+    out.push_back(es);
+  }
+  return out;
+}
+
+// ---------------------------------------------------------------- blocks
+
+struct DevBlock {
+  BlockLayout lay;
+  DBuf<double> ops;  // all stored families
+  // the renormalization that produced this block (for the wave-function prediction)
+  Enlarged parent;
+  std::vector<int> kept;
+  std::vector<int64_t> Ooff;
+  DBuf<double> O;
+  const double *arena() const { return ops.p; }
+};
+
+struct PsiBlock {
+  int a, b, c, d, ma, md;
+  int64_t off;
+};
+
+struct Psi {
+  std::vector<PsiBlock> blk;
+  std::vector<int> index;  // ((a*4+b)*4+c)*nr+d -> block or -1
+  int nl = 0, nr = 0;
+  int64_t dim = 0;
+  int find(int a, int b, int c, int d) const {
+    if (a < 0 || d < 0 || a >= nl || d >= nr) return -1;
+    return index[((a * 4 + b) * 4 + c) * nr + d];
+  }
+};
+
+static Psi psi_layout(const BlockLayout &l, const BlockLayout &r, int nu, int nd) {
+  Psi P;
+  P.nl = (int)l.sec.size();
+  P.nr = (int)r.sec.size();
+  P.index.assign((size_t)P.nl * 16 * P.nr, -1);
+  int64_t off = 0;
+  for (int a = 0; a < P.nl; ++a)
+    for (int b = 0; b < 4; ++b)
+      for (int c = 0; c < 4; ++c)
+        for (int d = 0; d < P.nr; ++d) {
+          const int u = l.sec[a].nu + SITE_NU[b] + SITE_NU[c] + r.sec[d].nu;
+          const int v = l.sec[a].nd + SITE_ND[b] + SITE_ND[c] + r.sec[d].nd;
+          if (u != nu || v != nd) continue;
+          P.index[((a * 4 + b) * 4 + c) * P.nr + d] = (int)P.blk.size();
+          P.blk.push_back({a, b, c, d, l.sec[a].dim, r.sec[d].dim, off});
+          off += (int64_t)l.sec[a].dim * r.sec[d].dim;
+        }
+  P.dim = off;
+  return P;
+}
+
+// resolved operator -> effective block for ket sector a
+struct Arenas {
+  const BlockLayout *lay[2];
+  const double *stored[2];
+  const TempSet *temps;
+  const double *temp[2];
+};
+
+static bool eff_block(const Ref &r, const Arenas &A, int side, int a, int &a2, uint64_t &addr,
+                      int &rs, int &cs) {
+  const BlockLayout &b = *A.lay[side];
+  if (r.arena < 0) {
+    a2 = a;
+    addr = ~0ull;
+    rs = cs = 0;
+    return true;
+  }
+  const std::vector<int> *bra;
+  const std::vector<int64_t> *off;
+  int64_t base;
+  int dnu, dnd;
+  const double *arena;
+  bool tr = r.tr;
+  if (r.arena < 2) {
+    const Family &F = b.fam[r.fam];
+    bra = &F.bra;
+    off = &F.off;
+    base = F.base;
+    dnu = F.dnu;
+    dnd = F.dnd;
+    arena = A.stored[side];
+  } else {
+    const TempFamily &T = A.temps->fam[side][r.fam];
+    bra = &T.bra;
+    off = &T.off;
+    base = T.base;
+    dnu = T.dnu;
+    dnd = T.dnd;
+    arena = A.temp[side];
+  }
+  const int ma = b.sec[a].dim;
+  if (!tr) {
+    a2 = (*bra)[a];
+    if (a2 < 0) return false;
+    const int m2 = b.sec[a2].dim;
+    addr = eaddr(arena) + base + (*off)[a] + (int64_t)r.k * m2 * ma;
+    rs = ma;
+    cs = 1;
+  } else {
+    const int ket = b.find(b.sec[a].nu - dnu, b.sec[a].nd - dnd);
+    if (ket < 0 || (*bra)[ket] != a) return false;
+    a2 = ket;
+    const int m2 = b.sec[ket].dim;
+    addr = eaddr(arena) + base + (*off)[ket] + (int64_t)r.k * ma * m2;
+    rs = 1;
+    cs = m2;
+  }
+  return true;
+}
+
+static int site_image(const Mat4 &S, int b, double &val) {
+  for (int r = 0; r < 4; ++r)
+    if (S[r * 4 + b] != 0.0) {
+      val = S[r * 4 + b];
+      return r;
+    }
+  return -1;
+}
+
+static inline int npart(const Sector &s) { return s.nu + s.nd; }
+static inline int nsite(int b) { return SITE_NU[b] + SITE_ND[b]; }
+
+// task list grouped by output block
+struct ChainList {
+  std::vector<std::pair<int, ChainEntry>> ent;  // (group key, entry)
+  std::vector<ChainGroup> grp;                  // one per key, filled by finish()
+  std::vector<ChainEntry> flat;
+  int ntiles = 0;
+  double flops = 0.0;
+  void finish(const std::vector<ChainGroup> &protos) {
+    std::stable_sort(ent.begin(), ent.end(),
+                     [](const std::pair<int, ChainEntry> &x, const std::pair<int, ChainEntry> &y) {
+                       return x.first < y.first;
+                     });
+    flat.clear();
+    grp.clear();
+    ntiles = 0;
+    size_t i = 0;
+    while (i < ent.size()) {
+      size_t j = i;
+      while (j < ent.size() && ent[j].first == ent[i].first) ++j;
+      ChainGroup g = protos[ent[i].first];
+      g.first = (int)flat.size();
+      g.count = (int)(j - i);
+      g.tile0 = ntiles;
+      ntiles += ((g.m + 31) / 32) * ((g.q + 31) / 32);
+      for (size_t t = i; t < j; ++t) flat.push_back(ent[t].second);
+      grp.push_back(g);
+      i = j;
+    }
+  }
+};
+
+static double entry_flops(int m, int n, int p, int q, bool xid, bool zid) {
+  if (xid && zid) return 0.0;
+  if (xid) return 2.0 * n * p * q;
+  if (zid) return 2.0 * m * n * p;
+  return 2.0 * std::min((double)m * n * p + (double)m * p * q, (double)n * p * q + (double)m * n * q);
+}
+
+// ---------------------------------------------------------------- temporaries
+
+struct DevTemps {
+  TempSet set;
+  DBuf<double> arena[2];
+  DBuf<double> coefs;
+  DBuf<LincombTask> tasks;
+};
+
+// Materialize the temporaries of a TempSet (Sec. 2.2.3 pre-summation).
+static void build_temps(DevTemps &T, const BlockLayout *lay[2], const double *stored[2],
+                        cudaStream_t s) {
+  T.set.layout(lay);
+  for (int side = 0; side < 2; ++side) T.arena[side].alloc((size_t)std::max<int64_t>(T.set.total[side], 1));
+  std::vector<double> coef;
+  std::vector<int64_t> coef_off;
+  std::vector<std::pair<int, int>> fam_list;
+  for (int side = 0; side < 2; ++side)
+    for (int f = 0; f < (int)T.set.fam[side].size(); ++f) {
+      const TempFamily &TF = T.set.fam[side][f];
+      const Family &SF = lay[side]->fam[TF.src_fam];
+      coef_off.push_back((int64_t)coef.size());
+      fam_list.push_back({side, f});
+      const size_t base = coef.size();
+      coef.resize(base + (size_t)TF.K() * SF.K(), 0.0);
+      for (int t = 0; t < TF.K(); ++t)
+        for (auto &u : TF.coefs[t]) coef[base + (size_t)t * SF.K() + u.first] += u.second;
+    }
+  T.coefs.upload(coef, s);
+  std::vector<LincombTask> tasks;
+  int ntiles = 0;
+  for (size_t fi = 0; fi < fam_list.size(); ++fi) {
+    const int side = fam_list[fi].first, f = fam_list[fi].second;
+    const TempFamily &TF = T.set.fam[side][f];
+    const BlockLayout &b = *lay[side];
+    const Family &SF = b.fam[TF.src_fam];
+    for (int a = 0; a < (int)b.sec.size(); ++a) {
+      const int a2 = TF.bra[a];
+      if (a2 < 0) continue;
+      LincombTask t;
+      t.out = eaddr(T.arena[side].p) + TF.base + TF.off[a];
+      int64_t src;
+      if (!TF.tr) {
+        if (SF.off[a] < 0) continue;
+        src = SF.base + SF.off[a];
+      } else {
+        if (SF.off[a2] < 0 || SF.bra[a2] != a) continue;
+        src = SF.base + SF.off[a2];
+      }
+      t.src = eaddr(stored[side]) + src;
+      t.coef = eaddr(T.coefs.p) + coef_off[fi];
+      t.kout = TF.K();
+      t.ksrc = SF.K();
+      t.rows = b.sec[a2].dim;
+      t.cols = b.sec[a].dim;
+      t.tr = TF.tr ? 1 : 0;
+      t.tile0 = ntiles;
+      const int64_t E = (int64_t)t.rows * t.cols;
+      ntiles += ((t.kout + 31) / 32) * (int)((E + 31) / 32);
+      tasks.push_back(t);
+    }
+  }
+  // temp slabs without a source slab stay zero
+  for (int side = 0; side < 2; ++side)
+    if (T.set.total[side] > 0)
+      CK(cudaMemsetAsync(T.arena[side].p, 0, T.set.total[side] * sizeof(double), s));
+  T.tasks.upload(tasks, s);
+  CK(launch_lincomb_fp64(T.tasks.p, (int)tasks.size(), ntiles, s));
+}
+
+// ---------------------------------------------------------------- H.psi plan
+
+struct HPlan {
+  bool valid = false;
+  int k = -1;
+  const DevBlock *lb = nullptr, *rb = nullptr;
+  Psi psi;
+  DevTemps temps;
+  DBuf<ChainEntry> ent;
+  DBuf<ChainGroup> grp;
+  int ngroups = 0, ntiles = 0;
+  double flops = 0.0;
+  long long ntasks = 0;
+  DBuf<double> diag;
+};
+
+}  // namespace dmrg
+
+struct dmrg_ctx {
+  int L = 0, N = 0, nu = 0, nd = 0, M = 0, prec = 0;
+  cudaStream_t stream = nullptr;
+  dmrg::Integrals I;
+  std::vector<std::unique_ptr<dmrg::DevBlock>> left, right;  // by size
+  int k = 0, dir = 1;
+  dmrg::HPlan plan;
+  // wave function at the current position
+  dmrg::DBuf<double> psi;
+  bool psi_valid = false;
+  // Davidson workspace
+  dmrg::DBuf<double> V, AV, work, partial, small, r, t, hx;
+  cusolverDnHandle_t solver = nullptr;
+  dmrg::DBuf<double> sol_work;
+  dmrg::DBuf<int> sol_info;
+};
+
+namespace dmrg {
+
+static DevBlock *lblock(dmrg_ctx *c) {
+  return c->k < (int)c->left.size() ? c->left[c->k].get() : nullptr;
+}
+static DevBlock *rblock(dmrg_ctx *c) {
+  const int n = c->L - c->k - 2;
+  return (n >= 0 && n < (int)c->right.size()) ? c->right[n].get() : nullptr;
+}
+
+static void require_blocks(dmrg_ctx *c) {
+  if (!lblock(c) || !rblock(c))
+    throw Fail{DMRG_ESTATE, "blocks for position " + std::to_string(c->k) + " are not built"};
+}
+
+static std::unique_ptr<DevBlock> empty_block(int side, int L) {
+  auto b = std::make_unique<DevBlock>();
+  build_layout(b->lay, side, L, {}, {{0, 0, 1}});
+  return b;
+}
+
+static void build_hplan(dmrg_ctx *c) {
+  HPlan &P = c->plan;
+  require_blocks(c);
+  DevBlock *lb = lblock(c), *rb = rblock(c);
+  if (P.valid && P.k == c->k && P.lb == lb && P.rb == rb) return;
+  P.valid = false;
+  P.k = c->k;
+  P.lb = lb;
+  P.rb = rb;
+  P.psi = psi_layout(lb->lay, rb->lay, c->nu, c->nd);
+  const Psi &Y = P.psi;
+  auto pieces = compress_pieces(hamiltonian_pieces(c->I, c->k, lb->lay.empty(), rb->lay.empty()));
+  P.temps.set = TempSet();
+  struct RP {
+    Ref l, r;
+    const Piece *p;
+  };
+  std::vector<RP> rps;
+  for (auto &p : pieces) {
+    bool zl, zr;
+    Ref l = resolve(p.l, 0, lb->lay, P.temps.set, zl);
+    if (zl) continue;
+    Ref r = resolve(p.r, 1, rb->lay, P.temps.set, zr);
+    if (zr) continue;
+    rps.push_back({l, r, &p});
+  }
+  const BlockLayout *lay[2] = {&lb->lay, &rb->lay};
+  const double *stored[2] = {lb->arena(), rb->arena()};
+  build_temps(P.temps, lay, stored, c->stream);
+  Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
+           {P.temps.arena[0].p, P.temps.arena[1].p}};
+
+  std::vector<ChainGroup> protos(Y.blk.size());
+  for (size_t i = 0; i < Y.blk.size(); ++i) {
+    ChainGroup g{};
+    g.d = (uint64_t)Y.blk[i].off;
+    g.drs = Y.blk[i].md;
+    g.dcs = 1;
+    g.m = Y.blk[i].ma;
+    g.q = Y.blk[i].md;
+    protos[i] = g;
+  }
+  ChainList CL;
+  double flops = 0.0;
+  for (auto &rp : rps) {
+    const Piece &p = *rp.p;
+    const int psl = mat_parity(p.sl), psr = mat_parity(p.sr);
+    for (size_t si = 0; si < Y.blk.size(); ++si) {
+      const PsiBlock &s = Y.blk[si];
+      double vb, vc;
+      const int b2 = site_image(p.sl, s.b, vb);
+      if (b2 < 0) continue;
+      const int c2 = site_image(p.sr, s.c, vc);
+      if (c2 < 0) continue;
+      int a2, d2, lrs, lcs, rrs, rcs;
+      uint64_t la, ra;
+      if (!eff_block(rp.l, A, 0, s.a, a2, la, lrs, lcs)) continue;
+      if (!eff_block(rp.r, A, 1, s.d, d2, ra, rrs, rcs)) continue;
+      const int so = Y.find(a2, b2, c2, d2);
+      if (so < 0) continue;
+      const PsiBlock &t = Y.blk[so];
+      const int na = npart(lb->lay.sec[s.a]), nb = nsite(s.b), nc = nsite(s.c);
+      const int sgn_exp = rp.r.par * (na + nb + nc) + psr * (na + nb) + psl * na;
+      const double f = p.coef * vb * vc * ((sgn_exp & 1) ? -1.0 : 1.0);
+      const bool xid = rp.l.arena < 0, zid = rp.r.arena < 0;
+      ChainEntry e{};
+      e.x = la;
+      e.xrs = lrs;
+      e.xcs = lcs;
+      e.y = (uint64_t)s.off;
+      e.yrs = s.md;
+      e.ycs = 1;
+      e.z = ra;
+      e.zrs = rcs;  // Z = R^T
+      e.zcs = rrs;
+      e.n = s.ma;
+      e.p = s.md;
+      e.f = f;
+      CL.ent.push_back({(int)so, e});
+      flops += entry_flops(t.ma, s.ma, s.md, t.md, xid, zid);
+      if (p.hc) {
+        ChainEntry h{};
+        h.x = la;
+        h.xrs = lcs;  // X = L^T
+        h.xcs = lrs;
+        h.y = (uint64_t)t.off;
+        h.yrs = t.md;
+        h.ycs = 1;
+        h.z = ra;  // Z = R
+        h.zrs = rrs;
+        h.zcs = rcs;
+        h.n = t.ma;
+        h.p = t.md;
+        h.f = f;
+        CL.ent.push_back({(int)si, h});
+        flops += entry_flops(s.ma, t.ma, t.md, s.md, xid, zid);
+      }
+    }
+  }
+  CL.finish(protos);
+  P.ent.upload(CL.flat, c->stream);
+  P.grp.upload(CL.grp, c->stream);
+  P.ngroups = (int)CL.grp.size();
+  P.ntiles = CL.ntiles;
+  P.flops = flops;
+  P.ntasks = (long long)CL.flat.size();
+  P.diag.alloc((size_t)std::max<int64_t>(Y.dim, 1));
+  CK(cudaMemsetAsync(P.diag.p, 0, Y.dim * sizeof(double), c->stream));
+  CK(launch_diag_fp64(P.ent.p, P.grp.p, P.ngroups, 0, 0, P.diag.p, c->stream));
+  CK(cudaStreamSynchronize(c->stream));  // host vectors above are released on return
+  P.valid = true;
+}
+
+static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma) {
+  HPlan &P = c->plan;
+  CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
+  CK(launch_chain_fp64(P.ent.p, P.grp.p, P.ngroups, P.ntiles, 0, (uint64_t)(uintptr_t)psi, 0,
+                       (uint64_t)(uintptr_t)sigma, c->stream));
+}
+
+// ---------------------------------------------------------------- renormalization
+
+// Operators of the new block: O^T (sum_pieces blk (x) site) O per new sector
+// pair (Sec. 2.2.2, Eq. renorm_mat), never forming the enlarged matrices.
+static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, const Enlarged &enl,
+                                                   const std::vector<int> &kept,
+                                                   DBuf<double> &Odev,
+                                                   const std::vector<int64_t> &Ooff) {
+  const int side = direction > 0 ? 0 : 1;
+  DevBlock *old = side == 0 ? lblock(c) : rblock(c);
+  auto nb = std::make_unique<DevBlock>();
+  std::vector<Sector> sec;
+  std::vector<int> new_of_enl(enl.size(), -1);
+  for (size_t e = 0; e < enl.size(); ++e)
+    if (kept[e] > 0) {
+      new_of_enl[e] = (int)sec.size();
+      sec.push_back({enl[e].nu, enl[e].nd, kept[e]});
+    }
+  if (sec.empty()) throw Fail{DMRG_EINVAL, "renormalization keeps no state"};
+  std::vector<int> sites;
+  if (side == 0) for (int s = 0; s <= c->k; ++s) sites.push_back(s);
+  else for (int s = c->k + 1; s < c->L; ++s) sites.push_back(s);
+  build_layout(nb->lay, side, c->L, sites, sec);
+  nb->ops.alloc((size_t)std::max<int64_t>(nb->lay.total, 1));
+  CK(cudaMemsetAsync(nb->ops.p, 0, std::max<int64_t>(nb->lay.total, 1) * sizeof(double), c->stream));
+
+  auto defs = new_block_ops(c->I, c->k, side, nb->lay, old->lay.empty());
+  DevTemps temps;
+  struct RD {
+    int fam, k;
+    Ref blk;
+    Mat4 site;
+    double coef;
+  };
+  std::vector<RD> rds;
+  for (auto &d : defs)
+    for (auto &hp : d.def) {
+      bool z;
+      Ref r = resolve(hp.blk, side, old->lay, temps.set, z);
+      if (z) continue;
+      rds.push_back({d.fam, d.k, r, hp.site, hp.coef});
+    }
+  const BlockLayout *lay[2];
+  const double *stored[2];
+  lay[side] = &old->lay;
+  stored[side] = old->arena();
+  // the other side has no temporaries; give it a harmless layout
+  BlockLayout dummy;
+  build_layout(dummy, 1 - side, c->L, {}, {{0, 0, 1}});
+  lay[1 - side] = &dummy;
+  stored[1 - side] = nullptr;
+  build_temps(temps, lay, stored, c->stream);
+  Arenas A{{lay[0], lay[1]}, {stored[0], stored[1]}, &temps.set,
+           {temps.arena[0].p, temps.arena[1].p}};
+
+  // sub-block lookup: enlarged sector index + row offset of (x, y)
+  std::map<std::pair<int, int>, std::pair<int, int>> where;
+  for (size_t e = 0; e < enl.size(); ++e)
+    for (auto &sb : enl[e].sub) where[{sb.x, sb.y}] = {(int)e, sb.roff};
+
+  // output groups: (family, k, new ket sector)
+  std::vector<ChainGroup> protos;
+  std::map<std::tuple<int, int, int>, int> gid;
+  ChainList CL;
+  const double *Op = Odev.p;
+  for (auto &rd : rds) {
+    const Family &F = nb->lay.fam[rd.fam];
+    const int pblk = rd.blk.par, psite = mat_parity(rd.site);
+    for (size_t e = 0; e < enl.size(); ++e) {
+      const int An = new_of_enl[e];
+      if (An < 0) continue;
+      const int Bn = F.bra[An];
+      if (Bn < 0) continue;
+      for (auto &sb : enl[e].sub) {
+        // ket sub-block (x, y): left (a, b), right (c, d)
+        const int blk_sec = side == 0 ? sb.x : sb.y;
+        const int site_st = side == 0 ? sb.y : sb.x;
+        double sv;
+        const int site2 = site_image(rd.site, site_st, sv);
+        if (site2 < 0) continue;
+        int b2, rs, cs;
+        uint64_t addr;
+        if (!eff_block(rd.blk, A, side, blk_sec, b2, addr, rs, cs)) continue;
+        const std::pair<int, int> key2 = side == 0 ? std::make_pair(b2, site2) : std::make_pair(site2, b2);
+        auto it = where.find(key2);
+        if (it == where.end()) continue;
+        const int e2 = it->second.first, roff2 = it->second.second;
+        if (new_of_enl[e2] != Bn) continue;
+        const int sgn_exp = side == 0 ? psite * npart(old->lay.sec[blk_sec])
+                                      : pblk * nsite(site_st);
+        const double f = rd.coef * sv * ((sgn_exp & 1) ? -1.0 : 1.0);
+        const int mk = kept[e], mk2 = kept[e2];
+        const int mb = old->lay.sec[blk_sec].dim, mb2 = old->lay.sec[b2].dim;
+        auto g = std::make_tuple(rd.fam, rd.k, An);
+        int gi;
+        auto git = gid.find(g);
+        if (git == gid.end()) {
+          ChainGroup cg{};
+          cg.d = eaddr(nb->ops.p) + F.base + F.off[An] + (int64_t)rd.k * mk2 * mk;
+          cg.drs = mk;
+          cg.dcs = 1;
+          cg.m = mk2;
+          cg.q = mk;
+          gi = (int)protos.size();
+          protos.push_back(cg);
+          gid[g] = gi;
+        } else {
+          gi = git->second;
+        }
+        ChainEntry ce{};
+        // X = O_{e2}[rows of (b2, site2)]^T : mk2 x mb2
+        ce.x = eaddr(Op) + Ooff[e2] + (int64_t)roff2 * mk2;
+        ce.xrs = 1;
+        ce.xcs = mk2;
+        ce.y = addr;
+        ce.yrs = rs;
+        ce.ycs = cs;
+        // Z = O_e[rows of (x, y)] : mb x mk
+        ce.z = eaddr(Op) + Ooff[e] + (int64_t)sb.roff * mk;
+        ce.zrs = mk;
+        ce.zcs = 1;
+        ce.n = mb2;
+        ce.p = mb;
+        ce.f = f;
+        if (rd.blk.arena < 0) {  // identity block operator: n == p
+          ce.y = ~0ull;
+          ce.n = mb;
+        }
+        CL.ent.push_back({gi, ce});
+      }
+    }
+  }
+  CL.finish(protos);
+  DBuf<ChainEntry> dent;
+  DBuf<ChainGroup> dgrp;
+  dent.upload(CL.flat, c->stream);
+  dgrp.upload(CL.grp, c->stream);
+  CK(launch_chain_fp64(dent.p, dgrp.p, (int)CL.grp.size(), CL.ntiles, 0, 0, 0, 0, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  nb->parent = enl;
+  nb->kept = kept;
+  nb->Ooff = Ooff;
+  std::swap(nb->O.p, Odev.p);
+  std::swap(nb->O.n, Odev.n);
+  return nb;
+}
+
+// ---------------------------------------------------------------- RDM + truncation
+
+static void rdm_truncate(dmrg_ctx *c, int direction, const Enlarged &enl, std::vector<int> &kept,
+                         DBuf<double> &Odev, std::vector<int64_t> &Ooff, double &dw) {
+  HPlan &P = c->plan;
+  const Psi &Y = P.psi;
+  const int ne = (int)enl.size();
+  std::vector<int64_t> roff(ne);
+  int64_t tot = 0;
+  for (int e = 0; e < ne; ++e) {
+    roff[e] = tot;
+    tot += (int64_t)enl[e].dim * enl[e].dim;
+  }
+  DBuf<double> rho;
+  rho.alloc((size_t)std::max<int64_t>(tot, 1));
+  CK(cudaMemsetAsync(rho.p, 0, std::max<int64_t>(tot, 1) * sizeof(double), c->stream));
+  // rho^L[(a,b),(a',b')] = sum_{c,d} psi_abcd psi_a'b'cd^T ; rho^R[(c,d),(c',d')] = sum_{a,b} psi_abcd^T psi_abc'd'
+  std::map<std::pair<int, int>, std::pair<int, int>> where;
+  for (int e = 0; e < ne; ++e)
+    for (auto &sb : enl[e].sub) where[{sb.x, sb.y}] = {e, sb.roff};
+  std::vector<ChainGroup> protos;
+  std::map<std::tuple<int, int, int, int>, int> gid;
+  ChainList CL;
+  for (auto &s1 : Y.blk)
+    for (auto &s2 : Y.blk) {
+      std::pair<int, int> k1, k2;
+      if (direction > 0) {
+        if (s1.c != s2.c || s1.d != s2.d) continue;
+        k1 = {s1.a, s1.b};
+        k2 = {s2.a, s2.b};
+      } else {
+        if (s1.a != s2.a || s1.b != s2.b) continue;
+        k1 = {s1.c, s1.d};
+        k2 = {s2.c, s2.d};
+      }
+      auto w1 = where.at(k1), w2 = where.at(k2);
+      if (w1.first != w2.first) continue;
+      const int e = w1.first, n = enl[e].dim;
+      auto key = std::make_tuple(k1.first, k1.second, k2.first, k2.second);
+      int gi;
+      auto git = gid.find(key);
+      const int rows = direction > 0 ? s1.ma : s1.md;
+      const int cols = direction > 0 ? s2.ma : s2.md;
+      if (git == gid.end()) {
+        ChainGroup g{};
+        g.d = eaddr(rho.p) + roff[e] + (int64_t)w1.second * n + w2.second;
+        g.drs = n;
+        g.dcs = 1;
+        g.m = rows;
+        g.q = cols;
+        gi = (int)protos.size();
+        protos.push_back(g);
+        gid[key] = gi;
+      } else {
+        gi = git->second;
+      }
+      ChainEntry ce{};
+      ce.x = ~0ull;
+      if (direction > 0) {  // psi1 (ma x md) * psi2^T (md x ma')
+        ce.y = (uint64_t)s1.off;
+        ce.yrs = s1.md;
+        ce.ycs = 1;
+        ce.z = (uint64_t)s2.off;
+        ce.zrs = 1;
+        ce.zcs = s2.md;
+        ce.n = s1.ma;
+        ce.p = s1.md;
+      } else {  // psi1^T (md x ma) * psi2 (ma x md')
+        ce.y = (uint64_t)s1.off;
+        ce.yrs = 1;
+        ce.ycs = s1.md;
+        ce.z = (uint64_t)s2.off;
+        ce.zrs = s2.md;
+        ce.zcs = 1;
+        ce.n = s1.md;
+        ce.p = s1.ma;
+      }
+      ce.f = 1.0;
+      CL.ent.push_back({gi, ce});
+    }
+  CL.finish(protos);
+  DBuf<ChainEntry> dent;
+  DBuf<ChainGroup> dgrp;
+  dent.upload(CL.flat, c->stream);
+  dgrp.upload(CL.grp, c->stream);
+  const uint64_t pb = (uint64_t)(uintptr_t)c->psi.p;
+  CK(launch_chain_fp64(dent.p, dgrp.p, (int)CL.grp.size(), CL.ntiles, 0, pb, pb, 0, c->stream));
+
+  // per-sector eigendecomposition (LAPACK-style syevd, eigenvalues ascending)
+  int maxn = 0;
+  for (auto &e : enl) maxn = std::max(maxn, e.dim);
+  if (!c->solver) {
+    CKS(cusolverDnCreate(&c->solver));
+  }
+  CKS(cusolverDnSetStream(c->solver, c->stream));
+  int lwork = 0;
+  CKS(cusolverDnDsyevd_bufferSize(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, maxn,
+                                  rho.p, maxn, nullptr, &lwork));
+  c->sol_work.alloc((size_t)std::max(lwork, 1));
+  c->sol_info.alloc(1);
+  std::vector<int64_t> eoff(ne);
+  int64_t etot = 0;
+  for (int e = 0; e < ne; ++e) {
+    eoff[e] = etot;
+    etot += enl[e].dim;
+  }
+  DBuf<double> ev;
+  ev.alloc((size_t)std::max<int64_t>(etot, 1));
+  for (int e = 0; e < ne; ++e) {
+    const int n = enl[e].dim;
+    if (n == 0) continue;
+    CKS(cusolverDnDsyevd(c->solver, CUSOLVER_EIG_MODE_VECTOR, CUBLAS_FILL_MODE_LOWER, n,
+                         rho.p + roff[e], n, ev.p + eoff[e], c->sol_work.p, lwork, c->sol_info.p));
+  }
+  std::vector<double> evh(etot);
+  CK(cudaMemcpyAsync(evh.data(), ev.p, etot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // global top-M selection: descending eigenvalue, ties by (sector, in-sector order)
+  struct Cand {
+    double v;
+    int e, j;
+  };
+  std::vector<Cand> cand;
+  double trace = 0.0;
+  for (int e = 0; e < ne; ++e)
+    for (int j = 0; j < enl[e].dim; ++j) {
+      const double x = evh[eoff[e] + (enl[e].dim - 1 - j)];  // j-th largest in the sector
+      cand.push_back({x, e, j});
+      trace += x;
+    }
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) {
+    if (x.v != y.v) return x.v > y.v;
+    if (x.e != y.e) return x.e < y.e;
+    return x.j < y.j;
+  });
+  kept.assign(ne, 0);
+  double kw = 0.0;
+  std::vector<std::vector<int>> cols(ne);
+  for (int i = 0; i < (int)cand.size() && i < c->M; ++i) {
+    if (cand[i].v <= 1e-13) break;
+    kept[cand[i].e]++;
+    kw += cand[i].v;
+    cols[cand[i].e].push_back(enl[cand[i].e].dim - 1 - cand[i].j);  // column in ascending order
+  }
+  dw = trace - kw;
+  Ooff.assign(ne, 0);
+  int64_t otot = 0;
+  for (int e = 0; e < ne; ++e) {
+    Ooff[e] = otot;
+    otot += (int64_t)enl[e].dim * kept[e];
+    std::sort(cols[e].begin(), cols[e].end(), std::greater<int>());  // descending eigenvalue
+  }
+  Odev.alloc((size_t)std::max<int64_t>(otot, 1));
+  std::vector<int> allcols;
+  std::vector<int64_t> coff(ne);
+  for (int e = 0; e < ne; ++e) {
+    coff[e] = (int64_t)allcols.size();
+    allcols.insert(allcols.end(), cols[e].begin(), cols[e].end());
+  }
+  DBuf<int> dcols;
+  dcols.upload(allcols, c->stream);
+  for (int e = 0; e < ne; ++e)
+    if (kept[e] > 0)
+      CK(launch_gather_columns(Odev.p + Ooff[e], rho.p + roff[e], enl[e].dim, dcols.p + coff[e],
+                               kept[e], c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+}
+
+// ---------------------------------------------------------------- wave-function prediction
+
+// Forward move k -> k+1 (new left block built from O): psi'(A, c, e, f) =
+// sum_{(a,b) in A, d} O_A[(a,b)]^T psi(a,b,c,d) O^R_d[(e,f)]^T, with O^R the
+// renormalization that built the old right block.  Backward move is the mirror.
+static void predict_psi(dmrg_ctx *c, const Psi &old, const DBuf<double> &oldpsi, int direction,
+                        const DevBlock &nb) {
+  c->psi_valid = false;
+  DevBlock *lb = lblock(c), *rb = rblock(c);  // position already moved
+  if (!lb || !rb) return;
+  const DevBlock &other = direction > 0 ? *c->right[c->L - c->k - 1] : *c->left[c->k + 1];
+  // "other" is the block whose parent enlarged layout splits into the new site + new block
+  if (other.parent.empty()) return;
+  Psi Y = psi_layout(lb->lay, rb->lay, c->nu, c->nd);
+  std::vector<ChainGroup> protos(Y.blk.size());
+  for (size_t i = 0; i < Y.blk.size(); ++i) {
+    ChainGroup g{};
+    g.d = (uint64_t)Y.blk[i].off;
+    g.drs = Y.blk[i].md;
+    g.dcs = 1;
+    g.m = Y.blk[i].ma;
+    g.q = Y.blk[i].md;
+    protos[i] = g;
+  }
+  // enlarged sector of the new block for each old (x, y) pair
+  std::map<std::pair<int, int>, std::pair<int, int>> where_new;
+  for (size_t e = 0; e < nb.parent.size(); ++e)
+    for (auto &sb : nb.parent[e].sub) where_new[{sb.x, sb.y}] = {(int)e, sb.roff};
+  std::vector<int> new_of_enl(nb.parent.size(), -1);
+  for (size_t e = 0, n = 0; e < nb.parent.size(); ++e)
+    if (nb.kept[e] > 0) new_of_enl[e] = (int)n++;
+  std::vector<int> oth_of_enl(other.parent.size(), -1);
+  for (size_t e = 0, n = 0; e < other.parent.size(); ++e)
+    if (other.kept[e] > 0) oth_of_enl[e] = (int)n++;
+  ChainList CL;
+  for (auto &s : old.blk) {
+    if (direction > 0) {
+      // new-left sector from (a, b)
+      auto wn = where_new.find({s.a, s.b});
+      if (wn == where_new.end()) continue;
+      const int eA = wn->second.first;
+      const int A = new_of_enl[eA];
+      if (A < 0) continue;
+      // old right sector d expands into (e_site, f) sub-blocks of other.parent[enl of d]
+      int ed = -1;
+      for (size_t e = 0; e < other.parent.size(); ++e)
+        if (oth_of_enl[e] == s.d) ed = (int)e;
+      if (ed < 0) continue;
+      const int mA = nb.kept[eA], md = other.kept[ed];
+      for (auto &sb : other.parent[ed].sub) {
+        const int so = Y.find(A, s.c, sb.x, sb.y);
+        if (so < 0) continue;
+        ChainEntry ce{};
+        ce.x = eaddr(nb.O.p) + nb.Ooff[eA] + (int64_t)wn->second.second * mA;  // O_A rows^T
+        ce.xrs = 1;
+        ce.xcs = mA;
+        ce.y = eaddr(oldpsi.p) + s.off;
+        ce.yrs = s.md;
+        ce.ycs = 1;
+        ce.z = eaddr(other.O.p) + other.Ooff[ed] + (int64_t)sb.roff * md;  // (O^R_d rows)^T
+        ce.zrs = 1;
+        ce.zcs = md;
+        ce.n = s.ma;
+        ce.p = s.md;
+        ce.f = 1.0;
+        CL.ent.push_back({so, ce});
+      }
+    } else {
+      auto wn = where_new.find({s.c, s.d});
+      if (wn == where_new.end()) continue;
+      const int eD = wn->second.first;
+      const int D = new_of_enl[eD];
+      if (D < 0) continue;
+      int ea = -1;
+      for (size_t e = 0; e < other.parent.size(); ++e)
+        if (oth_of_enl[e] == s.a) ea = (int)e;
+      if (ea < 0) continue;
+      const int mD = nb.kept[eD], ma = other.kept[ea];
+      for (auto &sb : other.parent[ea].sub) {
+        const int so = Y.find(sb.x, sb.y, s.b, D);
+        if (so < 0) continue;
+        ChainEntry ce{};
+        ce.x = eaddr(other.O.p) + other.Ooff[ea] + (int64_t)sb.roff * ma;  // O^L_a rows
+        ce.xrs = ma;
+        ce.xcs = 1;
+        ce.y = eaddr(oldpsi.p) + s.off;
+        ce.yrs = s.md;
+        ce.ycs = 1;
+        ce.z = eaddr(nb.O.p) + nb.Ooff[eD] + (int64_t)wn->second.second * mD;  // O_D rows
+        ce.zrs = mD;
+        ce.zcs = 1;
+        ce.n = s.ma;
+        ce.p = s.md;
+        ce.f = 1.0;
+        CL.ent.push_back({so, ce});
+      }
+    }
+  }
+  CL.finish(protos);
+  c->psi.alloc((size_t)std::max<int64_t>(Y.dim, 1));
+  CK(cudaMemsetAsync(c->psi.p, 0, Y.dim * sizeof(double), c->stream));
+  DBuf<ChainEntry> dent;
+  DBuf<ChainGroup> dgrp;
+  dent.upload(CL.flat, c->stream);
+  dgrp.upload(CL.grp, c->stream);
+  CK(launch_chain_fp64(dent.p, dgrp.p, (int)CL.grp.size(), CL.ntiles, 0, 0, 0,
+                       (uint64_t)(uintptr_t)c->psi.p, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->psi_valid = !CL.flat.empty();
+}
+
+static void do_renormalize(dmrg_ctx *c, int direction, const int *kept_in, const double *O,
+                           double *dw_out, int *kept_out) {
+  if (O == nullptr) require_blocks(c);
+  else if (!(direction > 0 ? lblock(c) : rblock(c)))
+    throw Fail{DMRG_ESTATE, "the block to enlarge is not built"};
+  if (direction > 0 && c->k >= c->L - 2) throw Fail{DMRG_ESTATE, "cannot move right of L-2"};
+  if (direction < 0 && c->k <= 0) throw Fail{DMRG_ESTATE, "cannot move left of 0"};
+  const int side = direction > 0 ? 0 : 1;
+  DevBlock *old = side == 0 ? lblock(c) : rblock(c);
+  Enlarged enl = enlarged(old->lay, direction);
+  std::vector<int> kept;
+  DBuf<double> Odev;
+  std::vector<int64_t> Ooff;
+  double dw = 0.0;
+  if (O == nullptr) {
+    build_hplan(c);
+    if (!c->psi_valid) throw Fail{DMRG_ESTATE, "no wave function at this position (run dmrg_davidson)"};
+    rdm_truncate(c, direction, enl, kept, Odev, Ooff, dw);
+  } else {
+    if (!kept_in) throw Fail{DMRG_EINVAL, "kept dims required with an explicit O"};
+    kept.assign(kept_in, kept_in + enl.size());
+    Ooff.assign(enl.size(), 0);
+    int64_t tot = 0;
+    for (size_t e = 0; e < enl.size(); ++e) {
+      if (kept[e] < 0 || kept[e] > enl[e].dim) throw Fail{DMRG_EINVAL, "kept dim out of range"};
+      Ooff[e] = tot;
+      tot += (int64_t)enl[e].dim * kept[e];
+    }
+    Odev.alloc((size_t)std::max<int64_t>(tot, 1));
+    if (tot) CK(cudaMemcpyAsync(Odev.p, O, tot * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  }
+  auto nb = renormalize_block(c, direction, enl, kept, Odev, Ooff);
+  // keep the old psi for the prediction
+  Psi oldlay = c->plan.valid ? c->plan.psi : Psi();
+  DBuf<double> oldpsi;
+  const bool can_predict = (O == nullptr) && c->psi_valid && c->plan.valid;
+  if (can_predict) std::swap(oldpsi.p, c->psi.p), std::swap(oldpsi.n, c->psi.n);
+  c->plan.valid = false;
+  c->psi_valid = false;
+  DevBlock *nbp = nb.get();
+  if (side == 0) {
+    if ((int)c->left.size() <= c->k + 1) c->left.resize(c->k + 2);
+    c->left[c->k + 1] = std::move(nb);
+    c->k += 1;
+  } else {
+    const int n = c->L - c->k - 1;
+    if ((int)c->right.size() <= n) c->right.resize(n + 1);
+    c->right[n] = std::move(nb);
+    c->k -= 1;
+  }
+  c->dir = direction;
+  if (can_predict) predict_psi(c, oldlay, oldpsi, direction, *nbp);
+  if (dw_out) *dw_out = dw;
+  if (kept_out) std::copy(kept.begin(), kept.end(), kept_out);
+}
+
+// ---------------------------------------------------------------- Davidson
+
+static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters, bool &conv) {
+  build_hplan(c);
+  HPlan &P = c->plan;
+  const int64_t n = P.psi.dim;
+  const int kmax = std::min<int64_t>(24, std::max<int64_t>(n, 1));
+  c->V.alloc((size_t)kmax * n);
+  c->AV.alloc((size_t)kmax * n);
+  c->r.alloc(n);
+  c->t.alloc(n);
+  c->hx.alloc(n);
+  c->partial.alloc((size_t)dots_partial_blocks(n) * 32);
+  c->small.alloc(4096);
+  double *G = c->small.p;              // kmax x kmax subspace matrix (row-major, ld 32)
+  double *evals = c->small.p + 1024;   // 32
+  double *evecs = c->small.p + 1056;   // up to 32 x 32
+  double *dots = c->small.p + 2200;    // 32
+  double *scal = c->small.p + 2300;    // theta, norm^2
+  cudaStream_t s = c->stream;
+  std::vector<double> Gh(32 * 32, 0.0);
+
+  // start vector
+  if (!c->psi_valid) {
+    c->psi.alloc(n);
+    CK(launch_fill_guess(c->psi.p, n, 12345ull, s));
+  }
+  CK(cudaMemcpyAsync(c->V.p, c->psi.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  auto normalize = [&](double *x) {
+    CK(launch_dots(x, 1, n, x, c->partial.p, scal + 1, s));
+    CK(launch_scale(x, scal + 1, 1, n, s));
+  };
+  normalize(c->V.p);
+  int k = 1;
+  hpsi_dev(c, c->V.p, c->AV.p);
+  // G[0][0]
+  CK(launch_dots(c->V.p, 1, n, c->AV.p, c->partial.p, dots, s));
+  CK(cudaMemcpyAsync(Gh.data(), dots, sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  double theta = Gh[0];
+  int it = 0;
+  conv = false;
+  double rnorm = 0.0;
+  for (it = 1; it <= max_iter; ++it) {
+    // subspace eigenproblem on the device
+    CK(cudaMemcpyAsync(G, Gh.data(), 32 * 32 * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_jacobi_eigh(G, k, 32, evals, evecs, s));
+    // y = evecs[:, 0] (row-major k x k): gather column 0 into dots
+    std::vector<double> ev(k), Y((size_t)k * k);
+    CK(cudaMemcpyAsync(ev.data(), evals, k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaMemcpyAsync(Y.data(), evecs, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    theta = ev[0];
+    std::vector<double> y0(k);
+    for (int i = 0; i < k; ++i) y0[i] = Y[(size_t)i * k + 0];
+    CK(cudaMemcpyAsync(dots, y0.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(cudaMemcpyAsync(scal, &theta, sizeof(double), cudaMemcpyHostToDevice, s));
+    // x = V y, hx = AV y, r = hx - theta x
+    CK(launch_combine(c->psi.p, c->V.p, dots, k, n, 0.0, s));
+    CK(launch_combine(c->hx.p, c->AV.p, dots, k, n, 0.0, s));
+    CK(launch_residual(c->r.p, c->hx.p, c->psi.p, scal, n, s));
+    CK(launch_dots(c->r.p, 1, n, c->r.p, c->partial.p, scal + 1, s));
+    double r2;
+    CK(cudaMemcpyAsync(&r2, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    rnorm = std::sqrt(std::max(r2, 0.0));
+    if (rnorm <= tol || k >= n) {
+      conv = rnorm <= tol || k >= n;
+      break;
+    }
+    if (k == kmax) {
+      // thick restart with the two lowest Ritz vectors
+      const int keep = std::min(2, k);
+      std::vector<double> yk((size_t)keep * k);
+      for (int j = 0; j < keep; ++j)
+        for (int i = 0; i < k; ++i) yk[(size_t)j * k + i] = Y[(size_t)i * k + j];
+      DBuf<double> nv, nav, dy;
+      nv.alloc((size_t)keep * n);
+      nav.alloc((size_t)keep * n);
+      dy.upload(yk, s);
+      for (int j = 0; j < keep; ++j) {
+        CK(launch_combine(nv.p + (int64_t)j * n, c->V.p, dy.p + (size_t)j * k, k, n, 0.0, s));
+        CK(launch_combine(nav.p + (int64_t)j * n, c->AV.p, dy.p + (size_t)j * k, k, n, 0.0, s));
+      }
+      CK(cudaMemcpyAsync(c->V.p, nv.p, (size_t)keep * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(c->AV.p, nav.p, (size_t)keep * n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      std::fill(Gh.begin(), Gh.end(), 0.0);
+      for (int j = 0; j < keep; ++j) Gh[j * 32 + j] = ev[j];
+      k = keep;
+      CK(cudaStreamSynchronize(s));
+    }
+    // correction t = r / (theta - diag), orthogonalized against V twice
+    CK(launch_precond(c->t.p, c->r.p, P.diag.p, scal, n, s));
+    for (int pass = 0; pass < 2; ++pass) {
+      CK(launch_dots(c->V.p, k, n, c->t.p, c->partial.p, dots, s));
+      CK(launch_sub_proj(c->t.p, c->V.p, dots, k, n, s));
+    }
+    CK(launch_dots(c->t.p, 1, n, c->t.p, c->partial.p, scal + 1, s));
+    double t2;
+    CK(cudaMemcpyAsync(&t2, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (!(t2 > 1e-28)) {
+      // preconditioned residual collapsed into the subspace: use the plain residual
+      CK(cudaMemcpyAsync(c->t.p, c->r.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      for (int pass = 0; pass < 2; ++pass) {
+        CK(launch_dots(c->V.p, k, n, c->t.p, c->partial.p, dots, s));
+        CK(launch_sub_proj(c->t.p, c->V.p, dots, k, n, s));
+      }
+      CK(launch_dots(c->t.p, 1, n, c->t.p, c->partial.p, scal + 1, s));
+      CK(cudaMemcpyAsync(&t2, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      if (!(t2 > 1e-28)) {
+        conv = true;  // the subspace is invariant
+        break;
+      }
+    }
+    CK(launch_scale(c->t.p, scal + 1, 1, n, s));
+    CK(cudaMemcpyAsync(c->V.p + (int64_t)k * n, c->t.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    hpsi_dev(c, c->V.p + (int64_t)k * n, c->AV.p + (int64_t)k * n);
+    // new row/column of G: V^T (A v_k)
+    CK(launch_dots(c->V.p, k + 1, n, c->AV.p + (int64_t)k * n, c->partial.p, dots, s));
+    std::vector<double> col(k + 1);
+    CK(cudaMemcpyAsync(col.data(), dots, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    for (int i = 0; i <= k; ++i) {
+      Gh[i * 32 + k] = col[i];
+      Gh[k * 32 + i] = col[i];
+    }
+    ++k;
+  }
+  // normalize the Ritz vector once more
+  normalize(c->psi.p);
+  CK(cudaStreamSynchronize(s));
+  c->psi_valid = true;
+  if (energy) *energy = theta;
+  if (iters) *iters = std::min(it, max_iter);
+}
+
+}  // namespace dmrg
+
+using namespace dmrg;
+
+#define API_BEGIN try {
+#define API_END                                                  \
+  }                                                              \
+  catch (const Fail &f) {                                        \
+    set_error(f.msg);                                            \
+    return f.code;                                               \
+  }                                                              \
+  catch (const std::bad_alloc &) {                               \
+    set_error("host allocation failed");                         \
+    return DMRG_ENOMEM;                                          \
+  }                                                              \
+  catch (const std::exception &e) {                              \
+    set_error(e.what());                                         \
+    return DMRG_EINVAL;                                          \
+  }                                                              \
+  return DMRG_OK;
+
+extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double *v, int M,
+                         int precision, void *cuda_stream, dmrg_ctx **out) {
+  API_BEGIN
+  if (!out) throw Fail{DMRG_EINVAL, "out is NULL"};
+  *out = nullptr;
+  if (L < 2) throw Fail{DMRG_EINVAL, "L must be >= 2"};
+  if (N < 0 || N > 2 * L) throw Fail{DMRG_EINVAL, "N out of range"};
+  if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
+  const int nu = (N + two_sz) / 2, nd = (N - two_sz) / 2;
+  if (nu > L || nd > L) throw Fail{DMRG_EINVAL, "more electrons of one spin than orbitals"};
+  if (M < 1) throw Fail{DMRG_EINVAL, "M must be >= 1"};
+  if (precision != DMRG_PREC_FP64)
+    throw Fail{DMRG_EINVAL, "only DMRG_PREC_FP64 is available in this build"};
+  if (!h || !v) throw Fail{DMRG_EINVAL, "integrals are NULL"};
+  const size_t L2 = (size_t)L * L, L4 = L2 * L2;
+  for (size_t i = 0; i < L2; ++i)
+    if (!std::isfinite(h[i])) throw Fail{DMRG_EINVAL, "h has a non-finite entry"};
+  for (size_t i = 0; i < L4; ++i)
+    if (!std::isfinite(v[i])) throw Fail{DMRG_EINVAL, "v has a non-finite entry"};
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j)
+      if (std::fabs(h[i * L + j] - h[j * L + i]) > 1e-12) throw Fail{DMRG_EINVAL, "h is not symmetric"};
+  auto c = std::make_unique<dmrg_ctx>();
+  c->L = L;
+  c->N = N;
+  c->nu = nu;
+  c->nd = nd;
+  c->M = M;
+  c->prec = precision;
+  c->stream = (cudaStream_t)cuda_stream;
+  c->I.L = L;
+  c->I.h.assign(h, h + L2);
+  c->I.v.assign(v, v + L4);
+  c->left.resize(L);
+  c->right.resize(L);
+  c->left[0] = empty_block(0, L);
+  c->right[0] = empty_block(1, L);
+  // Aufbau product state: right blocks right-to-left with one kept state each
+  for (int k = L - 2; k >= 1; --k) {
+    c->k = k;
+    DevBlock *r = rblock(c.get());
+    Enlarged enl = enlarged(r->lay, -1);
+    const int s = k + 1;
+    const int st = (s < nu ? 1 : 0) + (s < nd ? 2 : 0);
+    std::vector<int> kept(enl.size(), 0);
+    std::vector<double> O;
+    for (size_t e = 0; e < enl.size(); ++e)
+      for (auto &sb : enl[e].sub)
+        if (sb.x == st) {
+          kept[e] = 1;
+          O.assign((size_t)enl[e].dim, 0.0);
+          O[sb.roff] = 1.0;
+        }
+    // a single kept sector: O is its column
+    // (dmrg_renormalize expects all sectors concatenated; others keep 0 columns)
+    DBuf<double> Odev;
+    std::vector<int64_t> Ooff(enl.size(), 0);
+    Odev.upload(O, c->stream);
+    auto nb = renormalize_block(c.get(), -1, enl, kept, Odev, Ooff);
+    c->right[L - k - 1] = std::move(nb);
+  }
+  c->k = 0;
+  c->dir = 1;
+  *out = c.release();
+  API_END
+}
+
+extern "C" int dmrg_free(dmrg_ctx *c) {
+  if (!c) return DMRG_OK;
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  if (c->solver) cusolverDnDestroy(c->solver);
+  delete c;
+  return DMRG_OK;
+}
+
+extern "C" int dmrg_set_position(dmrg_ctx *c, int k, int direction) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
+  if (k < 0 || k > c->L - 2) throw Fail{DMRG_EINVAL, "position out of range"};
+  if (direction != 1 && direction != -1) throw Fail{DMRG_EINVAL, "direction must be +1 or -1"};
+  if (k != c->k) {
+    c->plan.valid = false;
+    c->psi_valid = false;
+  }
+  c->k = k;
+  c->dir = direction;
+  API_END
+}
+
+extern "C" int dmrg_get_position(dmrg_ctx *c, int *k, int *direction) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
+  if (k) *k = c->k;
+  if (direction) *direction = c->dir;
+  API_END
+}
+
+extern "C" int dmrg_psi_layout(dmrg_ctx *c, int *nblocks, int *blocks, long long *dim) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
+  require_blocks(c);
+  Psi P = psi_layout(lblock(c)->lay, rblock(c)->lay, c->nu, c->nd);
+  if (nblocks) *nblocks = (int)P.blk.size();
+  if (dim) *dim = P.dim;
+  if (blocks)
+    for (size_t i = 0; i < P.blk.size(); ++i) {
+      const PsiBlock &b = P.blk[i];
+      int *o = blocks + 7 * i;
+      o[0] = b.a; o[1] = b.b; o[2] = b.c; o[3] = b.d; o[4] = b.ma; o[5] = b.md; o[6] = (int)b.off;
+    }
+  API_END
+}
+
+extern "C" int dmrg_block_sectors(dmrg_ctx *c, int side, int *nsec, int *sectors) {
+  API_BEGIN
+  if (!c || (side != 0 && side != 1)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  DevBlock *b = side == 0 ? lblock(c) : rblock(c);
+  if (!b) throw Fail{DMRG_ESTATE, "block not built"};
+  if (nsec) *nsec = (int)b->lay.sec.size();
+  if (sectors)
+    for (size_t i = 0; i < b->lay.sec.size(); ++i) {
+      sectors[3 * i] = b->lay.sec[i].nu;
+      sectors[3 * i + 1] = b->lay.sec[i].nd;
+      sectors[3 * i + 2] = b->lay.sec[i].dim;
+    }
+  API_END
+}
+
+extern "C" int dmrg_enlarged_layout(dmrg_ctx *c, int direction, int *nsec, int *sectors) {
+  API_BEGIN
+  if (!c || (direction != 1 && direction != -1)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  DevBlock *b = direction > 0 ? lblock(c) : rblock(c);
+  if (!b) throw Fail{DMRG_ESTATE, "block not built"};
+  Enlarged e = enlarged(b->lay, direction);
+  if (nsec) *nsec = (int)e.size();
+  if (sectors)
+    for (size_t i = 0; i < e.size(); ++i) {
+      sectors[3 * i] = e[i].nu;
+      sectors[3 * i + 1] = e[i].nd;
+      sectors[3 * i + 2] = e[i].dim;
+    }
+  API_END
+}
+
+extern "C" int dmrg_hpsi(dmrg_ctx *c, const double *psi, double *sigma, int device_ptrs) {
+  API_BEGIN
+  if (!c || !psi || !sigma) throw Fail{DMRG_EINVAL, "NULL argument"};
+  build_hplan(c);
+  const int64_t n = c->plan.psi.dim;
+  if (device_ptrs) {
+    hpsi_dev(c, psi, sigma);
+  } else {
+    DBuf<double> dp, ds;
+    dp.alloc(n);
+    ds.alloc(n);
+    CK(cudaMemcpyAsync(dp.p, psi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+    hpsi_dev(c, dp.p, ds.p);
+    CK(cudaMemcpyAsync(sigma, ds.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  API_END
+}
+
+extern "C" int dmrg_hpsi_flops(dmrg_ctx *c, double *flops, long long *tasks) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
+  build_hplan(c);
+  if (flops) *flops = c->plan.flops;
+  if (tasks) *tasks = c->plan.ntasks;
+  API_END
+}
+
+extern "C" int dmrg_set_psi(dmrg_ctx *c, const double *psi) {
+  API_BEGIN
+  if (!c || !psi) throw Fail{DMRG_EINVAL, "NULL argument"};
+  build_hplan(c);
+  const int64_t n = c->plan.psi.dim;
+  c->psi.alloc(n);
+  CK(cudaMemcpyAsync(c->psi.p, psi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  c->psi_valid = true;
+  API_END
+}
+
+extern "C" int dmrg_get_psi(dmrg_ctx *c, double *psi) {
+  API_BEGIN
+  if (!c || !psi) throw Fail{DMRG_EINVAL, "NULL argument"};
+  if (!c->psi_valid) throw Fail{DMRG_ESTATE, "no wave function at this position"};
+  build_hplan(c);
+  CK(cudaMemcpyAsync(psi, c->psi.p, c->plan.psi.dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  API_END
+}
+
+extern "C" int dmrg_davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters) {
+  API_BEGIN
+  if (!c || !(tol > 0.0) || max_iter < 1) throw Fail{DMRG_EINVAL, "bad arguments"};
+  bool conv = false;
+  davidson(c, tol, max_iter, energy, iters, conv);
+  if (!conv) throw Fail{DMRG_ENOCONV, "Davidson did not reach the tolerance"};
+  API_END
+}
+
+extern "C" int dmrg_renormalize(dmrg_ctx *c, int direction, const int *kept, const double *O,
+                                double *discarded_weight) {
+  API_BEGIN
+  if (!c || (direction != 1 && direction != -1)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  do_renormalize(c, direction, O ? kept : nullptr, O, discarded_weight, O ? nullptr : const_cast<int *>(kept));
+  API_END
+}
+
+extern "C" int dmrg_sweep(dmrg_ctx *c, int nsweeps, double tol, double *energies) {
+  API_BEGIN
+  if (!c || nsweeps < 0 || !(tol > 0.0)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  if (c->L < 3) throw Fail{DMRG_EINVAL, "sweeps need L >= 3"};
+  c->k = 0;
+  c->dir = 1;
+  c->plan.valid = false;
+  int idx = 0;
+  for (int sw = 0; sw < nsweeps; ++sw) {
+    for (int k = 0; k <= c->L - 3; ++k) {
+      double e;
+      int it;
+      bool conv;
+      davidson(c, tol, 200, &e, &it, conv);
+      if (energies) energies[idx] = e;
+      ++idx;
+      do_renormalize(c, +1, nullptr, nullptr, nullptr, nullptr);
+    }
+    for (int k = c->L - 2; k >= 1; --k) {
+      double e;
+      int it;
+      bool conv;
+      davidson(c, tol, 200, &e, &it, conv);
+      if (energies) energies[idx] = e;
+      ++idx;
+      do_renormalize(c, -1, nullptr, nullptr, nullptr, nullptr);
+    }
+  }
+  API_END
+}
+
+extern "C" int dmrg_block_op(dmrg_ctx *c, int side, int kind, int i, int j, double *out,
+                             long long *n) {
+  API_BEGIN
+  if (!c || (side != 0 && side != 1)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  DevBlock *b = side == 0 ? lblock(c) : rblock(c);
+  if (!b) throw Fail{DMRG_ESTATE, "block not built"};
+  int f, kk;
+  if (!b->lay.get(kind, i, j, f, kk)) throw Fail{DMRG_EINVAL, "no such stored operator"};
+  const Family &F = b->lay.fam[f];
+  int64_t tot = 0;
+  for (int a = 0; a < (int)b->lay.sec.size(); ++a)
+    if (F.bra[a] >= 0) tot += (int64_t)b->lay.sec[F.bra[a]].dim * b->lay.sec[a].dim;
+  if (n) *n = tot;
+  if (out) {
+    int64_t pos = 0;
+    for (int a = 0; a < (int)b->lay.sec.size(); ++a) {
+      if (F.bra[a] < 0) continue;
+      const int64_t sz = (int64_t)b->lay.sec[F.bra[a]].dim * b->lay.sec[a].dim;
+      CK(cudaMemcpyAsync(out + pos, b->ops.p + F.base + F.off[a] + kk * sz, sz * sizeof(double),
+                         cudaMemcpyDeviceToHost, c->stream));
+      pos += sz;
+    }
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  API_END
+}

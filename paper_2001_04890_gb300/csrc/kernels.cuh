@@ -1,0 +1,55 @@
+// Device kernels of the two-site QC-DMRG hot path (sm_103a) -- launch wrappers.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace dmrg {
+
+// Pre-summation task (Sec. 2.2.3, Eq. presum): out[t] = sum_u coef[t,u] src[u]
+// for the K_out temporaries of one family in one sector transition.
+struct LincombTask {
+  uint64_t out;        // element address of the output slab (K_out blocks)
+  uint64_t src;        // element address of the source slab (K_src blocks)
+  uint64_t coef;       // element address of the K_out x K_src coefficient matrix
+  int kout, ksrc;
+  int rows, cols;      // output block shape
+  int tr;              // source blocks read transposed (source block is cols x rows)
+  int tile0;           // first tile of this task in the launch grid
+};
+
+// Bounded-wait / error flag shared by the kernels of one context.
+struct DevStatus {
+  int error;
+};
+
+cudaError_t launch_chain_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
+                              uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+cudaError_t launch_lincomb_fp64(const LincombTask *t, int ntasks, int ntiles, cudaStream_t s);
+cudaError_t launch_diag_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
+                             uint64_t xb, uint64_t zb, double *diag, cudaStream_t s);
+
+// Davidson helpers (all FP64, deterministic two-stage reductions)
+cudaError_t launch_dots(const double *V, int k, int64_t n, const double *w, double *partial,
+                        double *out, cudaStream_t s);
+cudaError_t launch_combine(double *out, const double *V, const double *y, int k, int64_t n,
+                           double beta, cudaStream_t s);
+cudaError_t launch_axpy(double *y, const double *x, double a, int64_t n, cudaStream_t s);
+cudaError_t launch_scale(double *x, const double *a_dev, int invert_sqrt, int64_t n, cudaStream_t s);
+cudaError_t launch_precond(double *t, const double *r, const double *diag, const double *theta,
+                           int64_t n, cudaStream_t s);
+cudaError_t launch_residual(double *r, const double *hx, const double *x, const double *theta,
+                            int64_t n, cudaStream_t s);
+cudaError_t launch_sub_proj(double *w, const double *V, const double *c, int k, int64_t n,
+                            cudaStream_t s);
+cudaError_t launch_fill_guess(double *x, int64_t n, uint64_t seed, cudaStream_t s);
+cudaError_t launch_jacobi_eigh(const double *A, int n, int lda, double *evals, double *evecs,
+                               cudaStream_t s);
+cudaError_t launch_gather_columns(double *O, const double *evecs, int n, const int *cols,
+                                  int kept, cudaStream_t s);
+
+int dots_partial_blocks(int64_t n);
+
+}  // namespace dmrg

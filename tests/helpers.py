@@ -1,0 +1,67 @@
+"""Shared test helpers: grow identical random block bases on the GPU library and in the oracle.
+
+The random renormalization matrices are inputs (seeded, from workloads); both
+sides receive the same O, and the enlarged-sector layouts they each compute
+independently are checked to agree before use.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from oracle import blocks as ob
+from paper_2001_04890_gb300 import workloads
+
+
+def choose_kept(dims, M):
+    tot = int(sum(dims))
+    if tot <= M:
+        return [int(d) for d in dims]
+    kept = [min(int(d), max(1, int(d * M / tot))) if d > 0 else 0 for d in dims]
+    while sum(kept) > M:
+        i = int(np.argmax(kept))
+        kept[i] -= 1
+    return kept
+
+
+def random_O(layout_dims, M, rng):
+    kept = choose_kept(layout_dims, M)
+    blocks = [workloads.orthonormal_columns(int(n), int(m), rng) for n, m in zip(layout_dims, kept)]
+    flat = np.concatenate([b.ravel() for b in blocks]) if blocks else np.zeros(0)
+    return kept, blocks, flat
+
+
+def _check_layout(gpu_layout, oracle_layout):
+    dims = ob.enlarged_dims(oracle_layout)
+    ref = np.array([(E[0], E[1], dims[E]) for E in oracle_layout], dtype=np.int64).reshape(-1, 3)
+    assert np.array_equal(np.asarray(gpu_layout, dtype=np.int64).reshape(-1, 3), ref), (gpu_layout, ref)
+
+
+def build_random_position(ctx, h, v, k, M, seed=0, left_M=None, right_M=None):
+    """Grow left blocks 0..k-1 and right blocks k+2..L-1 with the same random O on both sides.
+
+    Leaves ctx at position k and returns the oracle blocks (lb, rb).
+    """
+    L = h.shape[0]
+    rng = np.random.default_rng(seed)
+    left_M = left_M or M
+    right_M = right_M or M
+    lb = ob.empty_block()
+    ctx.set_position(0, 1)
+    for s in range(k):
+        lay = ob.enlarged_left(lb)
+        _check_layout(ctx.enlarged_layout(+1), lay)
+        dims = [ob.enlarged_dims(lay)[E] for E in lay]
+        kept, blocks, flat = random_O(dims, left_M, rng)
+        ctx.renormalize(+1, flat, kept)
+        lb = ob.grow_left(lb, s, {E: b for E, b in zip(lay, blocks)})
+    rb = ob.empty_block()
+    ctx.set_position(L - 2, -1)
+    for s in range(L - 1, k + 1, -1):
+        lay = ob.enlarged_right(rb)
+        _check_layout(ctx.enlarged_layout(-1), lay)
+        dims = [ob.enlarged_dims(lay)[E] for E in lay]
+        kept, blocks, flat = random_O(dims, right_M, rng)
+        ctx.renormalize(-1, flat, kept)
+        rb = ob.grow_right(rb, s, {E: b for E, b in zip(lay, blocks)})
+    ctx.set_position(k, 1)
+    return lb, rb

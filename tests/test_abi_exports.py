@@ -1,0 +1,44 @@
+"""The C-ABI library loads on a machine without a GPU and exports every declared symbol."""
+import glob
+import os
+import re
+
+from paper_2001_04890_gb300 import binding
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_functions():
+    names = set()
+    for hdr in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(hdr).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        names |= set(re.findall(r"\b(dmrg_\w+)\s*\(", text))
+    return names
+
+
+def test_header_declares_the_hot_path_calls():
+    names = declared_functions()
+    for required in ("dmrg_init", "dmrg_hpsi", "dmrg_renormalize", "dmrg_davidson", "dmrg_sweep",
+                     "dmrg_free", "dmrg_last_error"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol():
+    lib = binding.lib()
+    missing = [n for n in sorted(declared_functions()) if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_calls_report_errors_without_a_gpu():
+    import numpy as np
+    L = 3
+    h = np.eye(L)
+    v = np.zeros((L,) * 4)
+    try:
+        binding.debug_pieces(h, v, 7, False, False)
+    except binding.DMRGError as e:
+        assert e.code == binding.DMRG_EINVAL
+        assert "bad arguments" in str(e)
+    else:
+        raise AssertionError("expected an error for an out-of-range position")
