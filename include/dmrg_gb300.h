@@ -120,12 +120,14 @@ int dmrg_hpsi(dmrg_ctx *ctx, const double *psi, double *sigma, int device_ptrs);
 int dmrg_hpsi_flops(dmrg_ctx *ctx, double *flops, long long *tasks);
 
 /*
- * dmrg_set_psi / dmrg_get_psi -- the context's current wave function (host
- * pointers, dmrg_psi_layout length).  dmrg_set_psi also makes it the
- * Davidson starting vector.
+ * dmrg_set_psi / dmrg_get_psi -- the context's current wave function in the
+ * dmrg_psi_layout layout.  device_ptr != 0: psi is a device pointer (copied on
+ * the context stream); 0: a host pointer (the call returns after the copy).
+ * dmrg_set_psi also makes it the Davidson starting vector.  dmrg_get_psi
+ * returns DMRG_ESTATE if no wave function is held at this position.
  */
-int dmrg_set_psi(dmrg_ctx *ctx, const double *psi);
-int dmrg_get_psi(dmrg_ctx *ctx, double *psi);
+int dmrg_set_psi(dmrg_ctx *ctx, const double *psi, int device_ptr);
+int dmrg_get_psi(dmrg_ctx *ctx, double *psi, int device_ptr);
 
 /*
  * dmrg_davidson -- lowest eigenpair of Eq. h_mat at the current position by
@@ -175,6 +177,17 @@ int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
  * query *n (element count).  DMRG_EINVAL if the block stores no such operator.
  */
 int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, long long *n);
+
+/*
+ * dmrg_stats -- counters since context creation or the last reset (host outputs,
+ * any may be NULL): total device time of the H.psi kernel launches (CUDA events
+ * recorded on the context stream around each launch), number of H.psi calls,
+ * their summed algorithmic FLOPs, kernels launched by this library in the
+ * process, Davidson iterations.  reset != 0 zeroes the counters afterwards.
+ * Synchronizes the context stream.
+ */
+int dmrg_stats(dmrg_ctx *ctx, int reset, double *hpsi_ms, long long *hpsi_calls, double *hpsi_flops,
+               long long *kernel_launches, long long *davidson_iters);
 
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */

@@ -49,12 +49,13 @@ def lib():
         "dmrg_enlarged_layout": (C.c_int, [vp, C.c_int, ip, ip]),
         "dmrg_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
         "dmrg_hpsi_flops": (C.c_int, [vp, dp, llp]),
-        "dmrg_set_psi": (C.c_int, [vp, dp]),
-        "dmrg_get_psi": (C.c_int, [vp, dp]),
+        "dmrg_set_psi": (C.c_int, [vp, vp, C.c_int]),
+        "dmrg_get_psi": (C.c_int, [vp, vp, C.c_int]),
         "dmrg_davidson": (C.c_int, [vp, C.c_double, C.c_int, dp, ip]),
         "dmrg_renormalize": (C.c_int, [vp, C.c_int, ip, dp, dp]),
         "dmrg_sweep": (C.c_int, [vp, C.c_int, C.c_double, dp]),
         "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
+        "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -179,13 +180,22 @@ class DMRG:
         return f.value, t.value
 
     def set_psi(self, psi):
-        psi = _f64(psi)
-        _check(lib().dmrg_set_psi(self.ctx, _dptr(psi)))
+        """Set the current wave function from a numpy array or a CUDA torch tensor (float64)."""
+        if isinstance(psi, np.ndarray):
+            psi = _f64(psi)
+            _check(lib().dmrg_set_psi(self.ctx, psi.ctypes.data, 0))
+        else:
+            _check(lib().dmrg_set_psi(self.ctx, psi.data_ptr(), 1 if psi.is_cuda else 0))
 
-    def get_psi(self):
-        _, dim = self.psi_layout()
-        out = np.zeros(dim)
-        _check(lib().dmrg_get_psi(self.ctx, _dptr(out)))
+    def get_psi(self, out=None):
+        """Copy the current wave function into out (numpy / torch, host or device) or a new numpy array."""
+        if out is None:
+            _, dim = self.psi_layout()
+            out = np.zeros(dim)
+        if isinstance(out, np.ndarray):
+            _check(lib().dmrg_get_psi(self.ctx, out.ctypes.data, 0))
+        else:
+            _check(lib().dmrg_get_psi(self.ctx, out.data_ptr(), 1 if out.is_cuda else 0))
         return out
 
     def davidson(self, tol=1e-9, max_iter=200, allow_noconv=False):
@@ -212,6 +222,13 @@ class DMRG:
         e = np.zeros(nsweeps * 2 * (self.L - 2))
         _check(lib().dmrg_sweep(self.ctx, nsweeps, tol, _dptr(e)))
         return e
+
+    def stats(self, reset=False):
+        ms, calls, fl, launches, dav = C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_longlong()
+        _check(lib().dmrg_stats(self.ctx, int(reset), C.byref(ms), C.byref(calls), C.byref(fl),
+                                C.byref(launches), C.byref(dav)))
+        return dict(hpsi_ms=ms.value, hpsi_calls=calls.value, hpsi_flops=fl.value,
+                    kernel_launches=launches.value, davidson_iters=dav.value)
 
     def block_op(self, side, kind, i=-1, j=-1):
         n = C.c_longlong()

@@ -375,6 +375,14 @@ struct dmrg_ctx {
   cusolverDnHandle_t solver = nullptr;
   dmrg::DBuf<double> sol_work;
   dmrg::DBuf<int> sol_info;
+  // statistics: CUDA events around every H.psi kernel launch on the context stream
+  std::vector<cudaEvent_t> ev;
+  size_t ev_used = 0;
+  double hpsi_ms_folded = 0.0;
+  long long hpsi_calls = 0;
+  double hpsi_flops_acc = 0.0;
+  long long dav_iters = 0;
+  long long launch_base = 0;
 };
 
 namespace dmrg {
@@ -511,11 +519,33 @@ static void build_hplan(dmrg_ctx *c) {
   P.valid = true;
 }
 
+static void fold_events(dmrg_ctx *c) {
+  if (c->ev_used == 0) return;
+  CK(cudaStreamSynchronize(c->stream));
+  for (size_t i = 0; i + 1 < c->ev_used; i += 2) {
+    float ms = 0.f;
+    CK(cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]));
+    c->hpsi_ms_folded += ms;
+  }
+  c->ev_used = 0;
+}
+
 static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma) {
   HPlan &P = c->plan;
   CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
+  if (c->ev_used + 2 > 4096) fold_events(c);
+  while (c->ev.size() < c->ev_used + 2) {
+    cudaEvent_t e;
+    CK(cudaEventCreate(&e));
+    c->ev.push_back(e);
+  }
+  CK(cudaEventRecord(c->ev[c->ev_used], c->stream));
   CK(launch_chain_fp64(P.ent.p, P.grp.p, P.ngroups, P.ntiles, 0, (uint64_t)(uintptr_t)psi, 0,
                        (uint64_t)(uintptr_t)sigma, c->stream));
+  CK(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
+  c->ev_used += 2;
+  c->hpsi_calls += 1;
+  c->hpsi_flops_acc += P.flops;
 }
 
 // ---------------------------------------------------------------- renormalization
@@ -1134,6 +1164,7 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
   normalize(c->psi.p);
   CK(cudaStreamSynchronize(s));
   c->psi_valid = true;
+  c->dav_iters += std::min(it, max_iter);
   if (energy) *energy = theta;
   if (iters) *iters = std::min(it, max_iter);
 }
@@ -1222,6 +1253,7 @@ extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double
   }
   c->k = 0;
   c->dir = 1;
+  c->launch_base = kernel_launch_count();
   *out = c.release();
   API_END
 }
@@ -1230,6 +1262,7 @@ extern "C" int dmrg_free(dmrg_ctx *c) {
   if (!c) return DMRG_OK;
   if (c->stream) cudaStreamSynchronize(c->stream);
   if (c->solver) cusolverDnDestroy(c->solver);
+  for (auto e : c->ev) cudaEventDestroy(e);
   delete c;
   return DMRG_OK;
 }
@@ -1331,25 +1364,27 @@ extern "C" int dmrg_hpsi_flops(dmrg_ctx *c, double *flops, long long *tasks) {
   API_END
 }
 
-extern "C" int dmrg_set_psi(dmrg_ctx *c, const double *psi) {
+extern "C" int dmrg_set_psi(dmrg_ctx *c, const double *psi, int device_ptr) {
   API_BEGIN
   if (!c || !psi) throw Fail{DMRG_EINVAL, "NULL argument"};
   build_hplan(c);
   const int64_t n = c->plan.psi.dim;
   c->psi.alloc(n);
-  CK(cudaMemcpyAsync(c->psi.p, psi, n * sizeof(double), cudaMemcpyHostToDevice, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(c->psi.p, psi, n * sizeof(double),
+                     device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream));
+  if (!device_ptr) CK(cudaStreamSynchronize(c->stream));
   c->psi_valid = true;
   API_END
 }
 
-extern "C" int dmrg_get_psi(dmrg_ctx *c, double *psi) {
+extern "C" int dmrg_get_psi(dmrg_ctx *c, double *psi, int device_ptr) {
   API_BEGIN
   if (!c || !psi) throw Fail{DMRG_EINVAL, "NULL argument"};
   if (!c->psi_valid) throw Fail{DMRG_ESTATE, "no wave function at this position"};
   build_hplan(c);
-  CK(cudaMemcpyAsync(psi, c->psi.p, c->plan.psi.dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
-  CK(cudaStreamSynchronize(c->stream));
+  CK(cudaMemcpyAsync(psi, c->psi.p, c->plan.psi.dim * sizeof(double),
+                     device_ptr ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, c->stream));
+  if (!device_ptr) CK(cudaStreamSynchronize(c->stream));
   API_END
 }
 
@@ -1424,6 +1459,26 @@ extern "C" int dmrg_block_op(dmrg_ctx *c, int side, int kind, int i, int j, doub
       pos += sz;
     }
     CK(cudaStreamSynchronize(c->stream));
+  }
+  API_END
+}
+
+extern "C" int dmrg_stats(dmrg_ctx *c, int reset, double *hpsi_ms, long long *hpsi_calls,
+                          double *hpsi_flops, long long *kernel_launches, long long *davidson_iters) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
+  fold_events(c);
+  if (hpsi_ms) *hpsi_ms = c->hpsi_ms_folded;
+  if (hpsi_calls) *hpsi_calls = c->hpsi_calls;
+  if (hpsi_flops) *hpsi_flops = c->hpsi_flops_acc;
+  if (kernel_launches) *kernel_launches = kernel_launch_count() - c->launch_base;
+  if (davidson_iters) *davidson_iters = c->dav_iters;
+  if (reset) {
+    c->hpsi_ms_folded = 0.0;
+    c->hpsi_calls = 0;
+    c->hpsi_flops_acc = 0.0;
+    c->dav_iters = 0;
+    c->launch_base = kernel_launch_count();
   }
   API_END
 }

@@ -13,11 +13,17 @@
 // matrix, and a column gather that builds O from eigenvectors.
 #include <cuda_runtime.h>
 
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace dmrg {
 
 #define IDN (~0ull)
+
+static std::atomic<long long> g_launches{0};
+long long kernel_launch_count() { return g_launches.load(); }
+#define COUNT(n) g_launches.fetch_add(n)
 
 __device__ __forceinline__ const double *dptr(uint64_t base, uint64_t off) {
   return reinterpret_cast<const double *>(base + off * 8ull);
@@ -128,6 +134,7 @@ __global__ void __launch_bounds__(256) chain_fp64_kernel(const ChainEntry *__res
 cudaError_t launch_chain_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
                               uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
   if (ngroups <= 0 || ntiles <= 0) return cudaSuccess;
+  COUNT(1);
   chain_fp64_kernel<<<ntiles, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
   return cudaGetLastError();
 }
@@ -188,6 +195,7 @@ __global__ void __launch_bounds__(256) lincomb_fp64_kernel(const LincombTask *__
 
 cudaError_t launch_lincomb_fp64(const LincombTask *t, int ntasks, int ntiles, cudaStream_t s) {
   if (ntasks <= 0 || ntiles <= 0) return cudaSuccess;
+  COUNT(1);
   lincomb_fp64_kernel<<<ntiles, 256, 0, s>>>(t, ntasks);
   return cudaGetLastError();
 }
@@ -215,6 +223,7 @@ __global__ void diag_fp64_kernel(const ChainEntry *__restrict__ E, const ChainGr
 cudaError_t launch_diag_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
                              uint64_t zb, double *diag, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
+  COUNT(1);
   diag_fp64_kernel<<<ngroups, 256, 0, s>>>(e, g, xb, zb, diag);
   return cudaGetLastError();
 }
@@ -275,7 +284,9 @@ cudaError_t launch_dots(const double *V, int k, int64_t n, const double *w, doub
                         double *out, cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
   const int nb = dots_partial_blocks(n);
+  COUNT(1);
   dots_stage1<<<nb, 256, 0, s>>>(V, k, n, w, partial);
+  COUNT(1);
   dots_stage2<<<k, 256, 0, s>>>(partial, nb, k, out);
   return cudaGetLastError();
 }
@@ -298,6 +309,7 @@ static int grid_for(int64_t n) {
 
 cudaError_t launch_combine(double *out, const double *V, const double *y, int k, int64_t n,
                            double beta, cudaStream_t s) {
+  COUNT(1);
   combine_kernel<<<grid_for(n), 256, 0, s>>>(out, V, y, k, n, beta);
   return cudaGetLastError();
 }
@@ -314,6 +326,7 @@ __global__ void sub_proj_kernel(double *w, const double *__restrict__ V, const d
 cudaError_t launch_sub_proj(double *w, const double *V, const double *c, int k, int64_t n,
                             cudaStream_t s) {
   if (k <= 0) return cudaSuccess;
+  COUNT(1);
   sub_proj_kernel<<<grid_for(n), 256, 0, s>>>(w, V, c, k, n);
   return cudaGetLastError();
 }
@@ -324,6 +337,7 @@ __global__ void axpy_kernel(double *y, const double *x, double a, int64_t n) {
 }
 
 cudaError_t launch_axpy(double *y, const double *x, double a, int64_t n, cudaStream_t s) {
+  COUNT(1);
   axpy_kernel<<<grid_for(n), 256, 0, s>>>(y, x, a, n);
   return cudaGetLastError();
 }
@@ -335,6 +349,7 @@ __global__ void scale_kernel(double *x, const double *a_dev, int invert_sqrt, in
 }
 
 cudaError_t launch_scale(double *x, const double *a_dev, int invert_sqrt, int64_t n, cudaStream_t s) {
+  COUNT(1);
   scale_kernel<<<grid_for(n), 256, 0, s>>>(x, a_dev, invert_sqrt, n);
   return cudaGetLastError();
 }
@@ -351,6 +366,7 @@ __global__ void precond_kernel(double *t, const double *r, const double *diag, c
 
 cudaError_t launch_precond(double *t, const double *r, const double *diag, const double *theta,
                            int64_t n, cudaStream_t s) {
+  COUNT(1);
   precond_kernel<<<grid_for(n), 256, 0, s>>>(t, r, diag, theta, n);
   return cudaGetLastError();
 }
@@ -364,6 +380,7 @@ __global__ void residual_kernel(double *r, const double *hx, const double *x, co
 
 cudaError_t launch_residual(double *r, const double *hx, const double *x, const double *theta,
                             int64_t n, cudaStream_t s) {
+  COUNT(1);
   residual_kernel<<<grid_for(n), 256, 0, s>>>(r, hx, x, theta, n);
   return cudaGetLastError();
 }
@@ -384,6 +401,7 @@ __global__ void fill_guess_kernel(double *x, int64_t n, uint64_t seed) {
 }
 
 cudaError_t launch_fill_guess(double *x, int64_t n, uint64_t seed, cudaStream_t s) {
+  COUNT(1);
   fill_guess_kernel<<<grid_for(n), 256, 0, s>>>(x, n, seed);
   return cudaGetLastError();
 }
@@ -469,6 +487,7 @@ __global__ void jacobi_eigh_kernel(const double *A, int n, int lda, double *eval
 cudaError_t launch_jacobi_eigh(const double *A, int n, int lda, double *evals, double *evecs,
                                cudaStream_t s) {
   if (n > 64 || n < 1) return cudaErrorInvalidValue;
+  COUNT(1);
   jacobi_eigh_kernel<<<1, 64, 0, s>>>(A, n, lda, evals, evecs);
   return cudaGetLastError();
 }
@@ -485,6 +504,7 @@ __global__ void gather_columns_kernel(double *O, const double *evecs, int n, con
 cudaError_t launch_gather_columns(double *O, const double *evecs, int n, const int *cols, int kept,
                                   cudaStream_t s) {
   if (kept <= 0 || n <= 0) return cudaSuccess;
+  COUNT(1);
   gather_columns_kernel<<<grid_for((int64_t)n * kept), 256, 0, s>>>(O, evecs, n, cols, kept);
   return cudaGetLastError();
 }

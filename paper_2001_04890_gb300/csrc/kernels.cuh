@@ -52,4 +52,7 @@ cudaError_t launch_gather_columns(double *O, const double *evecs, int n, const i
 
 int dots_partial_blocks(int64_t n);
 
+// number of kernels this library has launched in the process
+long long kernel_launch_count();
+
 }  // namespace dmrg

@@ -122,3 +122,36 @@ def sector_dims_profile(k: int, n_up_tot: int, n_dn_tot: int, L: int, M: int,
             remaining -= int(base.sum())
         active = alloc < cap
     return {key: int(m) for key, m in zip(keys, alloc) if m > 0}
+
+
+def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: int = 0):
+    """Grow the left blocks 0..k-1 and right blocks k+2..L-1 of a context with seeded random O.
+
+    Each renormalization keeps, per enlarged sector, the number of states given
+    by sector_dims_profile (normalised to M) and draws a random orthonormal O.
+    Returns the list of (direction, kept, O_flat) applied, in order, so the same
+    bases can be replayed elsewhere.  Leaves ctx at position k.
+    """
+    rng = np.random.default_rng(seed)
+    applied = []
+    ctx.set_position(0, 1)
+    for s in range(k):
+        lay = ctx.enlarged_layout(+1)
+        caps = {(int(a), int(b)): int(d) for a, b, d in lay}
+        prof = sector_dims_profile(s + 1, n_up, n_dn, L, M, caps)
+        kept = [prof.get((int(a), int(b)), 0) for a, b, _ in lay]
+        O = np.concatenate([orthonormal_columns(int(d), m, rng).ravel() for (_, _, d), m in zip(lay, kept)])
+        ctx.renormalize(+1, O, kept)
+        applied.append((+1, kept, O))
+    ctx.set_position(L - 2, -1)
+    for s in range(L - 1, k + 1, -1):
+        n_sites = L - s
+        lay = ctx.enlarged_layout(-1)
+        caps = {(int(a), int(b)): int(d) for a, b, d in lay}
+        prof = sector_dims_profile(n_sites, n_up, n_dn, L, M, caps)
+        kept = [prof.get((int(a), int(b)), 0) for a, b, _ in lay]
+        O = np.concatenate([orthonormal_columns(int(d), m, rng).ravel() for (_, _, d), m in zip(lay, kept)])
+        ctx.renormalize(-1, O, kept)
+        applied.append((-1, kept, O))
+    ctx.set_position(k, 1)
+    return applied
