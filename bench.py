@@ -82,6 +82,16 @@ def _peaks():
         return {}
 
 
+def _flops_fn(wl):
+    """Algorithmic H.psi FLOPs for given block sector tables (host-only planner of the library)."""
+    from paper_2001_04890_gb300 import binding, workloads
+    h, v = workloads.integrals(wl["L"], seed=0)
+
+    def f(sec_l, sec_r, k):
+        return binding.plan_hpsi_flops(h, v, wl["N"], wl["two_sz"], k, sec_l, sec_r)[0]
+    return f
+
+
 def run_gpu(args, wl, rank, world):
     import torch
     from paper_2001_04890_gb300 import binding, workloads
@@ -178,10 +188,10 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
-        from oracle import baseline
         if rank != 0:
             return 0
-        line = baseline.reference_line(wl, args.steps, args.warmup, METRIC)
+        from oracle import baseline
+        line = baseline.reference_line(wl, args.steps, args.warmup, METRIC, _flops_fn(wl))
         print(json.dumps(line))
         return 0
     if world > 1:
@@ -237,7 +247,7 @@ def main():
     if rank == 0 and not args.no_cpu_baseline:
         try:
             from oracle import baseline
-            line["cpu_baseline"] = baseline.cpu_baseline(wl)
+            line["cpu_baseline"] = baseline.cpu_baseline(wl, _flops_fn(wl))
         except Exception as exc:  # reported, never silently replaced
             line["cpu_baseline"] = {"error": str(exc)}
     if rank == 0:

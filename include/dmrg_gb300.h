@@ -189,6 +189,15 @@ int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, 
 int dmrg_stats(dmrg_ctx *ctx, int reset, double *hpsi_ms, long long *hpsi_calls, double *hpsi_flops,
                long long *kernel_launches, long long *davidson_iters);
 
+/*
+ * dmrg_plan_hpsi_flops -- host only (no GPU): algorithmic FLOPs and task count
+ * of one H.psi at position k for given block sector tables (per sector
+ * n_up, n_dn, dim; nl left and nr right sectors, sorted), i.e. what
+ * dmrg_hpsi_flops reports for blocks with those sectors.
+ */
+int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                         const int *sec_l, int nr, const int *sec_r, double *flops, long long *tasks);
+
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */
 int dmrg_debug_pieces(int L, const double *h, const double *v, int k, int l_empty, int r_empty,

@@ -56,6 +56,8 @@ def lib():
         "dmrg_sweep": (C.c_int, [vp, C.c_int, C.c_double, dp]),
         "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
         "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp]),
+        "dmrg_plan_hpsi_flops": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip,
+                                           C.c_int, ip, dp, llp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -95,6 +97,17 @@ def _dump(fn, *args):
     buf = C.create_string_buffer(need.value)
     _check(fn(*args, buf, need.value, C.byref(need)))
     return buf.value.decode()
+
+
+def plan_hpsi_flops(h, v, N, two_sz, k, sec_l, sec_r):
+    """Host-only FLOP count of one H.psi for blocks with the given (n_up, n_dn, dim) sector tables."""
+    h, v = _f64(h), _f64(v)
+    sl = np.ascontiguousarray(np.asarray(sec_l).reshape(-1, 3), dtype=np.int32)
+    sr = np.ascontiguousarray(np.asarray(sec_r).reshape(-1, 3), dtype=np.int32)
+    f, t = C.c_double(), C.c_longlong()
+    _check(lib().dmrg_plan_hpsi_flops(h.shape[0], N, two_sz, _dptr(h), _dptr(v), k, len(sl), _iptr(sl),
+                                      len(sr), _iptr(sr), C.byref(f), C.byref(t)))
+    return f.value, t.value
 
 
 def debug_pieces(h, v, k, l_empty, r_empty, compress=True):

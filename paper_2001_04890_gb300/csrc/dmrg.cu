@@ -406,52 +406,36 @@ static std::unique_ptr<DevBlock> empty_block(int side, int L) {
   return b;
 }
 
-static void build_hplan(dmrg_ctx *c) {
-  HPlan &P = c->plan;
-  require_blocks(c);
-  DevBlock *lb = lblock(c), *rb = rblock(c);
-  if (P.valid && P.k == c->k && P.lb == lb && P.rb == rb) return;
-  P.valid = false;
-  P.k = c->k;
-  P.lb = lb;
-  P.rb = rb;
-  P.psi = psi_layout(lb->lay, rb->lay, c->nu, c->nd);
-  const Psi &Y = P.psi;
-  auto pieces = compress_pieces(hamiltonian_pieces(c->I, c->k, lb->lay.empty(), rb->lay.empty()));
-  P.temps.set = TempSet();
-  struct RP {
-    Ref l, r;
-    const Piece *p;
-  };
-  std::vector<RP> rps;
+struct RPiece {
+  Ref l, r;
+  Piece p;
+};
+
+// Resolve the (compressed) pieces of H at position k onto the two blocks;
+// pieces on operators that vanish there are dropped.
+static std::vector<RPiece> resolve_pieces(const Integrals &I, int k, const BlockLayout &L,
+                                          const BlockLayout &R, TempSet &temps) {
+  auto pieces = compress_pieces(hamiltonian_pieces(I, k, L.empty(), R.empty()));
+  std::vector<RPiece> out;
   for (auto &p : pieces) {
     bool zl, zr;
-    Ref l = resolve(p.l, 0, lb->lay, P.temps.set, zl);
+    Ref l = resolve(p.l, 0, L, temps, zl);
     if (zl) continue;
-    Ref r = resolve(p.r, 1, rb->lay, P.temps.set, zr);
+    Ref r = resolve(p.r, 1, R, temps, zr);
     if (zr) continue;
-    rps.push_back({l, r, &p});
+    out.push_back({l, r, p});
   }
-  const BlockLayout *lay[2] = {&lb->lay, &rb->lay};
-  const double *stored[2] = {lb->arena(), rb->arena()};
-  build_temps(P.temps, lay, stored, c->stream);
-  Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
-           {P.temps.arena[0].p, P.temps.arena[1].p}};
+  return out;
+}
 
-  std::vector<ChainGroup> protos(Y.blk.size());
-  for (size_t i = 0; i < Y.blk.size(); ++i) {
-    ChainGroup g{};
-    g.d = (uint64_t)Y.blk[i].off;
-    g.drs = Y.blk[i].md;
-    g.dcs = 1;
-    g.m = Y.blk[i].ma;
-    g.q = Y.blk[i].md;
-    protos[i] = g;
-  }
-  ChainList CL;
-  double flops = 0.0;
+// Expand pieces over the psi blocks of Eq. wf_sec into the H.psi task list
+// (Sec. 2.2.1): one entry per (piece, s -> s'), plus the transposed entry of
+// Hermitian-conjugate pieces.  Also counts the algorithmic FLOPs.
+static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const Psi &Y,
+                        const BlockLayout &lb, ChainList &CL, double &flops) {
+  flops = 0.0;
   for (auto &rp : rps) {
-    const Piece &p = *rp.p;
+    const Piece &p = rp.p;
     const int psl = mat_parity(p.sl), psr = mat_parity(p.sr);
     for (size_t si = 0; si < Y.blk.size(); ++si) {
       const PsiBlock &s = Y.blk[si];
@@ -467,7 +451,7 @@ static void build_hplan(dmrg_ctx *c) {
       const int so = Y.find(a2, b2, c2, d2);
       if (so < 0) continue;
       const PsiBlock &t = Y.blk[so];
-      const int na = npart(lb->lay.sec[s.a]), nb = nsite(s.b), nc = nsite(s.c);
+      const int na = npart(lb.sec[s.a]), nb = nsite(s.b), nc = nsite(s.c);
       const int sgn_exp = rp.r.par * (na + nb + nc) + psr * (na + nb) + psl * na;
       const double f = p.coef * vb * vc * ((sgn_exp & 1) ? -1.0 : 1.0);
       const bool xid = rp.l.arena < 0, zid = rp.r.arena < 0;
@@ -505,7 +489,44 @@ static void build_hplan(dmrg_ctx *c) {
       }
     }
   }
-  CL.finish(protos);
+}
+
+static std::vector<ChainGroup> psi_protos(const Psi &Y) {
+  std::vector<ChainGroup> protos(Y.blk.size());
+  for (size_t i = 0; i < Y.blk.size(); ++i) {
+    ChainGroup g{};
+    g.d = (uint64_t)Y.blk[i].off;
+    g.drs = Y.blk[i].md;
+    g.dcs = 1;
+    g.m = Y.blk[i].ma;
+    g.q = Y.blk[i].md;
+    protos[i] = g;
+  }
+  return protos;
+}
+
+static void build_hplan(dmrg_ctx *c) {
+  HPlan &P = c->plan;
+  require_blocks(c);
+  DevBlock *lb = lblock(c), *rb = rblock(c);
+  if (P.valid && P.k == c->k && P.lb == lb && P.rb == rb) return;
+  P.valid = false;
+  P.k = c->k;
+  P.lb = lb;
+  P.rb = rb;
+  P.psi = psi_layout(lb->lay, rb->lay, c->nu, c->nd);
+  const Psi &Y = P.psi;
+  P.temps.set = TempSet();
+  auto rps = resolve_pieces(c->I, c->k, lb->lay, rb->lay, P.temps.set);
+  const BlockLayout *lay[2] = {&lb->lay, &rb->lay};
+  const double *stored[2] = {lb->arena(), rb->arena()};
+  build_temps(P.temps, lay, stored, c->stream);
+  Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
+           {P.temps.arena[0].p, P.temps.arena[1].p}};
+  ChainList CL;
+  double flops = 0.0;
+  expand_hpsi(rps, A, Y, lb->lay, CL, flops);
+  CL.finish(psi_protos(Y));
   P.ent.upload(CL.flat, c->stream);
   P.grp.upload(CL.grp, c->stream);
   P.ngroups = (int)CL.grp.size();
@@ -1480,5 +1501,41 @@ extern "C" int dmrg_stats(dmrg_ctx *c, int reset, double *hpsi_ms, long long *hp
     c->dav_iters = 0;
     c->launch_base = kernel_launch_count();
   }
+  API_END
+}
+
+extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, const double *v, int k,
+                                    int nl, const int *sec_l, int nr, const int *sec_r, double *flops,
+                                    long long *tasks) {
+  API_BEGIN
+  if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r)
+    throw Fail{DMRG_EINVAL, "dmrg_plan_hpsi_flops: bad arguments"};
+  if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
+  Integrals I;
+  I.L = L;
+  I.h.assign(h, h + (size_t)L * L);
+  I.v.assign(v, v + (size_t)L * L * L * L);
+  auto sectors = [](int n, const int *t) {
+    std::vector<Sector> out;
+    for (int i = 0; i < n; ++i) out.push_back({t[3 * i], t[3 * i + 1], t[3 * i + 2]});
+    return out;
+  };
+  std::vector<int> ls, rs;
+  for (int s = 0; s < k; ++s) ls.push_back(s);
+  for (int s = k + 2; s < L; ++s) rs.push_back(s);
+  BlockLayout lb, rb;
+  build_layout(lb, 0, L, ls, sectors(nl, sec_l));
+  build_layout(rb, 1, L, rs, sectors(nr, sec_r));
+  Psi Y = psi_layout(lb, rb, (N + two_sz) / 2, (N - two_sz) / 2);
+  TempSet temps;
+  auto rps = resolve_pieces(I, k, lb, rb, temps);
+  const BlockLayout *lay[2] = {&lb, &rb};
+  temps.layout(lay);
+  Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}};
+  ChainList CL;
+  double f = 0.0;
+  expand_hpsi(rps, A, Y, lb, CL, f);
+  if (flops) *flops = f;
+  if (tasks) *tasks = (long long)CL.ent.size();
   API_END
 }

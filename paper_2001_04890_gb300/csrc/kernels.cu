@@ -406,67 +406,59 @@ cudaError_t launch_fill_guess(double *x, int64_t n, uint64_t seed, cudaStream_t 
   return cudaGetLastError();
 }
 
-// Cyclic Jacobi eigensolver for a small symmetric matrix (n <= 64), one CTA.
+// Cyclic Jacobi eigensolver for a small symmetric matrix (n <= 32) on one warp:
+// lane i owns row i; every lane evaluates the same rotation (Rutishauser's
+// stable tangent formula), so a rotation costs two warp barriers only.
 // Eigenvalues ascending; eigenvectors as columns of evecs (row-major n x n).
 __global__ void jacobi_eigh_kernel(const double *A, int n, int lda, double *evals, double *evecs) {
-  __shared__ double a[64][65];
-  __shared__ double v[64][65];
-  __shared__ double cs[2];
-  __shared__ int done;
-  const int tid = threadIdx.x;
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx % n;
-    a[i][j] = A[(int64_t)i * lda + j];
-    v[i][j] = (i == j) ? 1.0 : 0.0;
-  }
-  __syncthreads();
-  for (int sweep = 0; sweep < 60; ++sweep) {
-    if (tid == 0) {
-      double off = 0.0, dg = 0.0;
-      for (int i = 0; i < n; ++i) {
-        dg += a[i][i] * a[i][i];
-        for (int j = i + 1; j < n; ++j) off += a[i][j] * a[i][j];
-      }
-      done = (off <= 1e-32 * (dg + 1e-300)) ? 1 : 0;
+  __shared__ double a[32][33];
+  __shared__ double v[32][33];
+  const int lane = threadIdx.x;
+  for (int j = 0; j < n; ++j) {
+    if (lane < n) {
+      a[lane][j] = A[(int64_t)lane * lda + j];
+      v[lane][j] = (lane == j) ? 1.0 : 0.0;
     }
-    __syncthreads();
-    if (done) break;
+  }
+  __syncwarp();
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0.0, dg = 0.0;
+    if (lane < n) {
+      dg = a[lane][lane] * a[lane][lane];
+      for (int j = lane + 1; j < n; ++j) off += a[lane][j] * a[lane][j];
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(0xffffffffu, off, o);
+      dg += __shfl_xor_sync(0xffffffffu, dg, o);
+    }
+    if (off <= 1e-32 * (dg + 1e-300)) break;
     for (int p = 0; p < n; ++p)
       for (int q = p + 1; q < n; ++q) {
-        if (tid == 0) {
-          const double apq = a[p][q];
-          if (fabs(apq) < 1e-300) { cs[0] = 1.0; cs[1] = 0.0; }
-          else {
-            const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
-            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-            const double c = 1.0 / sqrt(t * t + 1.0);
-            cs[0] = c;
-            cs[1] = t * c;
-          }
+        const double apq = a[p][q];
+        if (fabs(apq) < 1e-300) continue;
+        const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(t * t + 1.0);
+        const double s = t * c;
+        __syncwarp();
+        if (lane < n) {
+          const double akp = a[lane][p], akq = a[lane][q];
+          a[lane][p] = c * akp - s * akq;
+          a[lane][q] = s * akp + c * akq;
+          const double vkp = v[lane][p], vkq = v[lane][q];
+          v[lane][p] = c * vkp - s * vkq;
+          v[lane][q] = s * vkp + c * vkq;
         }
-        __syncthreads();
-        const double c = cs[0], s = cs[1];
-        if (s != 0.0) {
-          if (tid < n) {
-            const double akp = a[tid][p], akq = a[tid][q];
-            a[tid][p] = c * akp - s * akq;
-            a[tid][q] = s * akp + c * akq;
-            const double vkp = v[tid][p], vkq = v[tid][q];
-            v[tid][p] = c * vkp - s * vkq;
-            v[tid][q] = s * vkp + c * vkq;
-          }
-          __syncthreads();
-          if (tid < n) {
-            const double apk = a[p][tid], aqk = a[q][tid];
-            a[p][tid] = c * apk - s * aqk;
-            a[q][tid] = s * apk + c * aqk;
-          }
+        __syncwarp();
+        if (lane < n) {
+          const double apk = a[p][lane], aqk = a[q][lane];
+          a[p][lane] = c * apk - s * aqk;
+          a[q][lane] = s * apk + c * aqk;
         }
-        __syncthreads();
+        __syncwarp();
       }
   }
-  if (tid == 0) {
-    // selection sort ascending, columns of v follow
+  if (lane == 0) {
     for (int i = 0; i < n; ++i) {
       int m = i;
       for (int j = i + 1; j < n; ++j) if (a[j][j] < a[m][m]) m = j;
@@ -476,19 +468,18 @@ __global__ void jacobi_eigh_kernel(const double *A, int n, int lda, double *eval
       }
     }
   }
-  __syncthreads();
-  for (int idx = tid; idx < n * n; idx += blockDim.x) {
-    const int i = idx / n, j = idx % n;
-    evecs[(int64_t)i * n + j] = v[i][j];
+  __syncwarp();
+  if (lane < n) {
+    for (int j = 0; j < n; ++j) evecs[(int64_t)lane * n + j] = v[lane][j];
+    evals[lane] = a[lane][lane];
   }
-  if (tid < n) evals[tid] = a[tid][tid];
 }
 
 cudaError_t launch_jacobi_eigh(const double *A, int n, int lda, double *evals, double *evecs,
                                cudaStream_t s) {
-  if (n > 64 || n < 1) return cudaErrorInvalidValue;
+  if (n > 32 || n < 1) return cudaErrorInvalidValue;
   COUNT(1);
-  jacobi_eigh_kernel<<<1, 64, 0, s>>>(A, n, lda, evals, evecs);
+  jacobi_eigh_kernel<<<1, 32, 0, s>>>(A, n, lda, evals, evecs);
   return cudaGetLastError();
 }
 
