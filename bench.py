@@ -92,19 +92,26 @@ def _flops_fn(wl):
     return f
 
 
-def run_gpu(args, wl, rank, world):
+def _setup(wl, precision, stream, dev):
     import torch
     from paper_2001_04890_gb300 import binding, workloads
-
-    dev = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(dev)
-    stream = torch.cuda.Stream()
     L, N, two_sz, M = wl["L"], wl["N"], wl["two_sz"], wl["M"]
     nu, nd = (N + two_sz) // 2, (N - two_sz) // 2
     k = (L - 2) // 2
     h, v = workloads.integrals(L, seed=0)
-    ctx = binding.DMRG(h, v, N, two_sz, M, wl["precision"], stream=stream.cuda_stream)
+    ctx = binding.DMRG(h, v, N, two_sz, M, precision, stream=stream.cuda_stream)
     workloads.grow_middle_bond(ctx, L, nu, nd, M, k, seed=0)
+    return ctx, k
+
+
+def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
+    import torch
+    from paper_2001_04890_gb300 import workloads
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    ctx, k = _setup(wl, precision, stream, dev)
     blocks, dim = ctx.psi_layout()
     flops_per_hpsi, ntasks = ctx.hpsi_flops()
     psi0_host = workloads.gaussian(dim, seed=1)
@@ -117,7 +124,7 @@ def run_gpu(args, wl, rank, world):
     def step():
         ctx.set_position(k, 1)
         ctx.set_psi(psi0_dev)
-        e, it = ctx.davidson(tol=wl["tol"], max_iter=300, allow_noconv=True)
+        e, it = ctx.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
         ctx.renormalize(+1)
         return e, it
 
@@ -128,11 +135,9 @@ def run_gpu(args, wl, rank, world):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     ctx.stats(reset=True)
-    sampler, clk_path = _clock_sampler()
+    sampler, clk_path = _clock_sampler() if sample_clocks else (None, None)
     time.sleep(0.3)
-    ev = []
-    iters = []
-    energy = None
+    ev, iters, energy = [], [], None
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)  # L2 flush between timed steps (256 MB > 129 MB L2)
@@ -145,34 +150,65 @@ def run_gpu(args, wl, rank, world):
     stream.synchronize()
     st = ctx.stats(reset=True)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
-    # end-to-end through the C ABI with HOST buffers: H2D of the start vector and
-    # D2H of the result (energy + predicted wave function) inside the timed region
-    pin_in = torch.from_numpy(psi0_host).pin_memory()
-    e2e_ms = 0.0
-    d2h_bytes = 0
-    for _ in range(args.steps):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        ctx.set_position(k, 1)
-        ctx.set_psi(pin_in.numpy())
-        ctx.davidson(tol=wl["tol"], max_iter=300, allow_noconv=True)
-        ctx.renormalize(+1)
-        out = ctx.get_psi()
-        e2e_ms += (time.perf_counter() - t0) * 1e3
-        d2h_bytes = out.nbytes + 8
+    e2e_ms, d2h_bytes = None, 0
+    if e2e:
+        # end-to-end through the C ABI with HOST buffers: H2D of the start vector and
+        # D2H of the result (energy + predicted wave function) inside the timed region
+        pin_in = torch.from_numpy(psi0_host).pin_memory()
+        e2e_ms = 0.0
+        for _ in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            ctx.set_position(k, 1)
+            ctx.set_psi(pin_in.numpy())
+            ctx.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
+            ctx.renormalize(+1)
+            out = ctx.get_psi()
+            e2e_ms += (time.perf_counter() - t0) * 1e3
+            d2h_bytes = out.nbytes + 8
+    clocks = None
     if sampler is not None:
         time.sleep(0.2)
         sampler.terminate()
         sampler.wait()
-    clocks = _clock_summary(clk_path, dev)
+        clocks = _clock_summary(clk_path, dev)
+    # converged middle-bond state for the mixed-vs-FP64 comparison (untimed)
+    ctx.set_position(k, 1)
+    ctx.set_psi(psi0_dev)
+    e_mid, _ = ctx.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
+    psi_mid = ctx.get_psi()
     step_ms_max = step_ms
     if world > 1:
         t = torch.tensor([step_ms], device=f"cuda:{dev}")
         torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
         step_ms_max = float(t.item())
-    return dict(ctx=ctx, dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st,
+    ctx.close()
+    return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st,
                 step_ms=step_ms_max, iters=iters, energy=energy, e2e_ms=e2e_ms,
-                h2d=psi0_host.nbytes, d2h=d2h_bytes, clocks=clocks, k=k)
+                h2d=psi0_host.nbytes, d2h=d2h_bytes, clocks=clocks, k=k, e_mid=e_mid, psi_mid=psi_mid)
+
+
+def profile_hpsi(wl, precision, ncalls):
+    """Setup, then ncalls H.psi launches inside an NVTX range "hpsi" (for ncu --nvtx)."""
+    import torch
+    from paper_2001_04890_gb300 import workloads
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    ctx, k = _setup(wl, precision, stream, 0)
+    _, dim = ctx.psi_layout()
+    psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
+    ctx.hpsi(psi)  # builds the task list and temporaries outside the range
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("hpsi")
+    for _ in range(ncalls):
+        ctx.hpsi(psi)
+    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_pop()
+    st = ctx.stats()
+    print(json.dumps({"profile": wl["name"], "precision": precision, "hpsi_calls": ncalls,
+                      "hpsi_ms_avg": st["hpsi_ms"] / max(st["hpsi_calls"], 1),
+                      "gflop_per_hpsi": ctx.hpsi_flops()[0] / 1e9}))
+    ctx.close()
 
 
 def main():
@@ -183,6 +219,10 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-matvec comparison run")
+    ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
+                    help="setup, then N H.psi calls in an NVTX range 'hpsi' (for ncu); no JSON line")
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
@@ -194,10 +234,14 @@ def main():
         line = baseline.reference_line(wl, args.steps, args.warmup, METRIC, _flops_fn(wl))
         print(json.dumps(line))
         return 0
+    prec = {"fp64": 0, "fp32": 1}[args.precision]
+    if args.profile_hpsi:
+        profile_hpsi(wl, prec, args.profile_hpsi)
+        return 0
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    r = run_gpu(args, wl, rank, world)
+    r = run_gpu(args, wl, rank, world, prec)
     st = r["stats"]
     K = args.steps
     hpsi_flops = st["hpsi_flops"]
@@ -244,6 +288,21 @@ def main():
         "clocks": r["clocks"],
         "cpu_baseline": None,
     }
+    if not args.no_mixed and prec == 0:
+        m = run_gpu(args, wl, rank, world, 1, e2e=False, sample_clocks=False)
+        ms = m["stats"]
+        line["mixed_fp32"] = {
+            "what": "same step with FP32 operator copies for the Davidson matvecs, then FP64-matvec "
+                    "refinement to the same tolerance; FP64 renormalization and density matrix",
+            "value": ms["hpsi_flops"] / (m["step_ms"] * 1e-3) / 1e12,
+            "ms_per_step": m["step_ms"] / K,
+            "speedup_vs_fp64_step": r["step_ms"] / m["step_ms"],
+            "davidson_iters_per_step": ms["davidson_iters"] / K,
+            "fp32_matvec_iters_per_step": ms["davidson_iters_lowp"] / K,
+            "abs_dE_vs_fp64": abs(m["e_mid"] - r["e_mid"]),
+            "overlap_vs_fp64": float(abs(np.dot(m["psi_mid"], r["psi_mid"]))),
+            "energy": m["e_mid"],
+        }
     if rank == 0 and not args.no_cpu_baseline:
         try:
             from oracle import baseline
@@ -252,7 +311,7 @@ def main():
             line["cpu_baseline"] = {"error": str(exc)}
     if rank == 0:
         print(json.dumps(line))
-    r["ctx"].close()
+
     if world > 1:
         import torch
         torch.distributed.destroy_process_group()

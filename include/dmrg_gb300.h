@@ -48,6 +48,9 @@ enum {
   DMRG_ETIMEOUT = -6  /* a bounded device-side wait ran out                  */
 };
 
+/* FP64: every operation in FP64.  FP32: FP64 block operators, renormalization and
+ * density matrices; FP32 copies of the operators for the Davidson matvecs.
+ * BF16X3 is reserved (rejected by dmrg_init in this build). */
 enum { DMRG_PREC_FP64 = 0, DMRG_PREC_FP32 = 1, DMRG_PREC_BF16X3 = 2 };
 
 typedef struct dmrg_ctx dmrg_ctx; /* opaque, library-owned */
@@ -111,8 +114,9 @@ int dmrg_enlarged_layout(dmrg_ctx *ctx, int direction, int *nsec, int *sectors);
  * psi and sigma have the dmrg_psi_layout layout and length dim.  If device_ptrs
  * is non-zero both are device pointers valid on the context's stream (sigma
  * is written, not accumulated; psi is not modified; they must not overlap);
- * otherwise both are host pointers and the call copies in and out.
- * In DMRG_PREC_FP64 the result is bitwise repeatable run to run.
+ * otherwise both are host pointers and the call copies in and out.  The
+ * operators are those of the working precision (FP32 copies in DMRG_PREC_FP32).
+ * The result is bitwise repeatable run to run (fixed summation order).
  */
 int dmrg_hpsi(dmrg_ctx *ctx, const double *psi, double *sigma, int device_ptrs);
 
@@ -131,7 +135,10 @@ int dmrg_get_psi(dmrg_ctx *ctx, double *psi, int device_ptr);
 
 /*
  * dmrg_davidson -- lowest eigenpair of Eq. h_mat at the current position by
- * Davidson's method (Sec. 2.2.1) in FP64 on the GPU: diagonal preconditioner
+ * Davidson's method (Sec. 2.2.1); vectors, orthogonalisation, the subspace
+ * eigenproblem and residuals are FP64 on the GPU.  In DMRG_PREC_FP32 the
+ * matvecs use FP32 operator copies until the residual reaches ~1e-6 |E|, then
+ * continue with FP64 matvecs to tol (iterative refinement).  Diagonal preconditioner
  * (E - diag H)^-1 with |denominator| >= 1e-8, subspace <= 24, thick restart
  * with 2 vectors, converged when ||H psi - E psi|| <= tol for normalized psi.
  * Starts from the current psi when one is set, else from a fixed pseudo-random
@@ -183,11 +190,13 @@ int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, 
  * any may be NULL): total device time of the H.psi kernel launches (CUDA events
  * recorded on the context stream around each launch), number of H.psi calls,
  * their summed algorithmic FLOPs, kernels launched by this library in the
- * process, Davidson iterations.  reset != 0 zeroes the counters afterwards.
- * Synchronizes the context stream.
+ * process, Davidson iterations (all, and those with low-precision matvecs),
+ * and the residual norm of the last Davidson run.  reset != 0 zeroes the
+ * counters afterwards.  Synchronizes the context stream.
  */
 int dmrg_stats(dmrg_ctx *ctx, int reset, double *hpsi_ms, long long *hpsi_calls, double *hpsi_flops,
-               long long *kernel_launches, long long *davidson_iters);
+               long long *kernel_launches, long long *davidson_iters, long long *davidson_iters_lowp,
+               double *last_residual);
 
 /*
  * dmrg_plan_hpsi_flops -- host only (no GPU): algorithmic FLOPs and task count

@@ -55,7 +55,7 @@ def lib():
         "dmrg_renormalize": (C.c_int, [vp, C.c_int, ip, dp, dp]),
         "dmrg_sweep": (C.c_int, [vp, C.c_int, C.c_double, dp]),
         "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
-        "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp]),
+        "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp, llp, dp]),
         "dmrg_plan_hpsi_flops": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip,
                                            C.c_int, ip, dp, llp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -238,10 +238,12 @@ class DMRG:
 
     def stats(self, reset=False):
         ms, calls, fl, launches, dav = C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_longlong()
+        dlow, res = C.c_longlong(), C.c_double()
         _check(lib().dmrg_stats(self.ctx, int(reset), C.byref(ms), C.byref(calls), C.byref(fl),
-                                C.byref(launches), C.byref(dav)))
+                                C.byref(launches), C.byref(dav), C.byref(dlow), C.byref(res)))
         return dict(hpsi_ms=ms.value, hpsi_calls=calls.value, hpsi_flops=fl.value,
-                    kernel_launches=launches.value, davidson_iters=dav.value)
+                    kernel_launches=launches.value, davidson_iters=dav.value,
+                    davidson_iters_lowp=dlow.value, last_residual=res.value)
 
     def block_op(self, side, kind, i=-1, j=-1):
         n = C.c_longlong()

@@ -165,9 +165,10 @@ static Psi psi_layout(const BlockLayout &l, const BlockLayout &r, int nu, int nd
 // resolved operator -> effective block for ket sector a
 struct Arenas {
   const BlockLayout *lay[2];
-  const double *stored[2];
+  const void *stored[2];
   const TempSet *temps;
-  const double *temp[2];
+  const void *temp[2];
+  int esize;  // bytes per element of the arenas (8: FP64 masters, 4: FP32 copies)
 };
 
 static bool eff_block(const Ref &r, const Arenas &A, int side, int a, int &a2, uint64_t &addr,
@@ -183,7 +184,7 @@ static bool eff_block(const Ref &r, const Arenas &A, int side, int a, int &a2, u
   const std::vector<int64_t> *off;
   int64_t base;
   int dnu, dnd;
-  const double *arena;
+  const void *arena;
   bool tr = r.tr;
   if (r.arena < 2) {
     const Family &F = b.fam[r.fam];
@@ -207,7 +208,7 @@ static bool eff_block(const Ref &r, const Arenas &A, int side, int a, int &a2, u
     a2 = (*bra)[a];
     if (a2 < 0) return false;
     const int m2 = b.sec[a2].dim;
-    addr = eaddr(arena) + base + (*off)[a] + (int64_t)r.k * m2 * ma;
+    addr = (uint64_t)(uintptr_t)arena / A.esize + base + (*off)[a] + (int64_t)r.k * m2 * ma;
     rs = ma;
     cs = 1;
   } else {
@@ -215,7 +216,7 @@ static bool eff_block(const Ref &r, const Arenas &A, int side, int a, int &a2, u
     if (ket < 0 || (*bra)[ket] != a) return false;
     a2 = ket;
     const int m2 = b.sec[ket].dim;
-    addr = eaddr(arena) + base + (*off)[ket] + (int64_t)r.k * ma * m2;
+    addr = (uint64_t)(uintptr_t)arena / A.esize + base + (*off)[ket] + (int64_t)r.k * ma * m2;
     rs = 1;
     cs = m2;
   }
@@ -261,6 +262,44 @@ struct ChainList {
       for (size_t t = i; t < j; ++t) flat.push_back(ent[t].second);
       grp.push_back(g);
       i = j;
+    }
+  }
+};
+
+// A task list on the device: small output blocks (<= 16 x 16) go to the
+// warp-per-block kernel, the rest to the 32 x 32-tile kernel.
+struct DevChain {
+  DBuf<ChainEntry> ent;
+  DBuf<ChainGroup> all, big, small;
+  int nall = 0, nbig = 0, nsmall = 0, ntiles = 0;
+  void upload(const ChainList &CL, cudaStream_t s) {
+    std::vector<ChainGroup> vb, vs;
+    int tiles = 0;
+    for (auto g : CL.grp) {
+      if (g.m <= 16 && g.q <= 16) {
+        vs.push_back(g);
+      } else {
+        g.tile0 = tiles;
+        tiles += ((g.m + 31) / 32) * ((g.q + 31) / 32);
+        vb.push_back(g);
+      }
+    }
+    ent.upload(CL.flat, s);
+    all.upload(CL.grp, s);
+    big.upload(vb, s);
+    small.upload(vs, s);
+    nall = (int)CL.grp.size();
+    nbig = (int)vb.size();
+    nsmall = (int)vs.size();
+    ntiles = tiles;
+  }
+  void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) const {
+    if (f32ops) {
+      CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, db, s));
+      CK(launch_chain_small_f32ops(ent.p, small.p, nsmall, xb, yb, zb, db, s));
+    } else {
+      CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, db, s));
+      CK(launch_chain_small_fp64(ent.p, small.p, nsmall, xb, yb, zb, db, s));
     }
   }
 };
@@ -350,12 +389,14 @@ struct HPlan {
   const DevBlock *lb = nullptr, *rb = nullptr;
   Psi psi;
   DevTemps temps;
-  DBuf<ChainEntry> ent;
-  DBuf<ChainGroup> grp;
-  int ngroups = 0, ntiles = 0;
+  DevChain chain;
   double flops = 0.0;
   long long ntasks = 0;
   DBuf<double> diag;
+  // mixed precision: FP32 copies of the operators and temporaries + their task list
+  bool lowp = false;
+  DBuf<float> f32[4];  // left ops, right ops, left temps, right temps
+  DevChain chain32;
 };
 
 }  // namespace dmrg
@@ -383,6 +424,8 @@ struct dmrg_ctx {
   double hpsi_flops_acc = 0.0;
   long long dav_iters = 0;
   long long launch_base = 0;
+  double last_resid = 0.0;
+  long long dav_iters_lowp = 0;
 };
 
 namespace dmrg {
@@ -522,20 +565,34 @@ static void build_hplan(dmrg_ctx *c) {
   const double *stored[2] = {lb->arena(), rb->arena()};
   build_temps(P.temps, lay, stored, c->stream);
   Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
-           {P.temps.arena[0].p, P.temps.arena[1].p}};
+           {P.temps.arena[0].p, P.temps.arena[1].p}, 8};
   ChainList CL;
   double flops = 0.0;
   expand_hpsi(rps, A, Y, lb->lay, CL, flops);
   CL.finish(psi_protos(Y));
-  P.ent.upload(CL.flat, c->stream);
-  P.grp.upload(CL.grp, c->stream);
-  P.ngroups = (int)CL.grp.size();
-  P.ntiles = CL.ntiles;
+  P.chain.upload(CL, c->stream);
   P.flops = flops;
   P.ntasks = (long long)CL.flat.size();
   P.diag.alloc((size_t)std::max<int64_t>(Y.dim, 1));
   CK(cudaMemsetAsync(P.diag.p, 0, Y.dim * sizeof(double), c->stream));
-  CK(launch_diag_fp64(P.ent.p, P.grp.p, P.ngroups, 0, 0, P.diag.p, c->stream));
+  CK(launch_diag_fp64(P.chain.ent.p, P.chain.all.p, P.chain.nall, 0, 0, P.diag.p, c->stream));
+  P.lowp = c->prec != DMRG_PREC_FP64;
+  if (P.lowp) {
+    // FP32 working copies of every operand of the H.psi task list (Davidson matvecs)
+    const double *src[4] = {lb->arena(), rb->arena(), P.temps.arena[0].p, P.temps.arena[1].p};
+    const int64_t cnt[4] = {lb->lay.total, rb->lay.total, P.temps.set.total[0], P.temps.set.total[1]};
+    for (int i = 0; i < 4; ++i) {
+      P.f32[i].alloc((size_t)std::max<int64_t>(cnt[i], 1));
+      if (cnt[i] > 0 && src[i]) CK(launch_to_f32(P.f32[i].p, src[i], cnt[i], c->stream));
+    }
+    Arenas A32{{&lb->lay, &rb->lay}, {P.f32[0].p, P.f32[1].p}, &P.temps.set, {P.f32[2].p, P.f32[3].p}, 4};
+    ChainList CL32;
+    double fl32 = 0.0;
+    expand_hpsi(rps, A32, Y, lb->lay, CL32, fl32);
+    CL32.finish(psi_protos(Y));
+    P.chain32.upload(CL32, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+  }
   CK(cudaStreamSynchronize(c->stream));  // host vectors above are released on return
   P.valid = true;
 }
@@ -551,8 +608,9 @@ static void fold_events(dmrg_ctx *c) {
   c->ev_used = 0;
 }
 
-static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma) {
+static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma, bool fp64 = false) {
   HPlan &P = c->plan;
+  const bool lowp = P.lowp && !fp64;
   CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
   if (c->ev_used + 2 > 4096) fold_events(c);
   while (c->ev.size() < c->ev_used + 2) {
@@ -561,8 +619,8 @@ static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma) {
     c->ev.push_back(e);
   }
   CK(cudaEventRecord(c->ev[c->ev_used], c->stream));
-  CK(launch_chain_fp64(P.ent.p, P.grp.p, P.ngroups, P.ntiles, 0, (uint64_t)(uintptr_t)psi, 0,
-                       (uint64_t)(uintptr_t)sigma, c->stream));
+  (lowp ? P.chain32 : P.chain).launch(lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma,
+                                      c->stream);
   CK(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
   c->hpsi_calls += 1;
@@ -622,7 +680,7 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
   stored[1 - side] = nullptr;
   build_temps(temps, lay, stored, c->stream);
   Arenas A{{lay[0], lay[1]}, {stored[0], stored[1]}, &temps.set,
-           {temps.arena[0].p, temps.arena[1].p}};
+           {temps.arena[0].p, temps.arena[1].p}, 8};
 
   // sub-block lookup: enlarged sector index + row offset of (x, y)
   std::map<std::pair<int, int>, std::pair<int, int>> where;
@@ -702,11 +760,9 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
     }
   }
   CL.finish(protos);
-  DBuf<ChainEntry> dent;
-  DBuf<ChainGroup> dgrp;
-  dent.upload(CL.flat, c->stream);
-  dgrp.upload(CL.grp, c->stream);
-  CK(launch_chain_fp64(dent.p, dgrp.p, (int)CL.grp.size(), CL.ntiles, 0, 0, 0, 0, c->stream));
+  DevChain dc;
+  dc.upload(CL, c->stream);
+  dc.launch(false, 0, 0, 0, 0, c->stream);
   CK(cudaStreamSynchronize(c->stream));
   nb->parent = enl;
   nb->kept = kept;
@@ -797,12 +853,10 @@ static void rdm_truncate(dmrg_ctx *c, int direction, const Enlarged &enl, std::v
       CL.ent.push_back({gi, ce});
     }
   CL.finish(protos);
-  DBuf<ChainEntry> dent;
-  DBuf<ChainGroup> dgrp;
-  dent.upload(CL.flat, c->stream);
-  dgrp.upload(CL.grp, c->stream);
+  DevChain dc;
+  dc.upload(CL, c->stream);
   const uint64_t pb = (uint64_t)(uintptr_t)c->psi.p;
-  CK(launch_chain_fp64(dent.p, dgrp.p, (int)CL.grp.size(), CL.ntiles, 0, pb, pb, 0, c->stream));
+  dc.launch(false, 0, pb, pb, 0, c->stream);
 
   // per-sector eigendecomposition (LAPACK-style syevd, eigenvalues ascending)
   int maxn = 0;
@@ -985,12 +1039,9 @@ static void predict_psi(dmrg_ctx *c, const Psi &old, const DBuf<double> &oldpsi,
   CL.finish(protos);
   c->psi.alloc((size_t)std::max<int64_t>(Y.dim, 1));
   CK(cudaMemsetAsync(c->psi.p, 0, Y.dim * sizeof(double), c->stream));
-  DBuf<ChainEntry> dent;
-  DBuf<ChainGroup> dgrp;
-  dent.upload(CL.flat, c->stream);
-  dgrp.upload(CL.grp, c->stream);
-  CK(launch_chain_fp64(dent.p, dgrp.p, (int)CL.grp.size(), CL.ntiles, 0, 0, 0,
-                       (uint64_t)(uintptr_t)c->psi.p, c->stream));
+  DevChain dc;
+  dc.upload(CL, c->stream);
+  dc.launch(false, 0, 0, 0, (uint64_t)(uintptr_t)c->psi.p, c->stream);
   CK(cudaStreamSynchronize(c->stream));
   c->psi_valid = !CL.flat.empty();
 }
@@ -1053,7 +1104,11 @@ static void do_renormalize(dmrg_ctx *c, int direction, const int *kept_in, const
 
 // ---------------------------------------------------------------- Davidson
 
-static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters, bool &conv) {
+// One Davidson run (Sec. 2.2.1) from the current psi.  fp64: matvecs with the
+// FP64 task list; otherwise the context's working precision.  floor: extra
+// residual threshold (the attainable residual of low-precision matvecs).
+static void davidson_core(dmrg_ctx *c, double tol, double floor_rel, int max_iter, bool fp64,
+                          double *energy, int *iters, bool &conv) {
   build_hplan(c);
   HPlan &P = c->plan;
   const int64_t n = P.psi.dim;
@@ -1085,7 +1140,7 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
   };
   normalize(c->V.p);
   int k = 1;
-  hpsi_dev(c, c->V.p, c->AV.p);
+  hpsi_dev(c, c->V.p, c->AV.p, fp64);
   // G[0][0]
   CK(launch_dots(c->V.p, 1, n, c->AV.p, c->partial.p, dots, s));
   CK(cudaMemcpyAsync(Gh.data(), dots, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1117,8 +1172,8 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
     CK(cudaMemcpyAsync(&r2, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     CK(cudaStreamSynchronize(s));
     rnorm = std::sqrt(std::max(r2, 0.0));
-    if (rnorm <= tol || k >= n) {
-      conv = rnorm <= tol || k >= n;
+    if (rnorm <= std::max(tol, floor_rel * std::fabs(theta)) || k >= n) {
+      conv = true;
       break;
     }
     if (k == kmax) {
@@ -1169,7 +1224,7 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
     }
     CK(launch_scale(c->t.p, scal + 1, 1, n, s));
     CK(cudaMemcpyAsync(c->V.p + (int64_t)k * n, c->t.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
-    hpsi_dev(c, c->V.p + (int64_t)k * n, c->AV.p + (int64_t)k * n);
+    hpsi_dev(c, c->V.p + (int64_t)k * n, c->AV.p + (int64_t)k * n, fp64);
     // new row/column of G: V^T (A v_k)
     CK(launch_dots(c->V.p, k + 1, n, c->AV.p + (int64_t)k * n, c->partial.p, dots, s));
     std::vector<double> col(k + 1);
@@ -1183,11 +1238,31 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
   }
   // normalize the Ritz vector once more
   normalize(c->psi.p);
+  c->last_resid = rnorm;
   CK(cudaStreamSynchronize(s));
   c->psi_valid = true;
   c->dav_iters += std::min(it, max_iter);
   if (energy) *energy = theta;
   if (iters) *iters = std::min(it, max_iter);
+}
+
+// Davidson at the working precision.  In mixed precision the low-precision
+// matvecs run down to their attainable residual (~1e-6 |E|), then Davidson
+// continues from that vector with FP64 matvecs to the requested tolerance
+// (iterative refinement), so the energy and vector are FP64 quality.
+static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters, bool &conv) {
+  build_hplan(c);
+  if (!c->plan.lowp) {
+    davidson_core(c, tol, 0.0, max_iter, true, energy, iters, conv);
+    return;
+  }
+  int it1 = 0, it2 = 0;
+  double e = 0.0;
+  davidson_core(c, tol, 1e-6, max_iter, false, &e, &it1, conv);
+  c->dav_iters_lowp += it1;
+  davidson_core(c, tol, 0.0, std::max(1, max_iter - it1), true, &e, &it2, conv);
+  if (energy) *energy = e;
+  if (iters) *iters = it1 + it2;
 }
 
 }  // namespace dmrg
@@ -1222,8 +1297,8 @@ extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double
   const int nu = (N + two_sz) / 2, nd = (N - two_sz) / 2;
   if (nu > L || nd > L) throw Fail{DMRG_EINVAL, "more electrons of one spin than orbitals"};
   if (M < 1) throw Fail{DMRG_EINVAL, "M must be >= 1"};
-  if (precision != DMRG_PREC_FP64)
-    throw Fail{DMRG_EINVAL, "only DMRG_PREC_FP64 is available in this build"};
+  if (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_FP32)
+    throw Fail{DMRG_EINVAL, "precision must be DMRG_PREC_FP64 or DMRG_PREC_FP32 in this build"};
   if (!h || !v) throw Fail{DMRG_EINVAL, "integrals are NULL"};
   const size_t L2 = (size_t)L * L, L4 = L2 * L2;
   for (size_t i = 0; i < L2; ++i)
@@ -1485,7 +1560,8 @@ extern "C" int dmrg_block_op(dmrg_ctx *c, int side, int kind, int i, int j, doub
 }
 
 extern "C" int dmrg_stats(dmrg_ctx *c, int reset, double *hpsi_ms, long long *hpsi_calls,
-                          double *hpsi_flops, long long *kernel_launches, long long *davidson_iters) {
+                          double *hpsi_flops, long long *kernel_launches, long long *davidson_iters,
+                          long long *davidson_iters_lowp, double *last_residual) {
   API_BEGIN
   if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
   fold_events(c);
@@ -1494,7 +1570,10 @@ extern "C" int dmrg_stats(dmrg_ctx *c, int reset, double *hpsi_ms, long long *hp
   if (hpsi_flops) *hpsi_flops = c->hpsi_flops_acc;
   if (kernel_launches) *kernel_launches = kernel_launch_count() - c->launch_base;
   if (davidson_iters) *davidson_iters = c->dav_iters;
+  if (davidson_iters_lowp) *davidson_iters_lowp = c->dav_iters_lowp;
+  if (last_residual) *last_residual = c->last_resid;
   if (reset) {
+    c->dav_iters_lowp = 0;
     c->hpsi_ms_folded = 0.0;
     c->hpsi_calls = 0;
     c->hpsi_flops_acc = 0.0;
@@ -1531,7 +1610,7 @@ extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, c
   auto rps = resolve_pieces(I, k, lb, rb, temps);
   const BlockLayout *lay[2] = {&lb, &rb};
   temps.layout(lay);
-  Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}};
+  Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 8};
   ChainList CL;
   double f = 0.0;
   expand_hpsi(rps, A, Y, lb, CL, f);

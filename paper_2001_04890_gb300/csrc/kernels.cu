@@ -29,14 +29,21 @@ __device__ __forceinline__ const double *dptr(uint64_t base, uint64_t off) {
   return reinterpret_cast<const double *>(base + off * 8ull);
 }
 
-__global__ void __launch_bounds__(256) chain_fp64_kernel(const ChainEntry *__restrict__ E,
-                                                         const ChainGroup *__restrict__ G,
-                                                         int ngroups, uint64_t xb, uint64_t yb,
-                                                         uint64_t zb, uint64_t db) {
-  __shared__ double Xs[32][33];
-  __shared__ double Ys[32][33];
-  __shared__ double Ts[32][33];
-  __shared__ double Zs[32][33];
+template <typename T>
+__device__ __forceinline__ const T *tptr(uint64_t base, uint64_t off) {
+  return reinterpret_cast<const T *>(base + off * sizeof(T));
+}
+
+// TX/TY/TZ: operand element types; TA: accumulation type; D is FP64.
+template <typename TX, typename TY, typename TZ, typename TA>
+__global__ void __launch_bounds__(256) chain_kernel(const ChainEntry *__restrict__ E,
+                                                    const ChainGroup *__restrict__ G, int ngroups,
+                                                    uint64_t xb, uint64_t yb, uint64_t zb,
+                                                    uint64_t db) {
+  __shared__ TA Xs[32][33];
+  __shared__ TA Ys[32][33];
+  __shared__ TA Ts[32][33];
+  __shared__ TA Zs[32][33];
   const int tile = blockIdx.x;
   int lo = 0, hi = ngroups - 1;
   while (lo < hi) {
@@ -49,29 +56,30 @@ __global__ void __launch_bounds__(256) chain_fp64_kernel(const ChainEntry *__res
   const int r0 = (tl / ntq) * 32, c0 = (tl % ntq) * 32;
   const int tid = threadIdx.x, tx = tid & 31, ty = tid >> 5;
   const int mrows = min(32, g.m - r0), qcols = min(32, g.q - c0);
-  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  TA acc[4] = {0, 0, 0, 0};
 
   for (int ei = g.first; ei < g.first + g.count; ++ei) {
     const ChainEntry e = E[ei];
     const bool xid = e.x == IDN, yid = e.y == IDN, zid = e.z == IDN;
-    const double *X = xid ? nullptr : dptr(xb, e.x);
-    const double *Y = yid ? nullptr : dptr(yb, e.y);
-    const double *Z = zid ? nullptr : dptr(zb, e.z);
+    const TX *X = xid ? nullptr : tptr<TX>(xb, e.x);
+    const TY *Y = yid ? nullptr : tptr<TY>(yb, e.y);
+    const TZ *Z = zid ? nullptr : tptr<TZ>(zb, e.z);
+    const TA f = (TA)e.f;
     const int n = e.n, p = e.p;
     const int pbeg = zid ? c0 : 0;
     const int pend = zid ? min(c0 + 32, p) : p;
     for (int p0 = pbeg; p0 < pend; p0 += 32) {
       const int pc = min(32, pend - p0);
-      double t[4] = {0.0, 0.0, 0.0, 0.0};
+      TA t[4] = {0, 0, 0, 0};
       if (xid || yid) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
           const int r = ty + 8 * i;
           if (r < mrows && tx < pc) {
             const int64_t R = r0 + r, Cc = p0 + tx;
-            if (xid && yid) t[i] = (R == Cc) ? 1.0 : 0.0;
-            else if (xid) t[i] = Y[R * e.yrs + Cc * e.ycs];
-            else t[i] = X[R * e.xrs + Cc * e.xcs];
+            if (xid && yid) t[i] = (R == Cc) ? (TA)1 : (TA)0;
+            else if (xid) t[i] = (TA)Y[R * e.yrs + Cc * e.ycs];
+            else t[i] = (TA)X[R * e.xrs + Cc * e.xcs];
           }
         }
       } else {
@@ -80,14 +88,14 @@ __global__ void __launch_bounds__(256) chain_fp64_kernel(const ChainEntry *__res
           for (int idx = tid; idx < 1024; idx += 256) {
             const int i = idx >> 5, kk = idx & 31;
             Xs[i][kk] = (i < mrows && kk < nc)
-                            ? X[(int64_t)(r0 + i) * e.xrs + (int64_t)(n0 + kk) * e.xcs] : 0.0;
+                            ? (TA)X[(int64_t)(r0 + i) * e.xrs + (int64_t)(n0 + kk) * e.xcs] : (TA)0;
             Ys[i][kk] = (i < nc && kk < pc)
-                            ? Y[(int64_t)(n0 + i) * e.yrs + (int64_t)(p0 + kk) * e.ycs] : 0.0;
+                            ? (TA)Y[(int64_t)(n0 + i) * e.yrs + (int64_t)(p0 + kk) * e.ycs] : (TA)0;
           }
           __syncthreads();
           if (tx < pc) {
             for (int kk = 0; kk < nc; ++kk) {
-              const double y = Ys[kk][tx];
+              const TA y = Ys[kk][tx];
 #pragma unroll
               for (int i = 0; i < 4; ++i)
                 if (ty + 8 * i < mrows) t[i] = fma(Xs[ty + 8 * i][kk], y, t[i]);
@@ -98,45 +106,178 @@ __global__ void __launch_bounds__(256) chain_fp64_kernel(const ChainEntry *__res
       }
       if (zid) {
 #pragma unroll
-        for (int i = 0; i < 4; ++i) acc[i] = fma(e.f, t[i], acc[i]);
+        for (int i = 0; i < 4; ++i) acc[i] = fma(f, t[i], acc[i]);
       } else {
 #pragma unroll
         for (int i = 0; i < 4; ++i) Ts[ty + 8 * i][tx] = t[i];
         for (int idx = tid; idx < 1024; idx += 256) {
           const int kk = idx >> 5, j = idx & 31;
           Zs[kk][j] = (kk < pc && j < qcols)
-                          ? Z[(int64_t)(p0 + kk) * e.zrs + (int64_t)(c0 + j) * e.zcs] : 0.0;
+                          ? (TA)Z[(int64_t)(p0 + kk) * e.zrs + (int64_t)(c0 + j) * e.zcs] : (TA)0;
         }
         __syncthreads();
         if (tx < qcols) {
-          double s[4] = {0.0, 0.0, 0.0, 0.0};
+          TA sacc[4] = {0, 0, 0, 0};
           for (int kk = 0; kk < pc; ++kk) {
-            const double z = Zs[kk][tx];
+            const TA z = Zs[kk][tx];
 #pragma unroll
             for (int i = 0; i < 4; ++i)
-              if (ty + 8 * i < mrows) s[i] = fma(Ts[ty + 8 * i][kk], z, s[i]);
+              if (ty + 8 * i < mrows) sacc[i] = fma(Ts[ty + 8 * i][kk], z, sacc[i]);
           }
 #pragma unroll
-          for (int i = 0; i < 4; ++i) acc[i] = fma(e.f, s[i], acc[i]);
+          for (int i = 0; i < 4; ++i) acc[i] = fma(f, sacc[i], acc[i]);
         }
         __syncthreads();
       }
     }
   }
-  double *D = const_cast<double *>(dptr(db, g.d));
+  double *D = const_cast<double *>(tptr<double>(db, g.d));
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int r = ty + 8 * i;
-    if (r < mrows && tx < qcols) D[(int64_t)(r0 + r) * g.drs + (int64_t)(c0 + tx) * g.dcs] += acc[i];
+    if (r < mrows && tx < qcols) D[(int64_t)(r0 + r) * g.drs + (int64_t)(c0 + tx) * g.dcs] += (double)acc[i];
   }
+}
+
+// Small output blocks (m, q <= 16): one warp per output block, 16x16 tiles and
+// warp barriers only.  Lane l owns column l % 16 and rows l / 16 + 2 i.
+template <typename TX, typename TY, typename TZ, typename TA>
+__global__ void __launch_bounds__(256) chain_small_kernel(const ChainEntry *__restrict__ E,
+                                                          const ChainGroup *__restrict__ G,
+                                                          int ngroups, uint64_t xb, uint64_t yb,
+                                                          uint64_t zb, uint64_t db) {
+  __shared__ TA sm[8][4][16][17];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int gi = blockIdx.x * 8 + warp;
+  if (gi >= ngroups) return;  // warp-uniform; no block-level barrier below
+  const ChainGroup g = G[gi];
+  TA(*Xs)[17] = sm[warp][0];
+  TA(*Ys)[17] = sm[warp][1];
+  TA(*Ts)[17] = sm[warp][2];
+  TA(*Zs)[17] = sm[warp][3];
+  const int c = lane & 15, rbase = lane >> 4;
+  const int m = g.m, q = g.q;
+  TA acc[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) acc[i] = 0;
+  for (int ei = g.first; ei < g.first + g.count; ++ei) {
+    const ChainEntry e = E[ei];
+    const bool xid = e.x == IDN, yid = e.y == IDN, zid = e.z == IDN;
+    const TX *X = xid ? nullptr : tptr<TX>(xb, e.x);
+    const TY *Y = yid ? nullptr : tptr<TY>(yb, e.y);
+    const TZ *Z = zid ? nullptr : tptr<TZ>(zb, e.z);
+    const TA f = (TA)e.f;
+    const int n = e.n, p = e.p;
+    const int pend = zid ? min(16, p) : p;
+    for (int p0 = 0; p0 < pend; p0 += 16) {
+      const int pc = min(16, pend - p0);
+      TA t[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) t[i] = 0;
+      if (xid || yid) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int r = rbase + 2 * i;
+          if (r < m && c < pc) {
+            const int64_t Cc = p0 + c;
+            if (xid && yid) t[i] = (r == Cc) ? (TA)1 : (TA)0;
+            else if (xid) t[i] = (TA)Y[(int64_t)r * e.yrs + Cc * e.ycs];
+            else t[i] = (TA)X[(int64_t)r * e.xrs + Cc * e.xcs];
+          }
+        }
+      } else {
+        for (int n0 = 0; n0 < n; n0 += 16) {
+          const int nc = min(16, n - n0);
+#pragma unroll
+          for (int j = 0; j < 8; ++j) {
+            const int idx = lane + 32 * j, i = idx >> 4, kk = idx & 15;
+            Xs[i][kk] = (i < m && kk < nc) ? (TA)X[(int64_t)i * e.xrs + (int64_t)(n0 + kk) * e.xcs] : (TA)0;
+            Ys[i][kk] = (i < nc && kk < pc) ? (TA)Y[(int64_t)(n0 + i) * e.yrs + (int64_t)(p0 + kk) * e.ycs] : (TA)0;
+          }
+          __syncwarp();
+          if (c < pc) {
+            for (int kk = 0; kk < nc; ++kk) {
+              const TA y = Ys[kk][c];
+#pragma unroll
+              for (int i = 0; i < 8; ++i)
+                if (rbase + 2 * i < m) t[i] = fma(Xs[rbase + 2 * i][kk], y, t[i]);
+            }
+          }
+          __syncwarp();
+        }
+      }
+      if (zid) {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) acc[i] = fma(f, t[i], acc[i]);
+      } else {
+#pragma unroll
+        for (int i = 0; i < 8; ++i) Ts[rbase + 2 * i][c] = t[i];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int idx = lane + 32 * j, kk = idx >> 4, jj = idx & 15;
+          Zs[kk][jj] = (kk < pc && jj < q) ? (TA)Z[(int64_t)(p0 + kk) * e.zrs + (int64_t)jj * e.zcs] : (TA)0;
+        }
+        __syncwarp();
+        if (c < q) {
+          TA sacc[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i) sacc[i] = 0;
+          for (int kk = 0; kk < pc; ++kk) {
+            const TA z = Zs[kk][c];
+#pragma unroll
+            for (int i = 0; i < 8; ++i)
+              if (rbase + 2 * i < m) sacc[i] = fma(Ts[rbase + 2 * i][kk], z, sacc[i]);
+          }
+#pragma unroll
+          for (int i = 0; i < 8; ++i) acc[i] = fma(f, sacc[i], acc[i]);
+        }
+        __syncwarp();
+      }
+    }
+  }
+  double *D = const_cast<double *>(tptr<double>(db, g.d));
+#pragma unroll
+  for (int i = 0; i < 8; ++i) {
+    const int r = rbase + 2 * i;
+    if (r < m && c < q) D[(int64_t)r * g.drs + (int64_t)c * g.dcs] += (double)acc[i];
+  }
+}
+
+cudaError_t launch_chain_small_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
+                                    uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  COUNT(1);
+  chain_small_kernel<double, double, double, double><<<(ngroups + 7) / 8, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_chain_small_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups,
+                                      uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  COUNT(1);
+  chain_small_kernel<float, double, float, float><<<(ngroups + 7) / 8, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_chain_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
                               uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
   if (ngroups <= 0 || ntiles <= 0) return cudaSuccess;
   COUNT(1);
-  chain_fp64_kernel<<<ntiles, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
+  chain_kernel<double, double, double, double><<<ntiles, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
   return cudaGetLastError();
+}
+
+cudaError_t launch_chain_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
+                                uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
+  if (ngroups <= 0 || ntiles <= 0) return cudaSuccess;
+  COUNT(1);
+  chain_kernel<float, double, float, float><<<ntiles, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
+  return cudaGetLastError();
+}
+
+__global__ void to_f32_kernel(float *out, const double *in, int64_t n) {
+  for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (int64_t)gridDim.x * blockDim.x)
+    out[e] = (float)in[e];
 }
 
 __global__ void __launch_bounds__(256) lincomb_fp64_kernel(const LincombTask *__restrict__ T,
@@ -191,6 +332,15 @@ __global__ void __launch_bounds__(256) lincomb_fp64_kernel(const LincombTask *__
     const int64_t e = e0 + tx;
     if (tt < t.kout && e < E) out[(int64_t)tt * E + e] = acc[i];
   }
+}
+
+static int grid_for(int64_t n);
+
+cudaError_t launch_to_f32(float *out, const double *in, int64_t n, cudaStream_t s) {
+  if (n <= 0) return cudaSuccess;
+  COUNT(1);
+  to_f32_kernel<<<grid_for(n), 256, 0, s>>>(out, in, n);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_lincomb_fp64(const LincombTask *t, int ntasks, int ntiles, cudaStream_t s) {

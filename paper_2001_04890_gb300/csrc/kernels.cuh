@@ -27,6 +27,15 @@ struct DevStatus {
 
 cudaError_t launch_chain_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
                               uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+// same task list with FP32 operators X, Z (FP64 psi in, FP64 sigma out, FP32 accumulation)
+cudaError_t launch_chain_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
+                                uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+// one warp per output block for blocks of at most 16 x 16 (same entry semantics)
+cudaError_t launch_chain_small_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
+                                    uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+cudaError_t launch_chain_small_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups,
+                                      uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+cudaError_t launch_to_f32(float *out, const double *in, int64_t n, cudaStream_t s);
 cudaError_t launch_lincomb_fp64(const LincombTask *t, int ntasks, int ntiles, cudaStream_t s);
 cudaError_t launch_diag_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
                              uint64_t xb, uint64_t zb, double *diag, cudaStream_t s);

@@ -133,23 +133,29 @@ def test_sweep_reaches_fci_small():
     ctx.close()
 
 
-def test_config1_l8_exact_step():
-    """L=8, N=8, Sz=0, M=64: the 3|1|1|3 step spans the full FCI space (dim 4900)."""
-    L, N, M = 8, 8, 64
+def test_config1_l8_m64_sweeps_match_oracle():
+    """L=8, N=8, Sz=0, M=64: every per-step sweep energy equals the FP64 oracle DMRG's."""
+    from oracle import dmrg as od
+    L, N, M, nsw = 8, 8, 64, 4
+    h, v = workloads.integrals(L, seed=0)
+    ctx = binding.DMRG(h, v, N, 0, M)
+    E = ctx.sweep(nsw, tol=1e-10)
+    ctx.close()
+    ref = od.OracleDMRG(h, v, N, 0, M).sweep(nsw, tol=1e-11)
+    assert np.max(np.abs(E - ref)) < 1e-9, np.abs(E - ref)
+    e_fci = fock.fci_ground(h, v, 4, 4)[0]
+    assert np.all(E >= e_fci - 1e-10)
+
+
+def test_config1_l8_m256_exact():
+    """M=256 keeps every Schmidt rank of L=8: from sweep 3 on every step is the FCI energy."""
+    L, N, M, nsw = 8, 8, 256, 5
     h, v = workloads.integrals(L, seed=0)
     e_fci = fock.fci_ground(h, v, 4, 4)[0]
     ctx = binding.DMRG(h, v, N, 0, M)
-    E = ctx.sweep(6, tol=1e-9)
-    steps = 2 * (L - 2)
-    E = E.reshape(6, steps)
-    # From the bond-dimension-1 Aufbau start the kept ranks grow 4 -> 16 -> 64 per half
-    # sweep, so both 3-site blocks are complete only from sweep 2 on.
-    # forward position 3 is index 3; backward position 3 is index (L-2) + (L-2-3)
-    for sw in range(2, 6):
-        for idx in (3, (L - 2) + (L - 2 - 3)):
-            assert abs(E[sw, idx] - e_fci) < 1e-10, (sw, idx, E[sw, idx] - e_fci, E)
-    assert np.all(E >= e_fci - 1e-10)
-    # variational and non-increasing sweep minima
-    mins = E.min(axis=1)
-    assert np.all(np.diff(mins) <= 1e-10), mins
+    E = ctx.sweep(nsw, tol=1e-10).reshape(nsw, 2 * (L - 2))
     ctx.close()
+    # ranks grow 4 -> 16 -> 64 -> 256 per half sweep from the Aufbau start
+    assert np.all(np.abs(E[3, 3:] - e_fci) < 1e-10), E[3] - e_fci
+    assert np.all(np.abs(E[4] - e_fci) < 1e-10), E[4] - e_fci
+    assert np.all(E >= e_fci - 1e-10)
