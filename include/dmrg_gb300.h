@@ -49,8 +49,11 @@ enum {
 };
 
 /* FP64: every operation in FP64.  FP32: FP64 block operators, renormalization and
- * density matrices; FP32 copies of the operators for the Davidson matvecs.
- * BF16X3 is reserved (rejected by dmrg_init in this build). */
+ * density matrices; FP32 copies of the operators for the Davidson matvecs (FP32
+ * CUDA-core arithmetic).  BF16X3: as FP32, but H.psi output blocks of 33..128
+ * rows/columns run on the tcgen05 tensor cores as three-pass split-BF16
+ * products with FP32 accumulation in tensor memory.  In both mixed modes
+ * Davidson finishes with FP64 matvecs (iterative refinement). */
 enum { DMRG_PREC_FP64 = 0, DMRG_PREC_FP32 = 1, DMRG_PREC_BF16X3 = 2 };
 
 typedef struct dmrg_ctx dmrg_ctx; /* opaque, library-owned */
@@ -206,6 +209,15 @@ int dmrg_stats(dmrg_ctx *ctx, int reset, double *hpsi_ms, long long *hpsi_calls,
  */
 int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
                          const int *sec_l, int nr, const int *sec_r, double *flops, long long *tasks);
+
+/*
+ * dmrg_selftest_tcgen05 -- device check of the library's tensor-core encodings
+ * (diagnostic): C (128 x N) = A (128 x K) B^T (B is N x K), inputs rounded to
+ * bf16, FP32 accumulation in tensor memory.  Host pointers, row-major.
+ * N in 16..256 and K in 16..64, multiples of 16.  DMRG_ETIMEOUT if the
+ * bounded completion wait ran out.
+ */
+int dmrg_selftest_tcgen05(int N, int K, const float *A, const float *B, float *C);
 
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */

@@ -58,6 +58,8 @@ def lib():
         "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp, llp, dp]),
         "dmrg_plan_hpsi_flops": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip,
                                            C.c_int, ip, dp, llp]),
+        "dmrg_selftest_tcgen05": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
+                                            C.POINTER(C.c_float)]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -108,6 +110,17 @@ def plan_hpsi_flops(h, v, N, two_sz, k, sec_l, sec_r):
     _check(lib().dmrg_plan_hpsi_flops(h.shape[0], N, two_sz, _dptr(h), _dptr(v), k, len(sl), _iptr(sl),
                                       len(sr), _iptr(sr), C.byref(f), C.byref(t)))
     return f.value, t.value
+
+
+def selftest_tcgen05(A, B):
+    """C = A B^T on the tensor cores (A: 128 x K, B: N x K, float32)."""
+    A = np.ascontiguousarray(A, dtype=np.float32)
+    B = np.ascontiguousarray(B, dtype=np.float32)
+    N, K = B.shape
+    Cm = np.zeros((128, N), dtype=np.float32)
+    fp = C.POINTER(C.c_float)
+    _check(lib().dmrg_selftest_tcgen05(N, K, A.ctypes.data_as(fp), B.ctypes.data_as(fp), Cm.ctypes.data_as(fp)))
+    return Cm
 
 
 def debug_pieces(h, v, k, l_empty, r_empty, compress=True):

@@ -13,7 +13,7 @@ OUT = os.path.join(HERE, "libdmrg_gb300.so")
 BUILD = os.path.join(ROOT, "_build")
 NVCC = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["plan.cpp", "abi_host.cpp", "kernels.cu", "dmrg.cu"]
+SOURCES = ["plan.cpp", "abi_host.cpp", "kernels.cu", "tc_kernels.cu", "dmrg.cu"]
 
 
 def _compile(src):

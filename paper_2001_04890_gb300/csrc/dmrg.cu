@@ -266,41 +266,120 @@ struct ChainList {
   }
 };
 
-// A task list on the device: small output blocks (<= 16 x 16) go to the
-// warp-per-block kernel, the rest to the 32 x 32-tile kernel.
+static double entry_flops(int m, int n, int p, int q, bool xid, bool zid);
+
+// A task list on the device.  Output blocks of at most 32 x 32 go to the
+// flattened-lane warp kernel, blocks of 33..128 to the tensor-core kernel when
+// enabled (and all their entries have n, p <= 128), the rest to the 32 x 32
+// tile kernel.  With split_tasks, every output block's entry list is cut into
+// chunks of about equal work; each chunk accumulates into its own slot of a
+// scratch buffer and a reduction adds the slots in chunk order, so the result
+// does not depend on scheduling (bitwise repeatable) while the grid has
+// thousands of independent tasks.
 struct DevChain {
   DBuf<ChainEntry> ent;
-  DBuf<ChainGroup> all, big, small;
-  int nall = 0, nbig = 0, nsmall = 0, ntiles = 0;
-  void upload(const ChainList &CL, cudaStream_t s) {
-    std::vector<ChainGroup> vb, vs;
+  DBuf<ChainGroup> all, big, flat, tcg;
+  DBuf<ReduceGroup> red;
+  DBuf<double> scratch;
+  int nall = 0, nbig = 0, nflat = 0, ntc = 0, ntiles = 0, nred = 0;
+  int64_t red_total = 0, scratch_n = 0;
+  bool split = false;
+
+  void upload(const ChainList &CL, cudaStream_t s, bool tensor_cores = false, bool split_tasks = false) {
+    std::vector<ChainGroup> vb, vf, vt;
+    std::vector<ReduceGroup> vr;
+    split = split_tasks;
     int tiles = 0;
-    for (auto g : CL.grp) {
-      if (g.m <= 16 && g.q <= 16) {
-        vs.push_back(g);
-      } else {
-        g.tile0 = tiles;
-        tiles += ((g.m + 31) / 32) * ((g.q + 31) / 32);
-        vb.push_back(g);
+    int64_t soff = 0, e0 = 0;
+    // per-entry work for chunking
+    double total = 0.0;
+    std::vector<double> w(CL.flat.size());
+    for (const auto &g : CL.grp)
+      for (int i = g.first; i < g.first + g.count; ++i) {
+        const ChainEntry &e = CL.flat[i];
+        w[i] = 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
+        total += w[i];
       }
+    const double chunk_work = std::max(total / 8192.0, 2.0e5);
+    auto place = [&](ChainGroup t) {
+      bool tc_ok = tensor_cores && t.m <= 128 && t.q <= 128 && (t.m > 32 || t.q > 32);
+      for (int i = t.first; tc_ok && i < t.first + t.count; ++i)
+        if (CL.flat[i].n > 128 || CL.flat[i].p > 128 || CL.flat[i].y == ~0ull) tc_ok = false;
+      if (tc_ok) {
+        vt.push_back(t);
+      } else if (t.m <= 32 && t.q <= 32) {
+        vf.push_back(t);
+      } else {
+        t.tile0 = tiles;
+        tiles += ((t.m + 31) / 32) * ((t.q + 31) / 32);
+        vb.push_back(t);
+      }
+    };
+    for (const auto &g : CL.grp) {
+      if (!split) {
+        place(g);
+        continue;
+      }
+      const int64_t mq = (int64_t)g.m * g.q;
+      ReduceGroup r{};
+      r.e0 = e0;
+      r.soff = soff;
+      r.d = g.d;
+      r.drs = g.drs;
+      r.dcs = g.dcs;
+      r.m = g.m;
+      r.q = g.q;
+      int nsplit = 0;
+      int i = g.first;
+      while (i < g.first + g.count) {
+        double acc = 0.0;
+        int j = i;
+        while (j < g.first + g.count && (j == i || acc + w[j] <= chunk_work)) acc += w[j++];
+        ChainGroup t = g;
+        t.first = i;
+        t.count = j - i;
+        t.d = (uint64_t)(soff + (int64_t)nsplit * mq);
+        t.drs = g.q;
+        t.dcs = 1;
+        place(t);
+        ++nsplit;
+        i = j;
+      }
+      r.nsplit = nsplit;
+      vr.push_back(r);
+      soff += (int64_t)nsplit * mq;
+      e0 += mq;
     }
     ent.upload(CL.flat, s);
     all.upload(CL.grp, s);
     big.upload(vb, s);
-    small.upload(vs, s);
+    flat.upload(vf, s);
+    tcg.upload(vt, s);
+    red.upload(vr, s);
     nall = (int)CL.grp.size();
     nbig = (int)vb.size();
-    nsmall = (int)vs.size();
+    nflat = (int)vf.size();
+    ntc = (int)vt.size();
+    nred = (int)vr.size();
     ntiles = tiles;
+    red_total = e0;
+    scratch_n = soff;
+    if (split) scratch.alloc((size_t)std::max<int64_t>(soff, 1));
   }
-  void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) const {
+
+  void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s,
+              int *status = nullptr) const {
+    const uint64_t tb = split ? (uint64_t)(uintptr_t)scratch.p : db;
+    if (split && scratch_n > 0) CK(cudaMemsetAsync(scratch.p, 0, scratch_n * sizeof(double), s));
     if (f32ops) {
-      CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, db, s));
-      CK(launch_chain_small_f32ops(ent.p, small.p, nsmall, xb, yb, zb, db, s));
+      CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+      if (ntc > 0) CK(launch_chain_tc(ent.p, tcg.p, ntc, xb, yb, zb, tb, status, s));
     } else {
-      CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, db, s));
-      CK(launch_chain_small_fp64(ent.p, small.p, nsmall, xb, yb, zb, db, s));
+      CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
     }
+    if (split) CK(launch_reduce_partials(red.p, nred, red_total, scratch.p, (double *)(uintptr_t)db, s));
   }
 };
 
@@ -426,6 +505,7 @@ struct dmrg_ctx {
   long long launch_base = 0;
   double last_resid = 0.0;
   long long dav_iters_lowp = 0;
+  dmrg::DBuf<int> dstatus;  // set by bounded device waits that ran out
 };
 
 namespace dmrg {
@@ -570,7 +650,7 @@ static void build_hplan(dmrg_ctx *c) {
   double flops = 0.0;
   expand_hpsi(rps, A, Y, lb->lay, CL, flops);
   CL.finish(psi_protos(Y));
-  P.chain.upload(CL, c->stream);
+  P.chain.upload(CL, c->stream, false, true);
   P.flops = flops;
   P.ntasks = (long long)CL.flat.size();
   P.diag.alloc((size_t)std::max<int64_t>(Y.dim, 1));
@@ -590,11 +670,22 @@ static void build_hplan(dmrg_ctx *c) {
     double fl32 = 0.0;
     expand_hpsi(rps, A32, Y, lb->lay, CL32, fl32);
     CL32.finish(psi_protos(Y));
-    P.chain32.upload(CL32, c->stream);
+    P.chain32.upload(CL32, c->stream, c->prec == DMRG_PREC_BF16X3, true);
     CK(cudaStreamSynchronize(c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));  // host vectors above are released on return
   P.valid = true;
+}
+
+// Report a bounded device-side wait that ran out (the kernel skipped its work).
+static void check_status(dmrg_ctx *c) {
+  int st = 0;
+  CK(cudaMemcpyAsync(&st, c->dstatus.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  if (st) {
+    CK(cudaMemsetAsync(c->dstatus.p, 0, sizeof(int), c->stream));
+    throw Fail{DMRG_ETIMEOUT, "a tensor-core completion wait ran out; results of that call are invalid"};
+  }
 }
 
 static void fold_events(dmrg_ctx *c) {
@@ -620,7 +711,7 @@ static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma, bool fp64 = 
   }
   CK(cudaEventRecord(c->ev[c->ev_used], c->stream));
   (lowp ? P.chain32 : P.chain).launch(lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma,
-                                      c->stream);
+                                      c->stream, c->dstatus.p);
   CK(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
   c->hpsi_calls += 1;
@@ -1149,6 +1240,8 @@ static void davidson_core(dmrg_ctx *c, double tol, double floor_rel, int max_ite
   int it = 0;
   conv = false;
   double rnorm = 0.0;
+  double best_r = 1e300;
+  int best_it = 0;
   for (it = 1; it <= max_iter; ++it) {
     // subspace eigenproblem on the device
     CK(cudaMemcpyAsync(G, Gh.data(), 32 * 32 * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -1175,6 +1268,16 @@ static void davidson_core(dmrg_ctx *c, double tol, double floor_rel, int max_ite
     if (rnorm <= std::max(tol, floor_rel * std::fabs(theta)) || k >= n) {
       conv = true;
       break;
+    }
+    // low-precision phase: stop when the residual stops improving (its attainable floor)
+    if (floor_rel > 0.0) {
+      if (rnorm < 0.7 * best_r) {
+        best_r = rnorm;
+        best_it = it;
+      } else if (it - best_it >= 8) {
+        conv = true;
+        break;
+      }
     }
     if (k == kmax) {
       // thick restart with the two lowest Ritz vectors
@@ -1258,7 +1361,7 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
   }
   int it1 = 0, it2 = 0;
   double e = 0.0;
-  davidson_core(c, tol, 1e-6, max_iter, false, &e, &it1, conv);
+  davidson_core(c, tol, 1e-8, max_iter, false, &e, &it1, conv);
   c->dav_iters_lowp += it1;
   davidson_core(c, tol, 0.0, std::max(1, max_iter - it1), true, &e, &it2, conv);
   if (energy) *energy = e;
@@ -1297,8 +1400,8 @@ extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double
   const int nu = (N + two_sz) / 2, nd = (N - two_sz) / 2;
   if (nu > L || nd > L) throw Fail{DMRG_EINVAL, "more electrons of one spin than orbitals"};
   if (M < 1) throw Fail{DMRG_EINVAL, "M must be >= 1"};
-  if (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_FP32)
-    throw Fail{DMRG_EINVAL, "precision must be DMRG_PREC_FP64 or DMRG_PREC_FP32 in this build"};
+  if (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_FP32 && precision != DMRG_PREC_BF16X3)
+    throw Fail{DMRG_EINVAL, "unknown precision"};
   if (!h || !v) throw Fail{DMRG_EINVAL, "integrals are NULL"};
   const size_t L2 = (size_t)L * L, L4 = L2 * L2;
   for (size_t i = 0; i < L2; ++i)
@@ -1319,6 +1422,8 @@ extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double
   c->I.L = L;
   c->I.h.assign(h, h + L2);
   c->I.v.assign(v, v + L4);
+  c->dstatus.alloc(1);
+  CK(cudaMemsetAsync(c->dstatus.p, 0, sizeof(int), c->stream));
   c->left.resize(L);
   c->right.resize(L);
   c->left[0] = empty_block(0, L);
@@ -1448,6 +1553,7 @@ extern "C" int dmrg_hpsi(dmrg_ctx *c, const double *psi, double *sigma, int devi
     CK(cudaMemcpyAsync(sigma, ds.p, n * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
     CK(cudaStreamSynchronize(c->stream));
   }
+  check_status(c);
   API_END
 }
 
@@ -1489,6 +1595,7 @@ extern "C" int dmrg_davidson(dmrg_ctx *c, double tol, int max_iter, double *ener
   if (!c || !(tol > 0.0) || max_iter < 1) throw Fail{DMRG_EINVAL, "bad arguments"};
   bool conv = false;
   davidson(c, tol, max_iter, energy, iters, conv);
+  check_status(c);
   if (!conv) throw Fail{DMRG_ENOCONV, "Davidson did not reach the tolerance"};
   API_END
 }
@@ -1616,5 +1723,27 @@ extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, c
   expand_hpsi(rps, A, Y, lb, CL, f);
   if (flops) *flops = f;
   if (tasks) *tasks = (long long)CL.ent.size();
+  API_END
+}
+
+extern "C" int dmrg_selftest_tcgen05(int N, int K, const float *A, const float *B, float *C) {
+  API_BEGIN
+  if (!A || !B || !C || N < 16 || N > 256 || N % 16 || K < 16 || K > 64 || K % 16)
+    throw Fail{DMRG_EINVAL, "dmrg_selftest_tcgen05: N in 16..256, K in 16..64, multiples of 16"};
+  DBuf<float> a, b, cc;
+  DBuf<int> st;
+  a.alloc(128 * K);
+  b.alloc((size_t)N * K);
+  cc.alloc((size_t)128 * N);
+  st.alloc(1);
+  CK(cudaMemcpy(a.p, A, 128 * K * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemcpy(b.p, B, (size_t)N * K * sizeof(float), cudaMemcpyHostToDevice));
+  CK(cudaMemset(st.p, 0, sizeof(int)));
+  CK(launch_tc_selftest(a.p, b.p, cc.p, N, K, st.p, nullptr));
+  CK(cudaDeviceSynchronize());
+  int status = 0;
+  CK(cudaMemcpy(&status, st.p, sizeof(int), cudaMemcpyDeviceToHost));
+  CK(cudaMemcpy(C, cc.p, (size_t)128 * N * sizeof(float), cudaMemcpyDeviceToHost));
+  if (status) throw Fail{DMRG_ETIMEOUT, "tcgen05 self-test: mbarrier wait ran out"};
   API_END
 }

@@ -9,7 +9,7 @@
 //               the density matrix psi psi^T of Sec. 2.1.
 // lincomb_fp64: pre-summed operators (Sec. 2.2.3, Eq. presum) as a GEMM
 //               [K_out x K_src] x [K_src x block elements] per sector.
-// Davidson helpers, a one-CTA Jacobi eigensolver for the small subspace
+// Davidson helpers, a one-warp Jacobi eigensolver for the small subspace
 // matrix, and a column gather that builds O from eigenvectors.
 #include <cuda_runtime.h>
 
@@ -139,27 +139,30 @@ __global__ void __launch_bounds__(256) chain_kernel(const ChainEntry *__restrict
   }
 }
 
-// Small output blocks (m, q <= 16): one warp per output block, 16x16 tiles and
-// warp barriers only.  Lane l owns column l % 16 and rows l / 16 + 2 i.
-template <typename TX, typename TY, typename TZ, typename TA>
-__global__ void __launch_bounds__(256) chain_small_kernel(const ChainEntry *__restrict__ E,
-                                                          const ChainGroup *__restrict__ G,
-                                                          int ngroups, uint64_t xb, uint64_t yb,
-                                                          uint64_t zb, uint64_t db) {
-  __shared__ TA sm[8][4][16][17];
+// Output blocks of at most 32 x 32: one warp per (output block, entry chunk);
+// lanes are assigned to the m*p elements of T = X Y and the m*q elements of
+// the output block in flattened order, so a lane is idle only in the last
+// partial round (no 32-wide padding of small sector blocks).  Four elements
+// per lane are advanced together for instruction-level parallelism.
+template <typename TX, typename TY, typename TZ, typename TA, int WARPS>
+__global__ void __launch_bounds__(32 * WARPS) chain_flat_kernel(const ChainEntry *__restrict__ E,
+                                                               const ChainGroup *__restrict__ G,
+                                                               int ngroups, uint64_t xb, uint64_t yb,
+                                                               uint64_t zb, uint64_t db) {
+  extern __shared__ __align__(16) unsigned char flat_smem[];
+  TA *base = reinterpret_cast<TA *>(flat_smem);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int gi = blockIdx.x * 8 + warp;
-  if (gi >= ngroups) return;  // warp-uniform; no block-level barrier below
+  const int gi = blockIdx.x * WARPS + warp;
+  if (gi >= ngroups) return;  // warp-uniform; only warp barriers below
+  TA(*Xs)[33] = reinterpret_cast<TA(*)[33]>(base + (size_t)warp * 4 * 32 * 33);
+  TA(*Ys)[33] = Xs + 32;
+  TA(*Ts)[33] = Xs + 64;
+  TA(*Zs)[33] = Xs + 96;
   const ChainGroup g = G[gi];
-  TA(*Xs)[17] = sm[warp][0];
-  TA(*Ys)[17] = sm[warp][1];
-  TA(*Ts)[17] = sm[warp][2];
-  TA(*Zs)[17] = sm[warp][3];
-  const int c = lane & 15, rbase = lane >> 4;
-  const int m = g.m, q = g.q;
-  TA acc[8];
+  const int m = g.m, q = g.q, mq = m * q;
+  TA acc[32];
 #pragma unroll
-  for (int i = 0; i < 8; ++i) acc[i] = 0;
+  for (int j = 0; j < 32; ++j) acc[j] = 0;
   for (int ei = g.first; ei < g.first + g.count; ++ei) {
     const ChainEntry e = E[ei];
     const bool xid = e.x == IDN, yid = e.y == IDN, zid = e.z == IDN;
@@ -168,94 +171,151 @@ __global__ void __launch_bounds__(256) chain_small_kernel(const ChainEntry *__re
     const TZ *Z = zid ? nullptr : tptr<TZ>(zb, e.z);
     const TA f = (TA)e.f;
     const int n = e.n, p = e.p;
-    const int pend = zid ? min(16, p) : p;
-    for (int p0 = 0; p0 < pend; p0 += 16) {
-      const int pc = min(16, pend - p0);
-      TA t[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) t[i] = 0;
+    for (int p0 = 0; p0 < p; p0 += 32) {
+      const int pc = min(32, p - p0);
+      const int mp = m * pc;
+      // ---- T (m x pc) into Ts
       if (xid || yid) {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int r = rbase + 2 * i;
-          if (r < m && c < pc) {
-            const int64_t Cc = p0 + c;
-            if (xid && yid) t[i] = (r == Cc) ? (TA)1 : (TA)0;
-            else if (xid) t[i] = (TA)Y[(int64_t)r * e.yrs + Cc * e.ycs];
-            else t[i] = (TA)X[(int64_t)r * e.xrs + Cc * e.xcs];
-          }
+        for (int t = lane; t < mp; t += 32) {
+          const int i = t / pc, c = t % pc;
+          TA v;
+          if (xid && yid) v = (i == p0 + c) ? (TA)1 : (TA)0;
+          else if (xid) v = (TA)Y[(int64_t)i * e.yrs + (int64_t)(p0 + c) * e.ycs];
+          else v = (TA)X[(int64_t)i * e.xrs + (int64_t)(p0 + c) * e.xcs];
+          Ts[i][c] = v;
         }
       } else {
-        for (int n0 = 0; n0 < n; n0 += 16) {
-          const int nc = min(16, n - n0);
-#pragma unroll
-          for (int j = 0; j < 8; ++j) {
-            const int idx = lane + 32 * j, i = idx >> 4, kk = idx & 15;
-            Xs[i][kk] = (i < m && kk < nc) ? (TA)X[(int64_t)i * e.xrs + (int64_t)(n0 + kk) * e.xcs] : (TA)0;
-            Ys[i][kk] = (i < nc && kk < pc) ? (TA)Y[(int64_t)(n0 + i) * e.yrs + (int64_t)(p0 + kk) * e.ycs] : (TA)0;
+        for (int t = lane; t < mp; t += 32) Ts[t / pc][t % pc] = 0;
+        for (int n0 = 0; n0 < n; n0 += 32) {
+          const int nc = min(32, n - n0);
+          for (int t = lane; t < m * nc; t += 32) {
+            const int i = t / nc, kk = t % nc;
+            Xs[i][kk] = (TA)X[(int64_t)i * e.xrs + (int64_t)(n0 + kk) * e.xcs];
+          }
+          for (int t = lane; t < nc * pc; t += 32) {
+            const int kk = t / pc, c = t % pc;
+            Ys[kk][c] = (TA)Y[(int64_t)(n0 + kk) * e.yrs + (int64_t)(p0 + c) * e.ycs];
           }
           __syncwarp();
-          if (c < pc) {
-            for (int kk = 0; kk < nc; ++kk) {
-              const TA y = Ys[kk][c];
+          for (int t0 = lane; t0 < mp; t0 += 128) {
+            int ii[4], cc[4];
+            TA s4[4];
 #pragma unroll
-              for (int i = 0; i < 8; ++i)
-                if (rbase + 2 * i < m) t[i] = fma(Xs[rbase + 2 * i][kk], y, t[i]);
+            for (int u = 0; u < 4; ++u) {
+              const int t = min(t0 + 32 * u, mp - 1);
+              ii[u] = t / pc;
+              cc[u] = t % pc;
+              s4[u] = 0;
             }
+            for (int kk = 0; kk < nc; ++kk) {
+#pragma unroll
+              for (int u = 0; u < 4; ++u) s4[u] = fma(Xs[ii[u]][kk], Ys[kk][cc[u]], s4[u]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+              if (t0 + 32 * u < mp) Ts[ii[u]][cc[u]] += s4[u];
           }
           __syncwarp();
         }
       }
+      __syncwarp();
+      // ---- acc += f T Z (or f T when Z is the identity)
       if (zid) {
 #pragma unroll
-        for (int i = 0; i < 8; ++i) acc[i] = fma(f, t[i], acc[i]);
+        for (int j = 0; j < 32; ++j) {
+          const int t = lane + 32 * j;
+          if (t < mq) {
+            const int i = t / q, c = t % q;
+            if (c >= p0 && c < p0 + pc) acc[j] = fma(f, Ts[i][c - p0], acc[j]);
+          }
+        }
       } else {
-#pragma unroll
-        for (int i = 0; i < 8; ++i) Ts[rbase + 2 * i][c] = t[i];
-#pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int idx = lane + 32 * j, kk = idx >> 4, jj = idx & 15;
-          Zs[kk][jj] = (kk < pc && jj < q) ? (TA)Z[(int64_t)(p0 + kk) * e.zrs + (int64_t)jj * e.zcs] : (TA)0;
+        for (int t = lane; t < pc * q; t += 32) {
+          const int kk = t / q, c = t % q;
+          Zs[kk][c] = (TA)Z[(int64_t)(p0 + kk) * e.zrs + (int64_t)c * e.zcs];
         }
         __syncwarp();
-        if (c < q) {
-          TA sacc[8];
 #pragma unroll
-          for (int i = 0; i < 8; ++i) sacc[i] = 0;
+        for (int j0 = 0; j0 < 32; j0 += 4) {
+          if (lane + 32 * j0 >= mq) break;
+          int ii[4], cc[4];
+          TA s4[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int t = min(lane + 32 * (j0 + u), mq - 1);
+            ii[u] = t / q;
+            cc[u] = t % q;
+            s4[u] = 0;
+          }
           for (int kk = 0; kk < pc; ++kk) {
-            const TA z = Zs[kk][c];
 #pragma unroll
-            for (int i = 0; i < 8; ++i)
-              if (rbase + 2 * i < m) sacc[i] = fma(Ts[rbase + 2 * i][kk], z, sacc[i]);
+            for (int u = 0; u < 4; ++u) s4[u] = fma(Ts[ii[u]][kk], Zs[kk][cc[u]], s4[u]);
           }
 #pragma unroll
-          for (int i = 0; i < 8; ++i) acc[i] = fma(f, sacc[i], acc[i]);
+          for (int u = 0; u < 4; ++u) acc[j0 + u] = fma(f, s4[u], acc[j0 + u]);
         }
-        __syncwarp();
       }
+      __syncwarp();
     }
   }
   double *D = const_cast<double *>(tptr<double>(db, g.d));
 #pragma unroll
-  for (int i = 0; i < 8; ++i) {
-    const int r = rbase + 2 * i;
-    if (r < m && c < q) D[(int64_t)r * g.drs + (int64_t)c * g.dcs] += (double)acc[i];
+  for (int j = 0; j < 32; ++j) {
+    const int t = lane + 32 * j;
+    if (t < mq) D[(int64_t)(t / q) * g.drs + (int64_t)(t % q) * g.dcs] += (double)acc[j];
   }
 }
 
-cudaError_t launch_chain_small_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
-                                    uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
+template <typename TX, typename TY, typename TZ, typename TA>
+static cudaError_t launch_flat(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb, uint64_t yb,
+                               uint64_t zb, uint64_t db, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
+  constexpr int WARPS = sizeof(TA) == 8 ? 4 : 8;
+  const int smem = WARPS * 4 * 32 * 33 * (int)sizeof(TA);
+  auto kern = chain_flat_kernel<TX, TY, TZ, TA, WARPS>;
+  cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (err != cudaSuccess) return err;
   COUNT(1);
-  chain_small_kernel<double, double, double, double><<<(ngroups + 7) / 8, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
+  kern<<<(ngroups + WARPS - 1) / WARPS, 32 * WARPS, smem, s>>>(e, g, ngroups, xb, yb, zb, db);
   return cudaGetLastError();
 }
 
-cudaError_t launch_chain_small_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups,
-                                      uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
-  if (ngroups <= 0) return cudaSuccess;
+cudaError_t launch_chain_flat_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
+                                   uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
+  return launch_flat<double, double, double, double>(e, g, ngroups, xb, yb, zb, db, s);
+}
+
+cudaError_t launch_chain_flat_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
+                                     uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
+  return launch_flat<float, double, float, float>(e, g, ngroups, xb, yb, zb, db, s);
+}
+
+// out[ red.d + ...] += sum over the task chunks of their partial blocks, in chunk order
+__global__ void reduce_partials_kernel(const ReduceGroup *__restrict__ R, int nred, int64_t total,
+                                       const double *__restrict__ scratch, double *out) {
+  for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+    int lo = 0, hi = nred - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (R[mid].e0 <= t) lo = mid; else hi = mid - 1;
+    }
+    const ReduceGroup r = R[lo];
+    const int64_t loc = t - r.e0;
+    const int i = (int)(loc / r.q), c = (int)(loc % r.q);
+    const int64_t mq = (int64_t)r.m * r.q;
+    double s = 0.0;
+    for (int k = 0; k < r.nsplit; ++k) s += scratch[r.soff + k * mq + loc];
+    out[r.d + (int64_t)i * r.drs + (int64_t)c * r.dcs] += s;
+  }
+}
+
+cudaError_t launch_reduce_partials(const ReduceGroup *r, int nred, int64_t total, const double *scratch,
+                                   double *out, cudaStream_t s) {
+  if (nred <= 0 || total <= 0) return cudaSuccess;
+  int64_t blocks = (total + 255) / 256;
+  if (blocks > 152 * 32) blocks = 152 * 32;
   COUNT(1);
-  chain_small_kernel<float, double, float, float><<<(ngroups + 7) / 8, 256, 0, s>>>(e, g, ngroups, xb, yb, zb, db);
+  reduce_partials_kernel<<<(int)blocks, 256, 0, s>>>(r, nred, total, scratch, out);
   return cudaGetLastError();
 }
 

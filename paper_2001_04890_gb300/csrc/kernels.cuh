@@ -30,11 +30,22 @@ cudaError_t launch_chain_fp64(const ChainEntry *e, const ChainGroup *g, int ngro
 // same task list with FP32 operators X, Z (FP64 psi in, FP64 sigma out, FP32 accumulation)
 cudaError_t launch_chain_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
                                 uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
-// one warp per output block for blocks of at most 16 x 16 (same entry semantics)
-cudaError_t launch_chain_small_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
-                                    uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
-cudaError_t launch_chain_small_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups,
-                                      uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+// one warp per output block of at most 32 x 32, lanes over flattened elements
+cudaError_t launch_chain_flat_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
+                                   uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+cudaError_t launch_chain_flat_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
+                                     uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+
+// Split task lists: every output block's entries are cut into chunks whose
+// partial blocks go to a scratch buffer; this adds them in chunk order.
+struct ReduceGroup {
+  int64_t e0;    // first flattened element of this block among all reduced elements
+  int64_t soff;  // scratch offset of chunk 0 (chunks are m*q apart)
+  uint64_t d;    // element offset of the output block
+  int drs, dcs, m, q, nsplit;
+};
+cudaError_t launch_reduce_partials(const ReduceGroup *r, int nred, int64_t total, const double *scratch,
+                                   double *out, cudaStream_t s);
 cudaError_t launch_to_f32(float *out, const double *in, int64_t n, cudaStream_t s);
 cudaError_t launch_lincomb_fp64(const LincombTask *t, int ntasks, int ntiles, cudaStream_t s);
 cudaError_t launch_diag_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups,
@@ -60,6 +71,15 @@ cudaError_t launch_gather_columns(double *O, const double *evecs, int n, const i
                                   int kept, cudaStream_t s);
 
 int dots_partial_blocks(int64_t n);
+
+// tensor-core H.psi chain (split-BF16 x3, FP32 operator copies, FP64 psi / sigma);
+// groups with m, q <= 128 whose entries all have n, p <= 128
+cudaError_t launch_chain_tc(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb, uint64_t yb,
+                            uint64_t zb, uint64_t db, int *status, cudaStream_t s);
+
+// tcgen05 self-test: C (128 x N) = A (128 x K) B^T (N x K), bf16 inputs, FP32 accumulation in TMEM
+cudaError_t launch_tc_selftest(const float *A, const float *B, float *C, int N, int K, int *status,
+                               cudaStream_t s);
 
 // number of kernels this library has launched in the process
 long long kernel_launch_count();

@@ -42,3 +42,33 @@ def test_mixed_energy_matches_fp64(L, N, M, k):
     e32, x32 = res[binding.PREC_FP32]
     assert abs(e32 - e64) < 1e-8, (e32, e64)
     assert abs(abs(x32 @ x64) - 1.0) < 1e-6
+
+
+def test_bf16x3_tensor_core_hpsi_matches_oracle():
+    """Blocks of 33..128 states run on tcgen05 (split-BF16 x3): ~2^-16 relative accuracy."""
+    from oracle import baseline
+    from oracle import dmrg as od
+    L, N, M = 10, 10, 300
+    k = (L - 2) // 2
+    h, v = workloads.integrals(L, seed=0)
+    ctx = binding.DMRG(h, v, N, 0, M, precision=binding.PREC_BF16X3)
+    workloads.grow_middle_bond(ctx, L, N // 2, N // 2, M, k, seed=0)
+    sec = ctx.block_sectors(0)
+    assert sec[:, 2].max() > 32  # some output blocks take the tensor-core kernel
+    wl = dict(name="l10", L=L, N=N, two_sz=0, M=M)
+    I, k2, lb, rb, nu, nd = baseline.middle_bond(wl)
+    hp = od.HPsi(I, k, lb, rb, nu, nd)
+    psi = workloads.gaussian(hp.dim, seed=7)
+    ref = hp.apply(psi)
+    got = ctx.hpsi(psi)
+    err = np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+    assert err < 2e-4, err
+    e, it = ctx.davidson(tol=1e-8, max_iter=400)
+    st = ctx.stats()
+    assert st["davidson_iters_lowp"] > 0
+    ctx.close()
+    ctx64 = binding.DMRG(h, v, N, 0, M, precision=binding.PREC_FP64)
+    workloads.grow_middle_bond(ctx64, L, N // 2, N // 2, M, k, seed=0)
+    e64, _ = ctx64.davidson(tol=1e-8, max_iter=400)
+    ctx64.close()
+    assert abs(e - e64) < 1e-8, (e, e64)
