@@ -1269,12 +1269,13 @@ static void davidson_core(dmrg_ctx *c, double tol, double floor_rel, int max_ite
       conv = true;
       break;
     }
-    // low-precision phase: stop when the residual stops improving (its attainable floor)
+    // low-precision phase: once the residual is within reach of the low-precision
+    // floor, stop when it no longer improves (further progress needs FP64 matvecs)
     if (floor_rel > 0.0) {
-      if (rnorm < 0.7 * best_r) {
+      if (rnorm < 0.5 * best_r) {
         best_r = rnorm;
         best_it = it;
-      } else if (it - best_it >= 8) {
+      } else if (rnorm < 1e-5 * std::fabs(theta) && it - best_it >= 10) {
         conv = true;
         break;
       }
