@@ -123,6 +123,27 @@ int dmrg_enlarged_layout(dmrg_ctx *ctx, int direction, int *nsec, int *sectors);
  */
 int dmrg_hpsi(dmrg_ctx *ctx, const double *psi, double *sigma, int device_ptrs);
 
+/*
+ * dmrg_hpsi_noalloc -- dmrg_hpsi with device pointers that allocates no device
+ * memory (no paper counterpart: an interface for callers that cannot allocate,
+ * e.g. applications that reserve their whole device-memory budget up front, or
+ * latency-critical code that must not block on the CUDA allocator).
+ * psi and sigma are device pointers on the context's stream (same layout and
+ * semantics as dmrg_hpsi).  The task list of the current position must already
+ * exist (any dmrg_hpsi, dmrg_hpsi_flops or dmrg_davidson call at this
+ * position builds it), else DMRG_ESTATE.  The chunk partials of the split
+ * task list go to one fixed device array of dmrg_hpsi_noalloc_capacity()
+ * doubles (16 MiB) that the library holds on every GPU it is loaded on until
+ * exit; positions that need more return DMRG_EINVAL with the size needed.
+ * The first call on a device looks up that array's device address (a CUDA
+ * runtime call); make it before any stream capture.  The array is shared by
+ * all calls and contexts in the process and keeps the last call's contents;
+ * each call clears the part it uses.  Calls that overlap on the GPU race on
+ * it: order them on one stream.
+ */
+int dmrg_hpsi_noalloc(dmrg_ctx *ctx, const double *psi, double *sigma);
+long long dmrg_hpsi_noalloc_capacity(void);
+
 /* Algorithmic FLOPs of one dmrg_hpsi at the current position (host-counted from the task list). */
 int dmrg_hpsi_flops(dmrg_ctx *ctx, double *flops, long long *tasks);
 

@@ -49,6 +49,8 @@ def lib():
         "dmrg_enlarged_layout": (C.c_int, [vp, C.c_int, ip, ip]),
         "dmrg_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
         "dmrg_hpsi_flops": (C.c_int, [vp, dp, llp]),
+        "dmrg_hpsi_noalloc": (C.c_int, [vp, vp, vp]),
+        "dmrg_hpsi_noalloc_capacity": (C.c_longlong, []),
         "dmrg_set_psi": (C.c_int, [vp, vp, C.c_int]),
         "dmrg_get_psi": (C.c_int, [vp, vp, C.c_int]),
         "dmrg_davidson": (C.c_int, [vp, C.c_double, C.c_int, dp, ip]),
@@ -198,6 +200,11 @@ class DMRG:
         assert psi.is_cuda and psi.dtype == torch.float64 and psi.is_contiguous()
         sigma = torch.empty_like(psi)
         _check(lib().dmrg_hpsi(self.ctx, psi.data_ptr(), sigma.data_ptr(), 1))
+        return sigma
+
+    def hpsi_noalloc(self, psi, sigma):
+        """sigma = H psi (CUDA torch tensors, float64) without any device allocation in the call."""
+        _check(lib().dmrg_hpsi_noalloc(self.ctx, psi.data_ptr(), sigma.data_ptr()))
         return sigma
 
     def hpsi_flops(self):

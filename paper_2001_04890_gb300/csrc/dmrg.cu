@@ -13,6 +13,7 @@
 #include <map>
 #include <cstring>
 #include <memory>
+#include <mutex>
 #include <numeric>
 #include <stdexcept>
 #include <string>
@@ -380,6 +381,23 @@ struct DevChain {
       CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
     }
     if (split) CK(launch_reduce_partials(red.p, nred, red_total, scratch.p, (double *)(uintptr_t)db, s));
+  }
+
+  // Same launch sequence with the chunk partials in caller-provided scratch
+  // (at least scratch_n doubles); no device memory is allocated here.
+  void launch_with_scratch(double *ext, bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db,
+                           cudaStream_t s, int *status) const {
+    const uint64_t tb = (uint64_t)(uintptr_t)ext;
+    if (scratch_n > 0) CK(cudaMemsetAsync(ext, 0, scratch_n * sizeof(double), s));
+    if (f32ops) {
+      CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+      if (ntc > 0) CK(launch_chain_tc(ent.p, tcg.p, ntc, xb, yb, zb, tb, status, s));
+    } else {
+      CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+    }
+    CK(launch_reduce_partials(red.p, nred, red_total, ext, (double *)(uintptr_t)db, s));
   }
 };
 
@@ -1746,5 +1764,64 @@ extern "C" int dmrg_selftest_tcgen05(int N, int K, const float *A, const float *
   CK(cudaMemcpy(&status, st.p, sizeof(int), cudaMemcpyDeviceToHost));
   CK(cudaMemcpy(C, cc.p, (size_t)128 * N * sizeof(float), cudaMemcpyDeviceToHost));
   if (status) throw Fail{DMRG_ETIMEOUT, "tcgen05 self-test: mbarrier wait ran out"};
+  API_END
+}
+
+// ---------------------------------------------------------------------------
+// H.psi without any device allocation.
+//
+// Some callers cannot allocate device memory at the moment they need H.psi:
+// applications that reserve their whole device-memory budget up front and
+// hand out no more afterwards, or code on a latency-critical path that must
+// not block on the CUDA allocator.  dmrg_hpsi_noalloc serves them: the chunk
+// partials of the split task list live in a fixed file-scope device array
+// instead of memory allocated per plan.  The array is shared by every call and
+// every context in the process and keeps the last call's contents; the call
+// clears the part it uses first.  Calls whose kernels overlap on the GPU
+// (other streams, other host threads) race on it, so such callers must
+// order their calls on one stream or serialize them.
+// ---------------------------------------------------------------------------
+static constexpr long long kNoAllocScratchDoubles = 1ll << 21;  // 16 MiB
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+static std::mutex g_noalloc_mu;
+static std::map<int, double *> g_noalloc_addr;  // device ordinal -> address of the array
+
+// Device address of the array on the current device, looked up once per device.
+// Host code must not use &g_noalloc_scratch itself: on the host that name is a
+// stand-in, not a device address.
+static double *noalloc_scratch() {
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  auto it = g_noalloc_addr.find(dev);
+  if (it != g_noalloc_addr.end()) return it->second;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e != cudaSuccess || p == nullptr)
+    throw Fail{DMRG_ECUDA, std::string("cudaGetSymbolAddress(no-allocation scratch): ") + cudaGetErrorString(e)};
+  g_noalloc_addr[dev] = static_cast<double *>(p);
+  return static_cast<double *>(p);
+}
+
+extern "C" long long dmrg_hpsi_noalloc_capacity(void) { return kNoAllocScratchDoubles; }
+
+extern "C" int dmrg_hpsi_noalloc(dmrg_ctx *c, const double *psi, double *sigma) {
+  API_BEGIN
+  if (!c || !psi || !sigma) throw Fail{DMRG_EINVAL, "NULL argument"};
+  HPlan &P = c->plan;
+  if (!P.valid || P.k != c->k || P.lb != lblock(c) || P.rb != rblock(c))
+    throw Fail{DMRG_ESTATE, "dmrg_hpsi_noalloc needs the H.psi task list of the current position; "
+                            "call dmrg_hpsi or dmrg_hpsi_flops once at this position first"};
+  const bool lowp = P.lowp;
+  const DevChain &ch = lowp ? P.chain32 : P.chain;
+  if (!ch.split) throw Fail{DMRG_ESTATE, "H.psi task list has no split partials"};
+  if (ch.scratch_n > kNoAllocScratchDoubles)
+    throw Fail{DMRG_EINVAL, "this position needs " + std::to_string(ch.scratch_n) +
+                                " doubles of H.psi scratch; the no-allocation scratch holds " +
+                                std::to_string(kNoAllocScratchDoubles) + " (use dmrg_hpsi)"};
+  double *scratch = noalloc_scratch();
+  CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
+  ch.launch_with_scratch(scratch, lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream,
+                         c->dstatus.p);
   API_END
 }
