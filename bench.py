@@ -30,6 +30,14 @@ WORKLOADS = {
     # FP64 two-site DMRG, L=24, N=24, Sz=0, M=512, Davidson tol 1e-8, middle bond
     "c2": dict(name="L24_N24_Sz0_M512_fp64_middle_bond", L=24, N=24, two_sz=0, M=512, tol=1e-8,
                precision=0),
+    # mixed-precision workload: L=40, N=40, Sz=0, M=2000 (middle bond)
+    "c3": dict(name="L40_N40_Sz0_M2000_middle_bond", L=40, N=40, two_sz=0, M=2000, tol=1e-8,
+               precision=1),
+    # FeMoco-shaped: L=76, N=113, 2Sz=1, M=3000 / 6000 (middle bond)
+    "c5a": dict(name="L76_N113_Sz1_M3000_middle_bond", L=76, N=113, two_sz=1, M=3000, tol=1e-8,
+                precision=1),
+    "c5b": dict(name="L76_N113_Sz1_M6000_middle_bond", L=76, N=113, two_sz=1, M=6000, tol=1e-8,
+                precision=1),
     # small case: L=8, N=8, M=64
     "c1": dict(name="L8_N8_Sz0_M64_fp64_middle_bond", L=8, N=8, two_sz=0, M=64, tol=1e-9,
                precision=0),
@@ -194,7 +202,9 @@ def profile_hpsi(wl, precision, ncalls):
     from paper_2001_04890_gb300 import workloads
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
     ctx, k = _setup(wl, precision, stream, 0)
+    setup_s = time.perf_counter() - t0
     _, dim = ctx.psi_layout()
     psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
     ctx.hpsi(psi)  # builds the task list and temporaries outside the range
@@ -206,9 +216,61 @@ def profile_hpsi(wl, precision, ncalls):
     torch.cuda.nvtx.range_pop()
     st = ctx.stats()
     print(json.dumps({"profile": wl["name"], "precision": precision, "hpsi_calls": ncalls,
+                      "setup_s": setup_s, "psi_dim": dim,
                       "hpsi_ms_avg": st["hpsi_ms"] / max(st["hpsi_calls"], 1),
-                      "gflop_per_hpsi": ctx.hpsi_flops()[0] / 1e9}))
+                      "gflop_per_hpsi": ctx.hpsi_flops()[0] / 1e9}), flush=True)
     ctx.close()
+
+
+def large_workload(wl, iters=4):
+    """Middle bond of a large workload: one context per precision on the same bases.
+
+    Reports the block-growth time, H.psi time and TFLOP/s per precision, a few
+    Davidson iterations (s/iter) and one renormalization, plus the relative
+    difference of each low-precision sigma from the FP64 sigma.
+    """
+    import torch
+    from paper_2001_04890_gb300 import binding, workloads
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    out = {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"], "M": wl["M"]}
+    sig64 = None
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16x3", 2)):
+        t0 = time.perf_counter()
+        ctx, k = _setup(wl, prec, stream, 0)
+        setup_s = time.perf_counter() - t0
+        _, dim = ctx.psi_layout()
+        psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
+        t0 = time.perf_counter()
+        sig = ctx.hpsi(psi)  # builds task list + temporaries
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        ctx.stats(reset=True)
+        for _ in range(3):
+            sig = ctx.hpsi(psi)
+        st = ctx.stats(reset=True)
+        fl, tasks = ctx.hpsi_flops()
+        ms = st["hpsi_ms"] / max(st["hpsi_calls"], 1)
+        r = {"setup_s": setup_s, "plan_s": plan_s, "hpsi_ms": ms, "hpsi_tflops": fl / (ms * 1e-3) / 1e12,
+             "gflop_per_hpsi": fl / 1e9, "tasks": tasks, "psi_dim": dim}
+        s = sig.double().cpu().numpy()
+        if sig64 is None:
+            sig64 = s
+        else:
+            r["rel_diff_vs_fp64"] = float(np.max(np.abs(s - sig64)) / np.max(np.abs(sig64)))
+        t0 = time.perf_counter()
+        ctx.set_psi(psi)
+        e, it = ctx.davidson(tol=1e-14, max_iter=iters, allow_noconv=True)
+        torch.cuda.synchronize()
+        r["davidson_s_per_iter"] = (time.perf_counter() - t0) / max(it, 1)
+        t0 = time.perf_counter()
+        dw, kept = ctx.renormalize(+1)
+        torch.cuda.synchronize()
+        r["renormalize_s"] = time.perf_counter() - t0
+        out[name] = r
+        print(json.dumps({name: r}), flush=True)
+        ctx.close()
+    return out
 
 
 def main():
@@ -222,7 +284,9 @@ def main():
     ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-matvec comparison run")
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="setup, then N H.psi calls in an NVTX range 'hpsi' (for ncu); no JSON line")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--large", action="store_true",
+                    help="middle-bond measurement of a large workload in every precision (JSON lines)")
     args = ap.parse_args()
     wl = WORKLOADS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
@@ -234,7 +298,10 @@ def main():
         line = baseline.reference_line(wl, args.steps, args.warmup, METRIC, _flops_fn(wl))
         print(json.dumps(line))
         return 0
-    prec = {"fp64": 0, "fp32": 1}[args.precision]
+    prec = {"fp64": 0, "fp32": 1, "bf16x3": 2}[args.precision]
+    if args.large:
+        print(json.dumps(large_workload(wl)))
+        return 0
     if args.profile_hpsi:
         profile_hpsi(wl, prec, args.profile_hpsi)
         return 0
