@@ -285,10 +285,14 @@ def main():
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="setup, then N H.psi calls in an NVTX range 'hpsi' (for ncu); no JSON line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--M", type=int, default=0, help="override the workload's bond dimension (profiling)")
     ap.add_argument("--large", action="store_true",
                     help="middle-bond measurement of a large workload in every precision (JSON lines)")
     args = ap.parse_args()
-    wl = WORKLOADS[args.workload]
+    wl = dict(WORKLOADS[args.workload])
+    if args.M:
+        wl["M"] = args.M
+        wl["name"] = wl["name"].replace(f"M{WORKLOADS[args.workload]['M']}", f"M{args.M}")
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
