@@ -136,6 +136,8 @@ __global__ void __launch_bounds__(128) chain_tc_kernel(const ChainEntry *__restr
     tc::tmem_relinquish();
   }
   if (tid == 0) tc::mbar_init(bar, 1);
+  // zero all operand tiles once: every element the tensor core reads is finite
+  for (int i = tid; i < 4 * TC_TILE / 16; i += 128) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
@@ -176,12 +178,18 @@ __global__ void __launch_bounds__(128) chain_tc_kernel(const ChainEntry *__restr
       bool t_first = true;
       for (int n0 = 0; n0 < n && !failed; n0 += TC_KC) {
         const int nc = min(TC_KC, n - n0);
-        for (int idx = tid; idx < 128 * TC_KC; idx += 128) {
-          const int r = idx / TC_KC, k = idx % TC_KC;
-          const float x = (r < m && k < nc) ? X[(int64_t)r * e.xrs + (int64_t)(n0 + k) * e.xcs] : 0.f;
+        const int kc16 = (nc + 15) & ~15;  // K padding up to the MMA step must be zero
+        // A rows < m (rows >= m may hold stale finite data: they only feed output rows >= m)
+        for (int idx = tid; idx < m * kc16; idx += 128) {
+          const int r = idx / kc16, k = idx % kc16;
+          const float x = (k < nc) ? X[(int64_t)r * e.xrs + (int64_t)(n0 + k) * e.xcs] : 0.f;
           put_split(Ahi, Alo, r, k, x);
-          const float y = (r < p && k < nc) ? (float)Y[(int64_t)(n0 + k) * e.yrs + (int64_t)r * e.ycs] : 0.f;
-          put_split(Bhi, Blo, r, k, y);  // B row j = column j of Y
+        }
+        // B row j = column j of Y, j < p (consecutive threads take consecutive j)
+        for (int idx = tid; idx < p * kc16; idx += 128) {
+          const int k = idx / p, j = idx % p;
+          const float y = (k < nc) ? (float)Y[(int64_t)(n0 + k) * e.yrs + (int64_t)j * e.ycs] : 0.f;
+          put_split(Bhi, Blo, j, k, y);
         }
         publish();
         if (tid == 0) issue3(tT, sAhi, sAlo, sBhi, sBlo, (nc + 15) / 16, tc::idesc_bf16(128, p16), t_first);
@@ -192,28 +200,33 @@ __global__ void __launch_bounds__(128) chain_tc_kernel(const ChainEntry *__restr
     // ---- stage 2: D += (f T) Z
     for (int p0 = 0; p0 < p && !failed; p0 += TC_KC) {
       const int pc = min(TC_KC, p - p0);
+      const int pc16 = (pc + 15) & ~15;
       if (xid) {
-        for (int k = 0; k < TC_KC; ++k) {
-          const float t = (row < m && k < pc) ? f * (float)Y[(int64_t)row * e.yrs + (int64_t)(p0 + k) * e.ycs] : 0.f;
-          put_split(Ahi, Alo, row, k, t);
+        if (row < m) {
+          for (int k = 0; k < pc16; ++k) {
+            const float t = (k < pc) ? f * (float)Y[(int64_t)row * e.yrs + (int64_t)(p0 + k) * e.ycs] : 0.f;
+            put_split(Ahi, Alo, row, k, t);
+          }
         }
       } else {
-        for (int c0 = 0; c0 < TC_KC; c0 += 16) {
+        for (int c0 = 0; c0 < pc16; c0 += 16) {
           float v[16];
-          if (p0 + c0 < p16) tc::tmem_ld16(tT + lane_off + (uint32_t)(p0 + c0), v);
-          else for (int i = 0; i < 16; ++i) v[i] = 0.f;
+          tc::tmem_ld16(tT + lane_off + (uint32_t)(p0 + c0), v);
+          if (row < m) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int k = c0 + i;
-            put_split(Ahi, Alo, row, k, (row < m && k < pc) ? f * v[i] : 0.f);
+            for (int i = 0; i < 16; ++i) {
+              const int k = c0 + i;
+              put_split(Ahi, Alo, row, k, (k < pc) ? f * v[i] : 0.f);
+            }
           }
         }
       }
-      for (int idx = tid; idx < 128 * TC_KC; idx += 128) {
-        const int j = idx / TC_KC, k = idx % TC_KC;
+      // B row j = column j of Z, j < q (consecutive threads take consecutive j)
+      for (int idx = tid; idx < q * pc16; idx += 128) {
+        const int k = idx / q, j = idx % q;
         float z = 0.f;
-        if (j < q && k < pc) z = zid ? ((p0 + k == j) ? 1.f : 0.f) : Z[(int64_t)(p0 + k) * e.zrs + (int64_t)j * e.zcs];
-        put_split(Bhi, Blo, j, k, z);  // B row j = column j of Z
+        if (k < pc) z = zid ? ((p0 + k == j) ? 1.f : 0.f) : Z[(int64_t)(p0 + k) * e.zrs + (int64_t)j * e.zcs];
+        put_split(Bhi, Blo, j, k, z);
       }
       publish();
       if (tid == 0) issue3(tD, sAhi, sAlo, sBhi, sBlo, (pc + 15) / 16, tc::idesc_bf16(128, q16), d_first);
