@@ -38,6 +38,9 @@ WORKLOADS = {
                 precision=1),
     "c5b": dict(name="L76_N113_Sz1_M6000_middle_bond", L=76, N=113, two_sz=1, M=6000, tol=1e-8,
                 precision=1),
+    # batched: 256 independent instances (seeds 0..255), L in 10..20, N=L, M in 64..256
+    "c4": dict(name="batched_256_L10-20_M64-256_middle_bonds", L=0, N=0, two_sz=0, M=0, tol=1e-8,
+               precision=1, instances=256),
     # small case: L=8, N=8, M=64
     "c1": dict(name="L8_N8_Sz0_M64_fp64_middle_bond", L=8, N=8, two_sz=0, M=64, tol=1e-9,
                precision=0),
@@ -222,6 +225,89 @@ def profile_hpsi(wl, precision, ncalls):
     ctx.close()
 
 
+def batched_workload(args, wl):
+    """Batched instances: one grouped, CUDA-graph-replayed H.psi over all middle bonds.
+
+    Reports the aggregate H.psi TFLOP/s of the grouped launch and of one launch
+    sequence per instance (same work), per-instance Davidson s/iter and, for
+    the first 16 instances, |dE| of the mixed run against FP64.
+    """
+    import torch
+    from paper_2001_04890_gb300 import binding, workloads
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    n = wl["instances"]
+    out = {"workload": wl["name"], "instances": n}
+    res = {}
+    for name, prec in (("fp32", 1), ("bf16x3", 2)):
+        ctxs = []
+        t0 = time.perf_counter()
+        for seed in range(n):
+            L, M, h, v = workloads.batched_instance(seed)
+            c = binding.DMRG(h, v, L, 0, M, prec, stream=stream.cuda_stream)
+            workloads.grow_middle_bond(c, L, L // 2, L // 2, M, (L - 2) // 2, seed=seed)
+            ctxs.append(c)
+        setup_s = time.perf_counter() - t0
+        batch = binding.Batch(ctxs)
+        with torch.cuda.stream(stream):
+            x = torch.from_numpy(workloads.gaussian(batch.offsets[-1], seed=1)).cuda()
+        stream.synchronize()
+        for _ in range(args.warmup):
+            batch.hpsi(x)
+        stream.synchronize()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(args.steps):
+            batch.hpsi(x)
+        b.record(stream)
+        stream.synchronize()
+        t_batch = a.elapsed_time(b) / args.steps
+        xs = [x[batch.offsets[i]:batch.offsets[i + 1]].clone() for i in range(n)]
+        for i, c in enumerate(ctxs):
+            c.hpsi(xs[i])
+        stream.synchronize()
+        a.record(stream)
+        for _ in range(args.steps):
+            for i, c in enumerate(ctxs):
+                c.hpsi(xs[i])
+        b.record(stream)
+        stream.synchronize()
+        t_seq = a.elapsed_time(b) / args.steps
+        t0 = time.perf_counter()
+        its = 0
+        energies = []
+        for c in ctxs:
+            e, it = c.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
+            its += it
+            energies.append(e)
+        dav_s = time.perf_counter() - t0
+        res[name] = {"setup_s": setup_s, "batched_hpsi_ms": t_batch,
+                     "batched_hpsi_tflops": batch.flops / (t_batch * 1e-3) / 1e12,
+                     "per_instance_hpsi_ms": t_seq,
+                     "per_instance_hpsi_tflops": batch.flops / (t_seq * 1e-3) / 1e12,
+                     "gflop_per_batched_hpsi": batch.flops / 1e9,
+                     "davidson_s_per_iter_avg": dav_s / max(its, 1), "davidson_iters_total": its,
+                     "energies_head": energies[:16]}
+        print(json.dumps({name: res[name]}), flush=True)
+        batch.close()
+        for c in ctxs:
+            c.close()
+    # FP64 reference energies for the first 16 instances
+    e64 = []
+    for seed in range(16):
+        L, M, h, v = workloads.batched_instance(seed)
+        c = binding.DMRG(h, v, L, 0, M, 0, stream=stream.cuda_stream)
+        workloads.grow_middle_bond(c, L, L // 2, L // 2, M, (L - 2) // 2, seed=seed)
+        e, _ = c.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
+        e64.append(e)
+        c.close()
+    for name in res:
+        res[name]["max_abs_dE_vs_fp64_first16"] = float(np.max(np.abs(np.array(res[name]["energies_head"]) - e64)))
+        del res[name]["energies_head"]
+    out.update(res)
+    return out
+
+
 def large_workload(wl, iters=4):
     """Middle bond of a large workload: one context per precision on the same bases.
 
@@ -303,6 +389,9 @@ def main():
         print(json.dumps(line))
         return 0
     prec = {"fp64": 0, "fp32": 1, "bf16x3": 2}[args.precision]
+    if args.workload == "c4":
+        print(json.dumps(batched_workload(args, wl)))
+        return 0
     if args.large:
         print(json.dumps(large_workload(wl)))
         return 0

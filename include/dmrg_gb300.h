@@ -210,6 +210,23 @@ int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
 int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, long long *n);
 
 /*
+ * Batched independent instances (many problems of uneven L and M, e.g. one per
+ * integral set): the H.psi task lists of n contexts, each at its current
+ * position, run as one task list over concatenated psi / sigma vectors; every
+ * kernel class is one grouped launch for all instances, captured once into a
+ * CUDA graph and replayed (Sec. 2.2.1 task list, merged over instances).
+ * All contexts must share one stream and the same precision class; they must
+ * not change position while the batch lives.  dmrg_batch_layout gives the n+1
+ * offsets of each instance's psi in the concatenated vector (dmrg_psi_layout
+ * order inside) and the summed algorithmic FLOPs of one batched H.psi.
+ */
+typedef struct dmrg_batch dmrg_batch;
+int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out);
+int dmrg_batch_layout(dmrg_batch *batch, long long *offsets, double *flops);
+int dmrg_batch_hpsi(dmrg_batch *batch, const double *psi, double *sigma, int device_ptrs);
+int dmrg_batch_free(dmrg_batch *batch);
+
+/*
  * dmrg_stats -- counters since context creation or the last reset (host outputs,
  * any may be NULL): total device time of the H.psi kernel launches (CUDA events
  * recorded on the context stream around each launch), number of H.psi calls,

@@ -62,6 +62,10 @@ def lib():
                                            C.c_int, ip, dp, llp]),
         "dmrg_selftest_tcgen05": (C.c_int, [C.c_int, C.c_int, C.POINTER(C.c_float), C.POINTER(C.c_float),
                                             C.POINTER(C.c_float)]),
+        "dmrg_batch_create": (C.c_int, [C.c_int, C.POINTER(vp), C.POINTER(vp)]),
+        "dmrg_batch_layout": (C.c_int, [vp, llp, dp]),
+        "dmrg_batch_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
+        "dmrg_batch_free": (C.c_int, [vp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -271,3 +275,42 @@ class DMRG:
         out = np.zeros(n.value)
         _check(lib().dmrg_block_op(self.ctx, side, kind, i, j, _dptr(out), C.byref(n)))
         return out
+
+
+class Batch:
+    """Grouped, graph-replayed H.psi over several contexts (each at its current position)."""
+
+    def __init__(self, ctxs):
+        arr = (C.c_void_p * len(ctxs))(*[c.ctx.value for c in ctxs])
+        h = C.c_void_p()
+        _check(lib().dmrg_batch_create(len(ctxs), arr, C.byref(h)))
+        self.h, self.n = h, len(ctxs)
+        self._ctxs = ctxs
+        off = (C.c_longlong * (self.n + 1))()
+        fl = C.c_double()
+        _check(lib().dmrg_batch_layout(h, off, C.byref(fl)))
+        self.offsets = list(off)
+        self.flops = fl.value
+
+    def hpsi(self, psi):
+        """psi: concatenated float64 vector (numpy, or CUDA torch tensor)."""
+        if isinstance(psi, np.ndarray):
+            psi = _f64(psi)
+            out = np.empty_like(psi)
+            _check(lib().dmrg_batch_hpsi(self.h, psi.ctypes.data, out.ctypes.data, 0))
+            return out
+        import torch
+        out = torch.empty_like(psi)
+        _check(lib().dmrg_batch_hpsi(self.h, psi.data_ptr(), out.data_ptr(), 1))
+        return out
+
+    def close(self):
+        if getattr(self, "h", None):
+            lib().dmrg_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

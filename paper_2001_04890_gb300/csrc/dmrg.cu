@@ -283,6 +283,7 @@ struct DevChain {
   DBuf<ReduceGroup> red;
   DBuf<double> scratch;
   int nall = 0, nbig = 0, nflat = 0, ntc = 0, ntiles = 0, nred = 0;
+  int64_t nent = 0;
   int64_t red_total = 0, scratch_n = 0;
   bool split = false;
 
@@ -352,6 +353,7 @@ struct DevChain {
       e0 += mq;
     }
     ent.upload(CL.flat, s);
+    nent = (int64_t)CL.flat.size();
     all.upload(CL.grp, s);
     big.upload(vb, s);
     flat.upload(vf, s);
@@ -1823,5 +1825,122 @@ extern "C" int dmrg_hpsi_noalloc(dmrg_ctx *c, const double *psi, double *sigma) 
   CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
   ch.launch_with_scratch(scratch, lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream,
                          c->dstatus.p);
+  API_END
+}
+
+// ---------------------------------------------------------------------------
+// Batched independent instances (many small problems of uneven L and M): the
+// H.psi task lists of all instances, each at its current position, are
+// concatenated into one task list over one concatenated psi / sigma, so each
+// kernel class runs as a single grouped launch for every instance; the launch
+// sequence is captured once into a CUDA graph and replayed.
+// ---------------------------------------------------------------------------
+struct dmrg_batch {
+  std::vector<dmrg_ctx *> ctx;
+  std::vector<long long> off;  // n + 1 offsets into the concatenated vectors
+  cudaStream_t stream = nullptr;
+  bool lowp = false;
+  DevChain chain;
+  DBuf<double> psi, sigma;
+  double flops = 0.0;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  long long graph_kernels = 0;
+  ~dmrg_batch() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (graph) cudaGraphDestroy(graph);
+  }
+};
+
+extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out) {
+  API_BEGIN
+  if (n < 1 || !ctxs || !out) throw Fail{DMRG_EINVAL, "bad arguments"};
+  *out = nullptr;
+  auto b = std::make_unique<dmrg_batch>();
+  b->stream = ctxs[0]->stream;
+  b->off.push_back(0);
+  ChainList CL;
+  for (int i = 0; i < n; ++i) {
+    dmrg_ctx *c = ctxs[i];
+    if (!c) throw Fail{DMRG_EINVAL, "NULL context in batch"};
+    if (c->stream != b->stream) throw Fail{DMRG_EINVAL, "batched contexts must share one stream"};
+    if ((c->prec != DMRG_PREC_FP64) != (ctxs[0]->prec != DMRG_PREC_FP64))
+      throw Fail{DMRG_EINVAL, "batched contexts must share the working precision class"};
+    build_hplan(c);
+    const HPlan &P = c->plan;
+    const DevChain &src = P.lowp ? P.chain32 : P.chain;
+    std::vector<ChainEntry> ent((size_t)src.nent);
+    std::vector<ChainGroup> grp((size_t)src.nall);
+    if (!ent.empty()) CK(cudaMemcpy(ent.data(), src.ent.p, ent.size() * sizeof(ChainEntry), cudaMemcpyDeviceToHost));
+    if (!grp.empty()) CK(cudaMemcpy(grp.data(), src.all.p, grp.size() * sizeof(ChainGroup), cudaMemcpyDeviceToHost));
+    const long long o = b->off.back();
+    const int base = (int)CL.flat.size();
+    for (auto e : ent) {
+      e.y += (uint64_t)o;
+      CL.flat.push_back(e);
+    }
+    for (auto g : grp) {
+      g.d += (uint64_t)o;
+      g.first += base;
+      CL.grp.push_back(g);
+    }
+    b->off.push_back(o + P.psi.dim);
+    b->flops += P.flops;
+    b->ctx.push_back(c);
+    b->lowp = P.lowp;
+  }
+  const bool tc = ctxs[0]->prec == DMRG_PREC_BF16X3;
+  b->chain.upload(CL, b->stream, tc, true);
+  b->psi.alloc((size_t)std::max<long long>(b->off.back(), 1));
+  b->sigma.alloc((size_t)std::max<long long>(b->off.back(), 1));
+  CK(cudaStreamSynchronize(b->stream));
+  *out = b.release();
+  API_END
+}
+
+extern "C" int dmrg_batch_free(dmrg_batch *b) {
+  if (!b) return DMRG_OK;
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  delete b;
+  return DMRG_OK;
+}
+
+extern "C" int dmrg_batch_layout(dmrg_batch *b, long long *offsets, double *flops) {
+  API_BEGIN
+  if (!b) throw Fail{DMRG_EINVAL, "batch is NULL"};
+  if (offsets) std::copy(b->off.begin(), b->off.end(), offsets);
+  if (flops) *flops = b->flops;
+  API_END
+}
+
+extern "C" int dmrg_batch_hpsi(dmrg_batch *b, const double *psi, double *sigma, int device_ptrs) {
+  API_BEGIN
+  if (!b || !psi || !sigma) throw Fail{DMRG_EINVAL, "NULL argument"};
+  const int64_t n = b->off.back();
+  cudaStream_t s = b->stream;
+  CK(cudaMemcpyAsync(b->psi.p, psi, n * sizeof(double),
+                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+  int *status = b->ctx[0]->dstatus.p;
+  auto body = [&]() {
+    CK(cudaMemsetAsync(b->sigma.p, 0, n * sizeof(double), s));
+    b->chain.launch(b->lowp, 0, (uint64_t)(uintptr_t)b->psi.p, 0, (uint64_t)(uintptr_t)b->sigma.p, s, status);
+  };
+  if (!b->exec) {
+    body();  // first call runs directly (and sets kernel attributes), then captures the sequence
+    const long long before = kernel_launch_count();
+    CK(cudaStreamBeginCapture(s, cudaStreamCaptureModeRelaxed));
+    body();
+    CK(cudaStreamEndCapture(s, &b->graph));
+    CK(cudaGraphInstantiate(&b->exec, b->graph, 0));
+    b->graph_kernels = kernel_launch_count() - before;
+    add_kernel_launches(-b->graph_kernels);  // captured, not launched
+  } else {
+    CK(cudaGraphLaunch(b->exec, s));
+    add_kernel_launches(b->graph_kernels);
+  }
+  CK(cudaMemcpyAsync(sigma, b->sigma.p, n * sizeof(double),
+                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+  if (!device_ptrs) CK(cudaStreamSynchronize(s));
+  check_status(b->ctx[0]);
   API_END
 }

@@ -23,6 +23,7 @@ namespace dmrg {
 
 static std::atomic<long long> g_launches{0};
 long long kernel_launch_count() { return g_launches.load(); }
+void add_kernel_launches(long long n) { g_launches.fetch_add(n); }
 #define COUNT(n) g_launches.fetch_add(n)
 
 __device__ __forceinline__ const double *dptr(uint64_t base, uint64_t off) {

@@ -83,5 +83,6 @@ cudaError_t launch_tc_selftest(const float *A, const float *B, float *C, int N, 
 
 // number of kernels this library has launched in the process
 long long kernel_launch_count();
+void add_kernel_launches(long long n);  // kernels run by CUDA-graph replays
 
 }  // namespace dmrg
