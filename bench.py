@@ -244,8 +244,9 @@ def batched_workload(args, wl):
         t0 = time.perf_counter()
         for seed in range(n):
             L, M, h, v = workloads.batched_instance(seed)
-            c = binding.DMRG(h, v, L, 0, M, prec, stream=stream.cuda_stream)
-            workloads.grow_middle_bond(c, L, L // 2, L // 2, M, (L - 2) // 2, seed=seed)
+            tsz = L % 2  # N = L; odd N has no Sz = 0 sector: lowest |Sz| (2Sz = 1)
+            c = binding.DMRG(h, v, L, tsz, M, prec, stream=stream.cuda_stream)
+            workloads.grow_middle_bond(c, L, (L + tsz) // 2, (L - tsz) // 2, M, (L - 2) // 2, seed=seed)
             ctxs.append(c)
         setup_s = time.perf_counter() - t0
         batch = binding.Batch(ctxs)
@@ -296,8 +297,9 @@ def batched_workload(args, wl):
     e64 = []
     for seed in range(16):
         L, M, h, v = workloads.batched_instance(seed)
-        c = binding.DMRG(h, v, L, 0, M, 0, stream=stream.cuda_stream)
-        workloads.grow_middle_bond(c, L, L // 2, L // 2, M, (L - 2) // 2, seed=seed)
+        tsz = L % 2
+        c = binding.DMRG(h, v, L, tsz, M, 0, stream=stream.cuda_stream)
+        workloads.grow_middle_bond(c, L, (L + tsz) // 2, (L - tsz) // 2, M, (L - 2) // 2, seed=seed)
         e, _ = c.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
         e64.append(e)
         c.close()
