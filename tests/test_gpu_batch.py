@@ -17,8 +17,9 @@ def test_batched_hpsi_equals_per_instance(prec):
     ctxs = []
     for seed, (L, M) in enumerate([(8, 40), (10, 64), (7, 24), (12, 80)]):
         h, v = workloads.integrals(L, seed=seed)
-        c = binding.DMRG(h, v, L, 0, M, precision=prec)
-        workloads.grow_middle_bond(c, L, L // 2, L // 2, M, (L - 2) // 2, seed=seed)
+        tsz = L % 2  # odd N: lowest |Sz|
+        c = binding.DMRG(h, v, L, tsz, M, precision=prec)
+        workloads.grow_middle_bond(c, L, (L + tsz) // 2, (L - tsz) // 2, M, (L - 2) // 2, seed=seed)
         ctxs.append(c)
     refs, psis = [], []
     for i, c in enumerate(ctxs):
