@@ -155,10 +155,11 @@ __global__ void __launch_bounds__(32 * WARPS) chain_flat_kernel(const ChainEntry
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int gi = blockIdx.x * WARPS + warp;
   if (gi >= ngroups) return;  // warp-uniform; only warp barriers below
-  TA(*Xs)[33] = reinterpret_cast<TA(*)[33]>(base + (size_t)warp * 4 * 32 * 33);
+  // three 32 x 33 tiles per warp; the Z tile reuses the X tile once T is formed
+  TA(*Xs)[33] = reinterpret_cast<TA(*)[33]>(base + (size_t)warp * 3 * 32 * 33);
   TA(*Ys)[33] = Xs + 32;
   TA(*Ts)[33] = Xs + 64;
-  TA(*Zs)[33] = Xs + 96;
+  TA(*Zs)[33] = Xs;
   const ChainGroup g = G[gi];
   const int m = g.m, q = g.q, mq = m * q;
   TA acc[32];
@@ -198,23 +199,26 @@ __global__ void __launch_bounds__(32 * WARPS) chain_flat_kernel(const ChainEntry
             Ys[kk][c] = (TA)Y[(int64_t)(n0 + kk) * e.yrs + (int64_t)(p0 + c) * e.ycs];
           }
           __syncwarp();
-          for (int t0 = lane; t0 < mp; t0 += 128) {
+          // element t = b0 + 32 u + lane; rounds of four warp-wide element groups
+          for (int b0 = 0; b0 < mp; b0 += 128) {
+            const int nu = min(4, (mp - b0 + 31) >> 5);  // warp-uniform
             int ii[4], cc[4];
             TA s4[4];
 #pragma unroll
             for (int u = 0; u < 4; ++u) {
-              const int t = min(t0 + 32 * u, mp - 1);
+              const int t = min(b0 + 32 * u + lane, mp - 1);
               ii[u] = t / pc;
               cc[u] = t % pc;
               s4[u] = 0;
             }
             for (int kk = 0; kk < nc; ++kk) {
 #pragma unroll
-              for (int u = 0; u < 4; ++u) s4[u] = fma(Xs[ii[u]][kk], Ys[kk][cc[u]], s4[u]);
+              for (int u = 0; u < 4; ++u)
+                if (u < nu) s4[u] = fma(Xs[ii[u]][kk], Ys[kk][cc[u]], s4[u]);
             }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
-              if (t0 + 32 * u < mp) Ts[ii[u]][cc[u]] += s4[u];
+              if (b0 + 32 * u + lane < mp) Ts[ii[u]][cc[u]] += s4[u];
           }
           __syncwarp();
         }
@@ -238,7 +242,8 @@ __global__ void __launch_bounds__(32 * WARPS) chain_flat_kernel(const ChainEntry
         __syncwarp();
 #pragma unroll
         for (int j0 = 0; j0 < 32; j0 += 4) {
-          if (lane + 32 * j0 >= mq) break;
+          const int nu = min(4, (mq - 32 * j0 + 31) >> 5);  // warp-uniform
+          if (nu <= 0) break;
           int ii[4], cc[4];
           TA s4[4];
 #pragma unroll
@@ -250,7 +255,8 @@ __global__ void __launch_bounds__(32 * WARPS) chain_flat_kernel(const ChainEntry
           }
           for (int kk = 0; kk < pc; ++kk) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) s4[u] = fma(Ts[ii[u]][kk], Zs[kk][cc[u]], s4[u]);
+            for (int u = 0; u < 4; ++u)
+              if (u < nu) s4[u] = fma(Ts[ii[u]][kk], Zs[kk][cc[u]], s4[u]);
           }
 #pragma unroll
           for (int u = 0; u < 4; ++u) acc[j0 + u] = fma(f, s4[u], acc[j0 + u]);
@@ -271,8 +277,8 @@ template <typename TX, typename TY, typename TZ, typename TA>
 static cudaError_t launch_flat(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb, uint64_t yb,
                                uint64_t zb, uint64_t db, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
-  constexpr int WARPS = sizeof(TA) == 8 ? 4 : 8;
-  const int smem = WARPS * 4 * 32 * 33 * (int)sizeof(TA);
+  constexpr int WARPS = sizeof(TA) == 8 ? 6 : 12;
+  const int smem = WARPS * 3 * 32 * 33 * (int)sizeof(TA);
   auto kern = chain_flat_kernel<TX, TY, TZ, TA, WARPS>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (err != cudaSuccess) return err;
