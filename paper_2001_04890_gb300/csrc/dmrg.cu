@@ -1846,9 +1846,16 @@ struct dmrg_batch {
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
   long long graph_kernels = 0;
+  // the graph runs on a private non-blocking stream (the legacy default stream
+  // cannot be captured), ordered after and before the contexts' stream by events
+  cudaStream_t own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
   ~dmrg_batch() {
     if (exec) cudaGraphExecDestroy(exec);
     if (graph) cudaGraphDestroy(graph);
+    if (ev_in) cudaEventDestroy(ev_in);
+    if (ev_out) cudaEventDestroy(ev_out);
+    if (own) cudaStreamDestroy(own);
   }
 };
 
@@ -1893,6 +1900,9 @@ extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out)
   b->chain.upload(CL, b->stream, tc, true);
   b->psi.alloc((size_t)std::max<long long>(b->off.back(), 1));
   b->sigma.alloc((size_t)std::max<long long>(b->off.back(), 1));
+  CK(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
+  CK(cudaEventCreateWithFlags(&b->ev_in, cudaEventDisableTiming));
+  CK(cudaEventCreateWithFlags(&b->ev_out, cudaEventDisableTiming));
   CK(cudaStreamSynchronize(b->stream));
   *out = b.release();
   API_END
@@ -1917,9 +1927,11 @@ extern "C" int dmrg_batch_hpsi(dmrg_batch *b, const double *psi, double *sigma, 
   API_BEGIN
   if (!b || !psi || !sigma) throw Fail{DMRG_EINVAL, "NULL argument"};
   const int64_t n = b->off.back();
-  cudaStream_t s = b->stream;
+  cudaStream_t cs = b->stream, s = b->own;
   CK(cudaMemcpyAsync(b->psi.p, psi, n * sizeof(double),
-                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, s));
+                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs));
+  CK(cudaEventRecord(b->ev_in, cs));
+  CK(cudaStreamWaitEvent(s, b->ev_in, 0));
   int *status = b->ctx[0]->dstatus.p;
   auto body = [&]() {
     CK(cudaMemsetAsync(b->sigma.p, 0, n * sizeof(double), s));
@@ -1938,9 +1950,11 @@ extern "C" int dmrg_batch_hpsi(dmrg_batch *b, const double *psi, double *sigma, 
     CK(cudaGraphLaunch(b->exec, s));
     add_kernel_launches(b->graph_kernels);
   }
+  CK(cudaEventRecord(b->ev_out, s));
+  CK(cudaStreamWaitEvent(cs, b->ev_out, 0));
   CK(cudaMemcpyAsync(sigma, b->sigma.p, n * sizeof(double),
-                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
-  if (!device_ptrs) CK(cudaStreamSynchronize(s));
+                     device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, cs));
+  if (!device_ptrs) CK(cudaStreamSynchronize(cs));
   check_status(b->ctx[0]);
   API_END
 }
