@@ -48,6 +48,10 @@ WORKLOADS = {
 
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, recipe table)
 
+# DRAM bytes (read + write) per launch of the dominant H.psi kernel, from one ncu
+# capture of the unchanged kernel at that workload and precision (else null)
+TRAFFIC_PER_LAUNCH = {("c2", 0, 512): 1.016e9 + 0.039e9}
+
 
 def _clock_sampler():
     f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
@@ -149,6 +153,7 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
     sampler, clk_path = _clock_sampler() if sample_clocks else (None, None)
     time.sleep(0.3)
     ev, iters, energy = [], [], None
+    torch.cuda.nvtx.range_push("step")  # lets ncu --nvtx-include "step/" capture the timed steps only
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)  # L2 flush between timed steps (256 MB > 129 MB L2)
@@ -159,6 +164,7 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
         ev.append((a, b))
         iters.append(it)
     stream.synchronize()
+    torch.cuda.nvtx.range_pop()
     st = ctx.stats(reset=True)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
     e2e_ms, d2h_bytes = None, 0
@@ -436,13 +442,13 @@ def main():
         "energy": r["energy"],
         "roofline": {
             "bound": "alu",
-            "kernel": "chain_fp64 (H.psi)",
+            "kernel": "chain_flat_kernel<double> (H.psi)",
             "achieved": kernel_tflops,
             "peak": FP64_NOMINAL_TFLOPS,
             "peak_source": "nominal GB300 FP64 from the recipe table (no measured FP64 peak in MEASURED_PEAKS.json)",
             "unit": "TFLOP/s",
             "frac": (kernel_tflops / FP64_NOMINAL_TFLOPS) if kernel_tflops else None,
-            "traffic": None,
+            "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, prec, wl["M"])),
         },
         "e2e": {"value": hpsi_flops / (r["e2e_ms"] * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},

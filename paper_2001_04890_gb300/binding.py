@@ -66,6 +66,10 @@ def lib():
         "dmrg_batch_layout": (C.c_int, [vp, llp, dp]),
         "dmrg_batch_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
         "dmrg_batch_free": (C.c_int, [vp]),
+        "dmrg_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
+        "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int]),
+        "dmrg_get_tune": (C.c_int, [vp, dp]),
+        "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -269,12 +273,34 @@ class DMRG:
                     kernel_launches=launches.value, davidson_iters=dav.value,
                     davidson_iters_lowp=dlow.value, last_residual=res.value)
 
+    def autotune(self, reps=3):
+        """Time candidate launch shapes of this position's H.psi task list; keep the fastest.
+
+        Returns (ms per H.psi with the chosen shape, {target_chunks, min_chunk, tc_min, by_work})."""
+        ms = C.c_double()
+        par = np.zeros(4)
+        _check(lib().dmrg_autotune(self.ctx, reps, C.byref(ms), _dptr(par)))
+        return ms.value, _tune_dict(par)
+
+    def set_tune(self, target_chunks=8192.0, min_chunk=2.0e5, tc_min=33, by_work=0):
+        _check(lib().dmrg_set_tune(self.ctx, float(target_chunks), float(min_chunk), int(tc_min), int(by_work)))
+
+    def get_tune(self):
+        par = np.zeros(4)
+        _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
+        return _tune_dict(par)
+
     def block_op(self, side, kind, i=-1, j=-1):
         n = C.c_longlong()
         _check(lib().dmrg_block_op(self.ctx, side, kind, i, j, None, C.byref(n)))
         out = np.zeros(n.value)
         _check(lib().dmrg_block_op(self.ctx, side, kind, i, j, _dptr(out), C.byref(n)))
         return out
+
+
+def _tune_dict(par):
+    return {"target_chunks": float(par[0]), "min_chunk": float(par[1]), "tc_min": int(par[2]),
+            "by_work": int(par[3])}
 
 
 class Batch:
@@ -303,6 +329,15 @@ class Batch:
         out = torch.empty_like(psi)
         _check(lib().dmrg_batch_hpsi(self.h, psi.data_ptr(), out.data_ptr(), 1))
         return out
+
+    def autotune(self, reps=3):
+        """Time candidate launch shapes of the grouped task list; keep the fastest.
+
+        Returns (ms per batched H.psi with the chosen shape, parameters)."""
+        ms = C.c_double()
+        par = np.zeros(4)
+        _check(lib().dmrg_batch_autotune(self.h, reps, C.byref(ms), _dptr(par)))
+        return ms.value, _tune_dict(par)
 
     def close(self):
         if getattr(self, "h", None):

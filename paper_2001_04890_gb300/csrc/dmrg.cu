@@ -269,6 +269,17 @@ struct ChainList {
 
 static double entry_flops(int m, int n, int p, int q, bool xid, bool zid);
 
+// Launch-shape parameters of a task list, chosen by dmrg_autotune: the split
+// granularity (about target_chunks chunks, none lighter than min_chunk FLOPs)
+// the smallest output-block side routed to the tensor cores, and the launch
+// order of the groups.
+struct ChainTune {
+  double target_chunks = 8192.0;
+  double min_chunk = 2.0e5;
+  int tc_min = 33;
+  int by_work = 0;  // 1: launch groups heaviest first; 0: in output-block order (operand locality)
+};
+
 // A task list on the device.  Output blocks of at most 32 x 32 go to the
 // flattened-lane warp kernel, blocks of 33..128 to the tensor-core kernel when
 // enabled (and all their entries have n, p <= 128), the rest to the 32 x 32
@@ -279,15 +290,23 @@ static double entry_flops(int m, int n, int p, int q, bool xid, bool zid);
 // thousands of independent tasks.
 struct DevChain {
   DBuf<ChainEntry> ent;
-  DBuf<ChainGroup> all, big, flat, tcg;
+  DBuf<ChainGroup> all, big, flat;
   DBuf<ReduceGroup> red;
   DBuf<double> scratch;
+  // tensor-core groups: entries with pre-split operand tiles (operators tiled
+  // once here, the psi blocks they read re-tiled at every launch)
+  DBuf<TcEntry> tce;
+  DBuf<TcGroup> tcg;
+  DBuf<PsiTileSpec> pts;
+  DBuf<uint8_t> optiles, psitiles;
+  int npts = 0;
   int nall = 0, nbig = 0, nflat = 0, ntc = 0, ntiles = 0, nred = 0;
   int64_t nent = 0;
   int64_t red_total = 0, scratch_n = 0;
   bool split = false;
 
-  void upload(const ChainList &CL, cudaStream_t s, bool tensor_cores = false, bool split_tasks = false) {
+  void upload(const ChainList &CL, cudaStream_t s, bool tensor_cores = false, bool split_tasks = false,
+              const ChainTune &tune = ChainTune()) {
     std::vector<ChainGroup> vb, vf, vt;
     std::vector<ReduceGroup> vr;
     split = split_tasks;
@@ -302,11 +321,17 @@ struct DevChain {
         w[i] = 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
         total += w[i];
       }
-    const double chunk_work = std::max(total / 8192.0, 2.0e5);
+    const double chunk_work = std::max(total / tune.target_chunks, tune.min_chunk);
     auto place = [&](ChainGroup t) {
-      bool tc_ok = tensor_cores && t.m <= 128 && t.q <= 128 && (t.m > 32 || t.q > 32);
-      for (int i = t.first; tc_ok && i < t.first + t.count; ++i)
-        if (CL.flat[i].n > 128 || CL.flat[i].p > 128 || CL.flat[i].y == ~0ull) tc_ok = false;
+      bool tc_ok = tensor_cores && t.count > 0 && t.m <= 128 && t.q <= 128 &&
+                   (t.m >= tune.tc_min || t.q >= tune.tc_min);
+      for (int i = t.first; tc_ok && i < t.first + t.count; ++i) {
+        const ChainEntry &e = CL.flat[i];
+        // Y must be a whole row-major psi block; identity sides are square
+        if (e.n < 1 || e.p < 1 || e.n > 128 || e.p > 128 || e.y == ~0ull || e.ycs != 1 || e.yrs != e.p ||
+            (e.x == ~0ull && e.n != t.m) || (e.z == ~0ull && e.p != t.q))
+          tc_ok = false;
+      }
       if (tc_ok) {
         vt.push_back(t);
       } else if (t.m <= 32 && t.q <= 32) {
@@ -352,22 +377,104 @@ struct DevChain {
       soff += (int64_t)nsplit * mq;
       e0 += mq;
     }
+    // optionally heaviest groups first: CTAs are dispatched in grid order, so the
+    // light groups fill the last wave; the natural order keeps the chunks of one
+    // output block (which read the same operators) adjacent.  Results do not
+    // depend on the order.
+    auto by_work = [&](std::vector<ChainGroup> &v) {
+      std::vector<std::pair<double, int>> key(v.size());
+      for (size_t i = 0; i < v.size(); ++i) {
+        double wsum = 0.0;
+        for (int e = v[i].first; e < v[i].first + v[i].count; ++e) wsum += w[e];
+        key[i] = {-wsum, (int)i};
+      }
+      std::stable_sort(key.begin(), key.end());
+      std::vector<ChainGroup> out(v.size());
+      for (size_t i = 0; i < v.size(); ++i) out[i] = v[key[i].second];
+      v.swap(out);
+    };
+    if (tune.by_work) {
+      by_work(vf);
+      by_work(vt);
+    }
     ent.upload(CL.flat, s);
     nent = (int64_t)CL.flat.size();
     all.upload(CL.grp, s);
     big.upload(vb, s);
     flat.upload(vf, s);
-    tcg.upload(vt, s);
+    build_tc(CL, vt, s);
     red.upload(vr, s);
     nall = (int)CL.grp.size();
     nbig = (int)vb.size();
     nflat = (int)vf.size();
-    ntc = (int)vt.size();
     nred = (int)vr.size();
     ntiles = tiles;
     red_total = e0;
     scratch_n = soff;
     if (split) scratch.alloc((size_t)std::max<int64_t>(soff, 1));
+  }
+
+  // Tensor-core entries: tile images of every X, Z^T operator view (deduplicated,
+  // exact identity tiles for identity sides) and of every psi block read as Y^T.
+  // Operator addresses are absolute (the task list is launched with x/z bases 0).
+  void build_tc(const ChainList &CL, const std::vector<ChainGroup> &vt, cudaStream_t s) {
+    std::vector<TcEntry> te;
+    std::vector<TcGroup> tg;
+    std::vector<TileSpec> ts;
+    std::vector<PsiTileSpec> ps;
+    std::map<std::tuple<uint64_t, int, int, int, int>, uint64_t> opmap;
+    std::unordered_map<uint64_t, uint64_t> psimap;
+    uint64_t opbytes = 0, psibytes = 0;
+    auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
+    auto op_tile = [&](uint64_t src, int rs, int cs, int R, int K) -> uint64_t {
+      const auto key = std::make_tuple(src, rs, cs, R, K);
+      auto it = opmap.find(key);
+      if (it != opmap.end()) return it->second;
+      ts.push_back(TileSpec{src, opbytes, rs, cs, R, K});
+      opmap.emplace(key, opbytes);
+      const uint64_t at = opbytes;
+      opbytes += c16(R) * c16(K) * 4;
+      return at;
+    };
+    for (const auto &g : vt) {
+      tg.push_back(TcGroup{g.d, g.drs, g.dcs, g.m, g.q, (int)te.size(), g.count});
+      for (int i = g.first; i < g.first + g.count; ++i) {
+        const ChainEntry &e = CL.flat[i];
+        TcEntry t{};
+        t.n = e.n;
+        t.p = e.p;
+        t.f = (float)e.f;
+        t.xt = e.x == ~0ull ? op_tile(~0ull, 0, 0, e.n, e.n) : op_tile(e.x * 4ull, e.xrs, e.xcs, g.m, e.n);
+        t.zt = e.z == ~0ull ? op_tile(~0ull, 0, 0, e.p, e.p) : op_tile(e.z * 4ull, e.zcs, e.zrs, g.q, e.p);
+        auto it = psimap.find(e.y);
+        if (it == psimap.end()) {
+          it = psimap.emplace(e.y, psibytes).first;
+          ps.push_back(PsiTileSpec{(int64_t)e.y, psibytes, e.n, e.p});
+          psibytes += c16(e.p) * c16(e.n) * 4;
+        }
+        t.yt = it->second;
+        te.push_back(t);
+      }
+    }
+    ntc = (int)tg.size();
+    npts = (int)ps.size();
+    if (ntc == 0) return;
+    tce.upload(te, s);
+    tcg.upload(tg, s);
+    pts.upload(ps, s);
+    optiles.alloc((size_t)opbytes);
+    psitiles.alloc((size_t)psibytes);
+    DBuf<TileSpec> tsd;
+    tsd.upload(ts, s);
+    CK(launch_build_tiles(tsd.p, (int)ts.size(), optiles.p, s));
+    CK(cudaStreamSynchronize(s));  // tsd is released on return
+  }
+
+  void launch_tc(uint64_t yb, uint64_t tb, int *status, cudaStream_t s) const {
+    if (ntc == 0) return;
+    if (!status) throw Fail{DMRG_EINVAL, "tensor-core task list launched without a status word"};
+    CK(launch_psi_tiles(pts.p, npts, reinterpret_cast<const double *>(yb), psitiles.p, s));
+    CK(launch_chain_tc2(tce.p, tcg.p, ntc, optiles.p, psitiles.p, tb, status, s));
   }
 
   void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s,
@@ -377,7 +484,7 @@ struct DevChain {
     if (f32ops) {
       CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
-      if (ntc > 0) CK(launch_chain_tc(ent.p, tcg.p, ntc, xb, yb, zb, tb, status, s));
+      launch_tc(yb, tb, status, s);
     } else {
       CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
@@ -394,7 +501,7 @@ struct DevChain {
     if (f32ops) {
       CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
-      if (ntc > 0) CK(launch_chain_tc(ent.p, tcg.p, ntc, xb, yb, zb, tb, status, s));
+      launch_tc(yb, tb, status, s);
     } else {
       CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
@@ -482,7 +589,13 @@ static void build_temps(DevTemps &T, const BlockLayout *lay[2], const double *st
 
 // ---------------------------------------------------------------- H.psi plan
 
+struct RPiece {
+  Ref l, r;
+  Piece p;
+};
+
 struct HPlan {
+  std::vector<RPiece> rps;  // resolved pieces of H at this position
   bool valid = false;
   int k = -1;
   const DevBlock *lb = nullptr, *rb = nullptr;
@@ -526,6 +639,7 @@ struct dmrg_ctx {
   double last_resid = 0.0;
   long long dav_iters_lowp = 0;
   dmrg::DBuf<int> dstatus;  // set by bounded device waits that ran out
+  dmrg::ChainTune tune;     // launch shape of H.psi task lists (dmrg_autotune)
 };
 
 namespace dmrg {
@@ -548,11 +662,6 @@ static std::unique_ptr<DevBlock> empty_block(int side, int L) {
   build_layout(b->lay, side, L, {}, {{0, 0, 1}});
   return b;
 }
-
-struct RPiece {
-  Ref l, r;
-  Piece p;
-};
 
 // Resolve the (compressed) pieces of H at position k onto the two blocks;
 // pieces on operators that vanish there are dropped.
@@ -648,6 +757,22 @@ static std::vector<ChainGroup> psi_protos(const Psi &Y) {
   return protos;
 }
 
+// The H.psi task list of the current plan over the FP64 masters or the FP32
+// copies (mixed precision), grouped by output psi block.
+static void hpsi_chainlist(dmrg_ctx *c, bool f32, ChainList &CL, double &flops) {
+  HPlan &P = c->plan;
+  DevBlock *lb = lblock(c), *rb = rblock(c);
+  if (f32) {
+    Arenas A32{{&lb->lay, &rb->lay}, {P.f32[0].p, P.f32[1].p}, &P.temps.set, {P.f32[2].p, P.f32[3].p}, 4};
+    expand_hpsi(P.rps, A32, P.psi, lb->lay, CL, flops);
+  } else {
+    Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
+             {P.temps.arena[0].p, P.temps.arena[1].p}, 8};
+    expand_hpsi(P.rps, A, P.psi, lb->lay, CL, flops);
+  }
+  CL.finish(psi_protos(P.psi));
+}
+
 static void build_hplan(dmrg_ctx *c) {
   HPlan &P = c->plan;
   require_blocks(c);
@@ -660,19 +785,19 @@ static void build_hplan(dmrg_ctx *c) {
   P.psi = psi_layout(lb->lay, rb->lay, c->nu, c->nd);
   const Psi &Y = P.psi;
   P.temps.set = TempSet();
-  auto rps = resolve_pieces(c->I, c->k, lb->lay, rb->lay, P.temps.set);
+  P.rps = resolve_pieces(c->I, c->k, lb->lay, rb->lay, P.temps.set);
   const BlockLayout *lay[2] = {&lb->lay, &rb->lay};
   const double *stored[2] = {lb->arena(), rb->arena()};
   build_temps(P.temps, lay, stored, c->stream);
-  Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
-           {P.temps.arena[0].p, P.temps.arena[1].p}, 8};
-  ChainList CL;
-  double flops = 0.0;
-  expand_hpsi(rps, A, Y, lb->lay, CL, flops);
-  CL.finish(psi_protos(Y));
-  P.chain.upload(CL, c->stream, false, true);
-  P.flops = flops;
-  P.ntasks = (long long)CL.flat.size();
+  {
+    ChainList CL;
+    double flops = 0.0;
+    hpsi_chainlist(c, false, CL, flops);
+    P.chain.upload(CL, c->stream, false, true, c->tune);
+    P.flops = flops;
+    P.ntasks = (long long)CL.flat.size();
+    CK(cudaStreamSynchronize(c->stream));  // host vectors are released at the end of the scope
+  }
   P.diag.alloc((size_t)std::max<int64_t>(Y.dim, 1));
   CK(cudaMemsetAsync(P.diag.p, 0, Y.dim * sizeof(double), c->stream));
   CK(launch_diag_fp64(P.chain.ent.p, P.chain.all.p, P.chain.nall, 0, 0, P.diag.p, c->stream));
@@ -685,15 +810,13 @@ static void build_hplan(dmrg_ctx *c) {
       P.f32[i].alloc((size_t)std::max<int64_t>(cnt[i], 1));
       if (cnt[i] > 0 && src[i]) CK(launch_to_f32(P.f32[i].p, src[i], cnt[i], c->stream));
     }
-    Arenas A32{{&lb->lay, &rb->lay}, {P.f32[0].p, P.f32[1].p}, &P.temps.set, {P.f32[2].p, P.f32[3].p}, 4};
     ChainList CL32;
     double fl32 = 0.0;
-    expand_hpsi(rps, A32, Y, lb->lay, CL32, fl32);
-    CL32.finish(psi_protos(Y));
-    P.chain32.upload(CL32, c->stream, c->prec == DMRG_PREC_BF16X3, true);
+    hpsi_chainlist(c, true, CL32, fl32);
+    P.chain32.upload(CL32, c->stream, c->prec == DMRG_PREC_BF16X3, true, c->tune);
     CK(cudaStreamSynchronize(c->stream));
   }
-  CK(cudaStreamSynchronize(c->stream));  // host vectors above are released on return
+  CK(cudaStreamSynchronize(c->stream));
   P.valid = true;
 }
 
@@ -1839,7 +1962,8 @@ struct dmrg_batch {
   std::vector<dmrg_ctx *> ctx;
   std::vector<long long> off;  // n + 1 offsets into the concatenated vectors
   cudaStream_t stream = nullptr;
-  bool lowp = false;
+  bool lowp = false, tc = false;
+  dmrg::ChainTune tune;
   DevChain chain;
   DBuf<double> psi, sigma;
   double flops = 0.0;
@@ -1859,20 +1983,13 @@ struct dmrg_batch {
   }
 };
 
-extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out) {
-  API_BEGIN
-  if (n < 1 || !ctxs || !out) throw Fail{DMRG_EINVAL, "bad arguments"};
-  *out = nullptr;
-  auto b = std::make_unique<dmrg_batch>();
-  b->stream = ctxs[0]->stream;
-  b->off.push_back(0);
-  ChainList CL;
-  for (int i = 0; i < n; ++i) {
-    dmrg_ctx *c = ctxs[i];
-    if (!c) throw Fail{DMRG_EINVAL, "NULL context in batch"};
-    if (c->stream != b->stream) throw Fail{DMRG_EINVAL, "batched contexts must share one stream"};
-    if ((c->prec != DMRG_PREC_FP64) != (ctxs[0]->prec != DMRG_PREC_FP64))
-      throw Fail{DMRG_EINVAL, "batched contexts must share the working precision class"};
+// The concatenated task list of the batch: every context's H.psi list (at its
+// current position) with psi / sigma offsets shifted by the context's offset.
+static void batch_chainlist(const std::vector<dmrg_ctx *> &ctxs, ChainList &CL, std::vector<long long> &off,
+                            double &flops) {
+  off.assign(1, 0);
+  flops = 0.0;
+  for (dmrg_ctx *c : ctxs) {
     build_hplan(c);
     const HPlan &P = c->plan;
     const DevChain &src = P.lowp ? P.chain32 : P.chain;
@@ -1880,7 +1997,7 @@ extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out)
     std::vector<ChainGroup> grp((size_t)src.nall);
     if (!ent.empty()) CK(cudaMemcpy(ent.data(), src.ent.p, ent.size() * sizeof(ChainEntry), cudaMemcpyDeviceToHost));
     if (!grp.empty()) CK(cudaMemcpy(grp.data(), src.all.p, grp.size() * sizeof(ChainGroup), cudaMemcpyDeviceToHost));
-    const long long o = b->off.back();
+    const long long o = off.back();
     const int base = (int)CL.flat.size();
     for (auto e : ent) {
       e.y += (uint64_t)o;
@@ -1891,13 +2008,30 @@ extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out)
       g.first += base;
       CL.grp.push_back(g);
     }
-    b->off.push_back(o + P.psi.dim);
-    b->flops += P.flops;
-    b->ctx.push_back(c);
-    b->lowp = P.lowp;
+    off.push_back(o + P.psi.dim);
+    flops += P.flops;
   }
-  const bool tc = ctxs[0]->prec == DMRG_PREC_BF16X3;
-  b->chain.upload(CL, b->stream, tc, true);
+}
+
+extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out) {
+  API_BEGIN
+  if (n < 1 || !ctxs || !out) throw Fail{DMRG_EINVAL, "bad arguments"};
+  *out = nullptr;
+  auto b = std::make_unique<dmrg_batch>();
+  b->stream = ctxs[0]->stream;
+  for (int i = 0; i < n; ++i) {
+    dmrg_ctx *c = ctxs[i];
+    if (!c) throw Fail{DMRG_EINVAL, "NULL context in batch"};
+    if (c->stream != b->stream) throw Fail{DMRG_EINVAL, "batched contexts must share one stream"};
+    if ((c->prec != DMRG_PREC_FP64) != (ctxs[0]->prec != DMRG_PREC_FP64))
+      throw Fail{DMRG_EINVAL, "batched contexts must share the working precision class"};
+    b->ctx.push_back(c);
+  }
+  ChainList CL;
+  batch_chainlist(b->ctx, CL, b->off, b->flops);
+  b->lowp = ctxs[0]->prec != DMRG_PREC_FP64;
+  b->tc = ctxs[0]->prec == DMRG_PREC_BF16X3;
+  b->chain.upload(CL, b->stream, b->tc, true, b->tune);
   b->psi.alloc((size_t)std::max<long long>(b->off.back(), 1));
   b->sigma.alloc((size_t)std::max<long long>(b->off.back(), 1));
   CK(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
@@ -1956,5 +2090,181 @@ extern "C" int dmrg_batch_hpsi(dmrg_batch *b, const double *psi, double *sigma, 
                      device_ptrs ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, cs));
   if (!device_ptrs) CK(cudaStreamSynchronize(cs));
   check_status(b->ctx[0]);
+  API_END
+}
+
+// ---------------------------------------------------------------------------
+// Autotuning of the launch shape of H.psi task lists (split granularity and
+// tensor-core routing): each candidate task list is built and its complete
+// launch sequence (zeroing, kernels, ordered reduction) timed with CUDA events
+// on the caller's stream; the fastest is kept.  Results are identical up to
+// floating-point summation order across candidates.
+// ---------------------------------------------------------------------------
+
+namespace dmrg {
+
+struct EventPair {
+  cudaEvent_t a = nullptr, b = nullptr;
+  EventPair() {
+    CK(cudaEventCreate(&a));
+    CK(cudaEventCreate(&b));
+  }
+  ~EventPair() {
+    if (a) cudaEventDestroy(a);
+    if (b) cudaEventDestroy(b);
+  }
+};
+
+static double time_chain(const DevChain &ch, bool lowp, const double *x, double *y, int64_t n,
+                         cudaStream_t s, int *status, int reps) {
+  EventPair ev;
+  auto once = [&]() {
+    CK(cudaMemsetAsync(y, 0, (size_t)n * sizeof(double), s));
+    ch.launch(lowp, 0, (uint64_t)(uintptr_t)x, 0, (uint64_t)(uintptr_t)y, s, status);
+  };
+  once();
+  CK(cudaEventRecord(ev.a, s));
+  for (int r = 0; r < reps; ++r) once();
+  CK(cudaEventRecord(ev.b, s));
+  CK(cudaEventSynchronize(ev.b));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, ev.a, ev.b));
+  return (double)ms / reps;
+}
+
+// Coordinate search: split granularity first, then (tensor cores only) the
+// smallest output-block side routed to the tensor-core kernel.
+static ChainTune autotune_chain(const ChainList &CL, bool tc, bool lowp, const double *x, double *y, int64_t n,
+                                cudaStream_t s, int *status, int reps, ChainTune start, double &best_ms) {
+  auto run = [&](const ChainTune &t) {
+    DevChain ch;
+    ch.upload(CL, s, tc, true, t);
+    return time_chain(ch, lowp, x, y, n, s, status, reps);
+  };
+  ChainTune best = start;
+  best_ms = run(best);
+  const double targets[] = {2048.0, 8192.0, 32768.0};
+  const double mins[] = {5.0e4, 2.0e5};
+  for (double tg : targets)
+    for (double mn : mins) {
+      ChainTune t = best;
+      t.target_chunks = tg;
+      t.min_chunk = mn;
+      if (t.target_chunks == best.target_chunks && t.min_chunk == best.min_chunk) continue;
+      const double ms = run(t);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  {
+    ChainTune t = best;
+    t.by_work = 1 - best.by_work;
+    const double ms = run(t);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
+  }
+  if (tc) {
+    const int tcs[] = {17, 33, 49, 65};
+    for (int v : tcs) {
+      if (v == best.tc_min) continue;
+      ChainTune t = best;
+      t.tc_min = v;
+      const double ms = run(t);
+      if (ms < best_ms) {
+        best_ms = ms;
+        best = t;
+      }
+    }
+  }
+  return best;
+}
+
+static void tune_out(const ChainTune &t, double *params) {
+  if (!params) return;
+  params[0] = t.target_chunks;
+  params[1] = t.min_chunk;
+  params[2] = t.tc_min;
+  params[3] = t.by_work;
+}
+
+}  // namespace dmrg
+
+extern "C" int dmrg_autotune(dmrg_ctx *c, int reps, double *best_ms, double *params) {
+  API_BEGIN
+  if (!c || reps < 1) throw Fail{DMRG_EINVAL, "dmrg_autotune: NULL context or reps < 1"};
+  build_hplan(c);
+  HPlan &P = c->plan;
+  const bool lowp = P.lowp, tc = c->prec == DMRG_PREC_BF16X3;
+  const int64_t n = P.psi.dim;
+  ChainTune best;
+  double ms = 0.0;
+  {
+    ChainList CL;
+    double fl = 0.0;
+    hpsi_chainlist(c, lowp, CL, fl);
+    DBuf<double> x, y;
+    x.alloc((size_t)std::max<int64_t>(n, 1));
+    y.alloc((size_t)std::max<int64_t>(n, 1));
+    CK(launch_fill_guess(x.p, n, 0x5eedull, c->stream));
+    best = autotune_chain(CL, tc, lowp, x.p, y.p, n, c->stream, c->dstatus.p, reps, c->tune, ms);
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  check_status(c);
+  c->tune = best;
+  c->plan.valid = false;  // rebuilt with the chosen shape
+  build_hplan(c);
+  if (best_ms) *best_ms = ms;
+  tune_out(best, params);
+  API_END
+}
+
+extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk, int tc_min, int by_work) {
+  API_BEGIN
+  if (!c || !(target_chunks >= 1.0) || !(min_chunk >= 0.0) || tc_min < 1 || tc_min > 129 ||
+      (by_work != 0 && by_work != 1))
+    throw Fail{DMRG_EINVAL,
+               "dmrg_set_tune: target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, by_work 0 or 1"};
+  c->tune.target_chunks = target_chunks;
+  c->tune.min_chunk = min_chunk;
+  c->tune.tc_min = tc_min;
+  c->tune.by_work = by_work;
+  c->plan.valid = false;
+  API_END
+}
+
+extern "C" int dmrg_get_tune(dmrg_ctx *c, double *params) {
+  API_BEGIN
+  if (!c || !params) throw Fail{DMRG_EINVAL, "NULL argument"};
+  tune_out(c->tune, params);
+  API_END
+}
+
+extern "C" int dmrg_batch_autotune(dmrg_batch *b, int reps, double *best_ms, double *params) {
+  API_BEGIN
+  if (!b || reps < 1) throw Fail{DMRG_EINVAL, "dmrg_batch_autotune: NULL batch or reps < 1"};
+  CK(cudaStreamSynchronize(b->stream));
+  ChainList CL;
+  std::vector<long long> off;
+  double fl = 0.0;
+  batch_chainlist(b->ctx, CL, off, fl);
+  if (off != b->off) throw Fail{DMRG_ESTATE, "a batched context changed position since dmrg_batch_create"};
+  const int64_t n = b->off.back();
+  CK(launch_fill_guess(b->psi.p, n, 0x5eedull, b->stream));
+  double ms = 0.0;
+  ChainTune best = autotune_chain(CL, b->tc, b->lowp, b->psi.p, b->sigma.p, n, b->stream,
+                                  b->ctx[0]->dstatus.p, reps, b->tune, ms);
+  check_status(b->ctx[0]);
+  b->tune = best;
+  b->chain.upload(CL, b->stream, b->tc, true, best);
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  if (b->graph) cudaGraphDestroy(b->graph);
+  b->exec = nullptr;
+  b->graph = nullptr;  // captured again on the next dmrg_batch_hpsi
+  CK(cudaStreamSynchronize(b->stream));
+  if (best_ms) *best_ms = ms;
+  tune_out(best, params);
   API_END
 }

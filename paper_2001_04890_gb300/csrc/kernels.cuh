@@ -72,11 +72,6 @@ cudaError_t launch_gather_columns(double *O, const double *evecs, int n, const i
 
 int dots_partial_blocks(int64_t n);
 
-// tensor-core H.psi chain (split-BF16 x3, FP32 operator copies, FP64 psi / sigma);
-// groups with m, q <= 128 whose entries all have n, p <= 128
-cudaError_t launch_chain_tc(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb, uint64_t yb,
-                            uint64_t zb, uint64_t db, int *status, cudaStream_t s);
-
 // tcgen05 self-test: C (128 x N) = A (128 x K) B^T (N x K), bf16 inputs, FP32 accumulation in TMEM
 cudaError_t launch_tc_selftest(const float *A, const float *B, float *C, int N, int K, int *status,
                                cudaStream_t s);
@@ -84,5 +79,46 @@ cudaError_t launch_tc_selftest(const float *A, const float *B, float *C, int N, 
 // number of kernels this library has launched in the process
 long long kernel_launch_count();
 void add_kernel_launches(long long n);  // kernels run by CUDA-graph replays
+
+}  // namespace dmrg
+
+namespace dmrg {
+
+// Tensor-core tiles: an R x K operand pre-split into bf16 hi / lo parts in the
+// K-major core-matrix layout (8-row x 16-byte core matrices, core matrix
+// (rg, kg) at byte (rg * K16/8 + kg) * 128), rows padded to R8 = ceil8(R),
+// K to K16 = ceil16(K) with zeros; the lo part follows the hi part.
+struct TileSpec {
+  uint64_t src;     // element address of the FP32 source view (element (r, k) at src + r*rs + k*cs)
+  uint64_t dst;     // byte offset of the tile in the tile arena
+  int rs, cs, R, K;
+};
+struct PsiTileSpec {
+  int64_t src;      // element offset of the psi block (n x p, row-major) in psi
+  uint64_t dst;     // byte offset of its transposed tile (rows p, K n)
+  int n, p;
+};
+// One task of the pipelined tensor-core chain: D += f X Y Z with X, Y^T, Z^T given as tiles
+struct TcEntry {
+  uint64_t xt, yt, zt;  // byte offsets: X tile (op arena), Y^T tile (psi tiles), Z^T tile (op arena)
+  int n, p;             // inner dims (<= 64)
+  float f;
+  int pad;
+};
+struct TcGroup {
+  uint64_t d;       // element offset of the output block (or scratch slot)
+  int drs, dcs, m, q;
+  int first, count;
+};
+
+// operator tiles from FP32 sources (src == ~0: exact identity tile)
+cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, cudaStream_t s);
+// Y^T tiles of FP64 psi blocks
+cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi, uint8_t *arena,
+                             cudaStream_t s);
+// tensor-core H.psi chain (split-BF16 x3, FP32 accumulation, FP64 output blocks), one CTA per
+// group (m, q <= 128, every entry n, p <= 128); *status is raised if an mbarrier wait ran out
+cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
+                             const uint8_t *psitiles, uint64_t db, int *status, cudaStream_t s);
 
 }  // namespace dmrg

@@ -86,185 +86,372 @@ cudaError_t launch_tc_selftest(const float *A, const float *B, float *C, int N, 
 namespace dmrg {
 
 // ---------------------------------------------------------------------------
-// Fused H.psi chain on the tensor cores (split-BF16, three passes, FP32 in TMEM).
+// Pre-split operand tiles and the pipelined tensor-core chain.
 //
-// One CTA (4 warps, thread = tile row) per output block D (m x q, both <= 128)
-// of the task list; for every entry  D += f X Y Z  (Sec. 2.2.1, Eq. dgemm:
-// X = A_l, Y = psi^s, Z = A_r^T) with n, p <= 128:
-//   stage 1  T = X Y        (M=128, N=p16, K=n in chunks of 64) -> TMEM cols [0,128)
-//   stage 2  D += (f T) Z   (M=128, N=q16, K=p in chunks of 64) -> TMEM cols [128,256)
-// Each product is hi*hi + hi*lo + lo*hi of the bf16 splits.  X and Z are FP32
-// (operator copies), Y is FP64 (psi), D is FP64.  Identity X or Z are handled
-// by feeding Y directly to stage 2 / multiplying by an exact identity tile.
+// Every operand the tensor core reads from global memory is stored once as a
+// ready-made shared-memory image: rows padded to R16 = ceil16(R) and K to
+// K16 = ceil16(K) with zeros, cut into K chunks of T2_W = 32 columns (the last
+// chunk 16 wide when K16 % 32 == 16).  Chunk c starts at byte 128 * R16 * c and
+// holds the bf16 hi part (R16 x w, K-major core matrices, core matrix (rg, kg)
+// at (rg * w/8 + kg) * 128) followed by the lo part.  A chunk is one 1-D bulk
+// copy (cp.async.bulk) into shared memory, so staging costs no thread work.
+//
+// Operator blocks (X and Z^T views of the stored and pre-summed operators)
+// are tiled once per task list; the psi blocks (as Y^T) once per H.psi call.
 // ---------------------------------------------------------------------------
 
-static constexpr int TC_KC = 64;
-static constexpr int TC_TILE = 128 * TC_KC * 2;  // one bf16 operand tile (16 KB)
+static constexpr int T2_W = 32;
 
-__device__ __forceinline__ void put_split(uint8_t *hi_tile, uint8_t *lo_tile, int r, int k, float x) {
-  __nv_bfloat16 h, l;
-  tc::split_bf16(x, h, l);
-  const uint32_t o = tc::kmajor_off(r, k, TC_KC);
-  *reinterpret_cast<__nv_bfloat16 *>(hi_tile + o) = h;
-  *reinterpret_cast<__nv_bfloat16 *>(lo_tile + o) = l;
-}
-
-__device__ __forceinline__ void issue3(uint32_t dtmem, uint32_t ahi, uint32_t alo, uint32_t bhi, uint32_t blo,
-                                       int ksteps, uint32_t idesc, bool first) {
-  constexpr uint32_t SBO = (TC_KC / 8) * 128;
-  for (int ks = 0; ks < ksteps; ++ks) {
-    const uint32_t off = ks * 2 * 128;
-    tc::mma_bf16(dtmem, tc::make_desc(ahi + off, 128, SBO), tc::make_desc(bhi + off, 128, SBO), idesc,
-                 first ? 0u : 1u);
-    first = false;
-    tc::mma_bf16(dtmem, tc::make_desc(ahi + off, 128, SBO), tc::make_desc(blo + off, 128, SBO), idesc, 1u);
-    tc::mma_bf16(dtmem, tc::make_desc(alo + off, 128, SBO), tc::make_desc(bhi + off, 128, SBO), idesc, 1u);
+template <typename Load>
+__device__ __forceinline__ void write_tile(uint8_t *img, int R, int K, Load load, int t0, int nt) {
+  const int R16 = (R + 15) & ~15, K16 = (K + 15) & ~15;
+  const int units = R16 * (K16 >> 3);
+  for (int u = t0; u < units; u += nt) {
+    const int r = u % R16, kg = u / R16, k0 = kg * 8;
+    const int c = k0 / T2_W, w = min(T2_W, K16 - c * T2_W), kgi = (k0 - c * T2_W) >> 3;
+    uint8_t *hi = img + (size_t)128 * R16 * c + ((r >> 3) * (w >> 3) + kgi) * 128 + (r & 7) * 16;
+    uint8_t *lo = hi + (size_t)R16 * w * 2;
+    __align__(16) __nv_bfloat16 h[8], l[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      const float x = (r < R && k0 + i < K) ? load(r, k0 + i) : 0.f;
+      tc::split_bf16(x, h[i], l[i]);
+    }
+    *reinterpret_cast<uint4 *>(hi) = *reinterpret_cast<const uint4 *>(h);
+    *reinterpret_cast<uint4 *>(lo) = *reinterpret_cast<const uint4 *>(l);
   }
 }
 
-__global__ void __launch_bounds__(128) chain_tc_kernel(const ChainEntry *__restrict__ E,
-                                                       const ChainGroup *__restrict__ G, uint64_t xb,
-                                                       uint64_t yb, uint64_t zb, uint64_t db, int *status) {
+__global__ void __launch_bounds__(256) build_tiles_kernel(const TileSpec *__restrict__ T, int ntiles,
+                                                          uint8_t *arena) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const TileSpec s = T[t];
+    uint8_t *img = arena + s.dst;
+    if (s.src == ~0ull) {
+      write_tile(img, s.R, s.K, [](int r, int k) { return r == k ? 1.f : 0.f; }, threadIdx.x, blockDim.x);
+    } else {
+      const float *X = reinterpret_cast<const float *>(s.src);
+      const int64_t rs = s.rs, cs = s.cs;
+      write_tile(img, s.R, s.K, [&](int r, int k) { return X[r * rs + k * cs]; }, threadIdx.x, blockDim.x);
+    }
+  }
+}
+
+// Y^T of a psi block: tile row j (< p), column k (< n) is psi[src + k * p + j].
+__global__ void __launch_bounds__(256) psi_tiles_kernel(const PsiTileSpec *__restrict__ T, int ntiles,
+                                                        const double *__restrict__ psi, uint8_t *arena) {
+  for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
+    const PsiTileSpec s = T[t];
+    const double *Y = psi + s.src;
+    const int p = s.p;
+    write_tile(arena + s.dst, s.p, s.n, [&](int j, int k) { return (float)Y[(int64_t)k * p + j]; },
+               threadIdx.x, blockDim.x);
+  }
+}
+
+cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  add_kernel_launches(1);
+  build_tiles_kernel<<<std::min(ntiles, 152 * 16), 256, 0, s>>>(t, ntiles, arena);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi, uint8_t *arena,
+                             cudaStream_t s) {
+  if (ntiles <= 0) return cudaSuccess;
+  add_kernel_launches(1);
+  psi_tiles_kernel<<<std::min(ntiles, 152 * 16), 256, 0, s>>>(t, ntiles, psi, arena);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// chain_tc2: D += sum_e f_e X_e Y_e Z_e for one output block per CTA on the
+// tensor cores (split-BF16 three-pass products, FP32 accumulation in TMEM).
+//
+// Work of one entry is a sequence of "jobs", one per K chunk:
+//   stage 1 (K = n):  T = X Y           A = X chunk, B = Y^T chunk, both bulk-copied
+//   stage 2 (K = p):  D += (f T) Z      A = f T chunk written by the converter
+//                                        warps from TMEM, B = Z^T chunk bulk-copied
+// Identity X / Z are exact identity tiles.  Jobs run through a ring of T2_NS
+// shared-memory stages (A half | B half, 16 KB each) with warp roles:
+//   warps 0-3  converters: T (TMEM lanes = rows) -> f T split into bf16 hi/lo
+//              in stage 2 jobs; finally D (TMEM) -> FP64 output block
+//   warp 4     producer: bulk copies of the operand chunks
+//   warp 5     MMA issuer: one thread issues tcgen05.mma and commits
+// mbarriers per stage: full (copies landed), cvf (converters wrote A),
+// empty (MMAs that read the stage finished); per entry: tfull (T complete),
+// tempty (converters finished reading T); dfull (D complete).
+// Every wait is bounded: on time-out the CTA raises *status, all roles stop,
+// copies and MMAs in flight are waited for, and TMEM is released.
+// ---------------------------------------------------------------------------
+
+static constexpr int T2_NS = 3;
+static constexpr int T2_HALF = 16384;
+static constexpr int T2_STAGE = 2 * T2_HALF;
+static constexpr int T2_BAR_OFF = T2_NS * T2_STAGE;
+static constexpr int T2_THREADS = 192;
+
+struct T2Bars {
+  uint64_t full[T2_NS], cvf[T2_NS], empty[T2_NS];
+  uint64_t tfull, tempty, dfull, drain;
+  uint32_t tslot;
+  int abort;
+};
+static constexpr int T2_SMEM = T2_BAR_OFF + (int)sizeof(T2Bars);
+// at most two CTAs (2 x 256 TMEM columns) per SM
+static constexpr int T2_SMEM_LAUNCH = 100 * 1024;
+
+// single-thread bounded wait that gives up early when another role aborted
+__device__ __forceinline__ bool t2_wait1(uint64_t *bar, uint32_t parity, volatile int *abort, int *status) {
+  for (long long i = 0; i < kMaxWaitTries; ++i) {
+    if (tc::mbar_try_wait(bar, parity)) return true;
+    if ((i & 63) == 63 && *abort) return false;
+  }
+  *abort = 1;
+  atomicExch(status, 1);
+  return false;
+}
+
+// warp-uniform bounded wait (all 32 lanes take the same decision)
+__device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatile int *abort, int *status) {
+  for (long long i = 0; i < kMaxWaitTries; ++i) {
+    if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity))) return true;
+    if ((i & 63) == 63 && __any_sync(0xffffffffu, *abort)) return false;
+  }
+  if ((threadIdx.x & 31) == 0) {
+    *abort = 1;
+    atomicExch(status, 1);
+  }
+  __syncwarp();
+  return false;
+}
+
+__device__ __forceinline__ int ceil16(int x) { return (x + 15) & ~15; }
+
+__global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__restrict__ E,
+                                                               const TcGroup *__restrict__ G,
+                                                               const uint8_t *__restrict__ optiles,
+                                                               const uint8_t *__restrict__ psitiles,
+                                                               uint64_t db, int *status) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  uint8_t *Ahi = smem, *Alo = smem + TC_TILE, *Bhi = smem + 2 * TC_TILE, *Blo = smem + 3 * TC_TILE;
-  uint64_t *bar = reinterpret_cast<uint64_t *>(smem + 4 * TC_TILE);
-  uint32_t *tslot = reinterpret_cast<uint32_t *>(smem + 4 * TC_TILE + 16);
-  const int tid = threadIdx.x, warp = tid >> 5;
-  const ChainGroup g = G[blockIdx.x];
+  T2Bars *B = reinterpret_cast<T2Bars *>(smem + T2_BAR_OFF);
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const TcGroup g = G[blockIdx.x];
   if (warp == 0) {
-    tc::tmem_alloc(tslot, 256);
+    tc::tmem_alloc(&B->tslot, 256);
     tc::tmem_relinquish();
   }
-  if (tid == 0) tc::mbar_init(bar, 1);
-  // zero all operand tiles once: every element the tensor core reads is finite
-  for (int i = tid; i < 4 * TC_TILE / 16; i += 128) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+  if (tid == 0) {
+    for (int s = 0; s < T2_NS; ++s) {
+      tc::mbar_init(&B->full[s], 1);
+      tc::mbar_init(&B->cvf[s], 4);
+      tc::mbar_init(&B->empty[s], 1);
+    }
+    tc::mbar_init(&B->tfull, 1);
+    tc::mbar_init(&B->tempty, 4);
+    tc::mbar_init(&B->dfull, 1);
+    tc::mbar_init(&B->drain, 1);
+    B->abort = 0;
+  }
+  // stale rows of an A operand only feed discarded TMEM lanes, but must be finite
+  for (int i = tid; i < T2_BAR_OFF / 16; i += T2_THREADS) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+  tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tbase = *tslot;
-  const uint32_t tT = tbase, tD = tbase + 128;
-  const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-  const uint32_t sAhi = tc::smem_u32(Ahi), sAlo = tc::smem_u32(Alo), sBhi = tc::smem_u32(Bhi),
-                 sBlo = tc::smem_u32(Blo);
-  const int m = g.m, q = g.q, q16 = (q + 15) & ~15;
-  uint32_t phase = 0;
-  bool d_first = true, failed = false;
-  const int row = tid;
+  const uint32_t tbase = B->tslot, tT = tbase, tD = tbase + 128;
+  volatile int *abort = &B->abort;
+  const int m = g.m, q = g.q, m16 = ceil16(m), q16 = ceil16(q);
+  const int e_end = g.first + g.count;
 
-  auto commit_wait = [&]() -> bool {
-    if (tid == 0) tc::mma_commit(bar);
-    const bool ok = tc::mbar_wait(bar, phase, kMaxWaitTries);
-    phase ^= 1u;
-    tc::fence_after();
-    return __syncthreads_or(!ok) == 0;
-  };
-  auto publish = [&]() {
-    tc::fence_async_smem();
-    tc::fence_before();
-    __syncthreads();
-    tc::fence_after();
-  };
-
-  for (int ei = g.first; ei < g.first + g.count && !failed; ++ei) {
-    const ChainEntry e = E[ei];
-    const bool xid = e.x == ~0ull, zid = e.z == ~0ull;
-    const float *X = xid ? nullptr : reinterpret_cast<const float *>(xb + e.x * 4ull);
-    const double *Y = reinterpret_cast<const double *>(yb + e.y * 8ull);
-    const float *Z = zid ? nullptr : reinterpret_cast<const float *>(zb + e.z * 4ull);
-    const float f = (float)e.f;
-    const int n = e.n, p = e.p, p16 = (p + 15) & ~15;
-    // ---- stage 1: T = X Y
-    if (!xid) {
-      bool t_first = true;
-      for (int n0 = 0; n0 < n && !failed; n0 += TC_KC) {
-        const int nc = min(TC_KC, n - n0);
-        const int kc16 = (nc + 15) & ~15;  // K padding up to the MMA step must be zero
-        // A rows < m (rows >= m may hold stale finite data: they only feed output rows >= m)
-        for (int idx = tid; idx < m * kc16; idx += 128) {
-          const int r = idx / kc16, k = idx % kc16;
-          const float x = (k < nc) ? X[(int64_t)r * e.xrs + (int64_t)(n0 + k) * e.xcs] : 0.f;
-          put_split(Ahi, Alo, r, k, x);
-        }
-        // B row j = column j of Y, j < p (consecutive threads take consecutive j)
-        for (int idx = tid; idx < p * kc16; idx += 128) {
-          const int k = idx / p, j = idx % p;
-          const float y = (k < nc) ? (float)Y[(int64_t)(n0 + k) * e.yrs + (int64_t)j * e.ycs] : 0.f;
-          put_split(Bhi, Blo, j, k, y);
-        }
-        publish();
-        if (tid == 0) issue3(tT, sAhi, sAlo, sBhi, sBlo, (nc + 15) / 16, tc::idesc_bf16(128, p16), t_first);
-        t_first = false;
-        failed = !commit_wait();
-      }
-    }
-    // ---- stage 2: D += (f T) Z
-    for (int p0 = 0; p0 < p && !failed; p0 += TC_KC) {
-      const int pc = min(TC_KC, p - p0);
-      const int pc16 = (pc + 15) & ~15;
-      if (xid) {
-        if (row < m) {
-          for (int k = 0; k < pc16; ++k) {
-            const float t = (k < pc) ? f * (float)Y[(int64_t)row * e.yrs + (int64_t)(p0 + k) * e.ycs] : 0.f;
-            put_split(Ahi, Alo, row, k, t);
+  if (warp == 4) {
+    // ---------------- producer
+    if (lane == 0) {
+      int j = 0;
+      bool ok = true;
+      for (int ei = g.first; ei < e_end && ok; ++ei) {
+        const TcEntry e = E[ei];
+        const int n16 = ceil16(e.n), p16 = ceil16(e.p);
+        const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+        for (int c = 0; c < nch1 + nch2 && ok; ++c, ++j) {
+          const int s = j % T2_NS;
+          const uint32_t u = (uint32_t)(j / T2_NS);
+          if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+            ok = false;
+            break;
+          }
+          uint8_t *st = smem + s * T2_STAGE;
+          if (c < nch1) {
+            const int w = min(T2_W, n16 - c * T2_W);
+            const uint32_t bx = (uint32_t)(m16 * w * 4), by = (uint32_t)(p16 * w * 4);
+            tc::mbar_arrive_expect_tx(&B->full[s], bx + by);
+            tc::bulk_g2s(st, optiles + e.xt + (uint64_t)128 * m16 * c, bx, &B->full[s]);
+            tc::bulk_g2s(st + T2_HALF, psitiles + e.yt + (uint64_t)128 * p16 * c, by, &B->full[s]);
+          } else {
+            const int c2 = c - nch1, w = min(T2_W, p16 - c2 * T2_W);
+            const uint32_t bz = (uint32_t)(q16 * w * 4);
+            tc::mbar_arrive_expect_tx(&B->full[s], bz);
+            tc::bulk_g2s(st + T2_HALF, optiles + e.zt + (uint64_t)128 * q16 * c2, bz, &B->full[s]);
           }
         }
-      } else {
-        for (int c0 = 0; c0 < pc16; c0 += 16) {
+      }
+      // copies in flight land before the CTA exits (bounded)
+      for (int s = 0; s < T2_NS; ++s) {
+        int jl = j - 1;
+        while (jl >= 0 && jl % T2_NS != s) --jl;
+        if (jl >= 0) tc::mbar_wait(&B->full[s], (uint32_t)(jl / T2_NS) & 1u, kMaxWaitTries);
+      }
+    }
+  } else if (warp == 5) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      int j = 0, le = 0;
+      uint32_t cvpar = 0;
+      bool dfirst = true, ok = true;
+      for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
+        const TcEntry e = E[ei];
+        const int n16 = ceil16(e.n), p16 = ceil16(e.p);
+        const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+        if (le > 0) {
+          if (!t2_wait1(&B->tempty, (uint32_t)(le - 1) & 1u, abort, status)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+        }
+        const uint32_t id1 = tc::idesc_bf16(128, p16), id2 = tc::idesc_bf16(128, q16);
+        for (int c = 0; c < nch1 && ok; ++c, ++j) {
+          const int s = j % T2_NS;
+          const uint32_t u = (uint32_t)(j / T2_NS);
+          if (!t2_wait1(&B->full[s], u & 1u, abort, status)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const int w = min(T2_W, n16 - c * T2_W);
+          const uint32_t sbo = (uint32_t)(w / 8) * 128;
+          const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
+          const uint32_t alo = a + (uint32_t)(m16 * w * 2), blo = b + (uint32_t)(p16 * w * 2);
+          for (int ks = 0; ks < w / 16; ++ks) {
+            const uint32_t o = (uint32_t)ks * 256;
+            tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1,
+                         (c == 0 && ks == 0) ? 0u : 1u);
+            tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id1, 1u);
+            tc::mma_bf16(tT, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1, 1u);
+          }
+          tc::mma_commit(&B->empty[s]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&B->tfull);
+        for (int c = 0; c < nch2 && ok; ++c, ++j) {
+          const int s = j % T2_NS;
+          const uint32_t u = (uint32_t)(j / T2_NS);
+          if (!t2_wait1(&B->full[s], u & 1u, abort, status) ||
+              !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status)) {
+            ok = false;
+            break;
+          }
+          cvpar ^= 1u << s;
+          tc::fence_after();
+          const int w = min(T2_W, p16 - c * T2_W);
+          const uint32_t sbo = (uint32_t)(w / 8) * 128;
+          const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
+          const uint32_t alo = a + 8192, blo = b + (uint32_t)(q16 * w * 2);
+          for (int ks = 0; ks < w / 16; ++ks) {
+            const uint32_t o = (uint32_t)ks * 256;
+            tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
+                         dfirst ? 0u : 1u);
+            dfirst = false;
+            tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
+            tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+          }
+          tc::mma_commit(&B->empty[s]);
+        }
+      }
+      if (ok) tc::mma_commit(&B->dfull);
+      tc::mma_commit(&B->drain);  // every MMA issued above has finished before TMEM is released
+      tc::mbar_wait(&B->drain, 0, kMaxWaitTries);
+    }
+  } else {
+    // ---------------- converters (thread = row = TMEM lane)
+    const int row = tid;
+    const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
+    int j = 0, le = 0;
+    bool ok = true;
+    for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
+      const TcEntry e = E[ei];
+      const int n16 = ceil16(e.n), p16 = ceil16(e.p);
+      const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+      const float f = e.f;
+      j += nch1;
+      if (!t2_waitw(&B->tfull, (uint32_t)le & 1u, abort, status)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+      for (int c = 0; c < nch2; ++c, ++j) {
+        const int s = j % T2_NS;
+        const uint32_t u = (uint32_t)(j / T2_NS);
+        if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const int w = min(T2_W, p16 - c * T2_W);
+        uint8_t *A = smem + s * T2_STAGE;
+        for (int h = 0; h < w / 16; ++h) {
           float v[16];
-          tc::tmem_ld16(tT + lane_off + (uint32_t)(p0 + c0), v);
+          tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
           if (row < m) {
 #pragma unroll
-            for (int i = 0; i < 16; ++i) {
-              const int k = c0 + i;
-              put_split(Ahi, Alo, row, k, (k < pc) ? f * v[i] : 0.f);
+            for (int g2 = 0; g2 < 2; ++g2) {
+              __align__(16) __nv_bfloat16 hb[8], lb[8];
+#pragma unroll
+              for (int i = 0; i < 8; ++i) tc::split_bf16(f * v[8 * g2 + i], hb[i], lb[i]);
+              uint8_t *dst = A + ((row >> 3) * (w >> 3) + 2 * h + g2) * 128 + (row & 7) * 16;
+              *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
+              *reinterpret_cast<uint4 *>(dst + 8192) = *reinterpret_cast<const uint4 *>(lb);
             }
           }
         }
+        tc::fence_async_smem();
+        __syncwarp();
+        if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
       }
-      // B row j = column j of Z, j < q (consecutive threads take consecutive j)
-      for (int idx = tid; idx < q * pc16; idx += 128) {
-        const int k = idx / q, j = idx % q;
-        float z = 0.f;
-        if (k < pc) z = zid ? ((p0 + k == j) ? 1.f : 0.f) : Z[(int64_t)(p0 + k) * e.zrs + (int64_t)j * e.zcs];
-        put_split(Bhi, Blo, j, k, z);
-      }
-      publish();
-      if (tid == 0) issue3(tD, sAhi, sAlo, sBhi, sBlo, (pc + 15) / 16, tc::idesc_bf16(128, q16), d_first);
-      d_first = false;
-      failed = !commit_wait();
+      if (!ok) break;
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&B->tempty);
     }
-  }
-  if (failed) {
-    if (tid == 0) atomicExch(status, 1);
-  } else if (!d_first) {
-    double *D = reinterpret_cast<double *>(db + g.d * 8ull);
-    for (int c0 = 0; c0 < q16; c0 += 16) {
-      float v[16];
-      tc::tmem_ld16(tD + lane_off + (uint32_t)c0, v);
-      if (row < m) {
+    if (ok && t2_waitw(&B->dfull, 0, abort, status)) {
+      tc::fence_after();
+      double *D = reinterpret_cast<double *>(db + g.d * 8ull);
+      for (int c0 = 0; c0 < q16; c0 += 16) {
+        float v[16];
+        tc::tmem_ld16(tD + lane_off + (uint32_t)c0, v);
+        if (row < m) {
 #pragma unroll
-        for (int i = 0; i < 16; ++i)
-          if (c0 + i < q) D[(int64_t)row * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
+          for (int i = 0; i < 16; ++i)
+            if (c0 + i < q) D[(int64_t)row * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
+        }
       }
     }
   }
+  __syncwarp();  // lanes 1-31 of the producer and MMA warps rejoin lane 0
   tc::fence_before();
   __syncthreads();
   if (warp == 0) tc::tmem_dealloc(tbase, 256);
 }
 
-static constexpr int TC_SMEM = 4 * TC_TILE + 64;
-// request enough shared memory that at most two CTAs (2 x 256 TMEM columns) share an SM
-static constexpr int TC_SMEM_LAUNCH = 100 * 1024;
-
-cudaError_t launch_chain_tc(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb, uint64_t yb,
-                            uint64_t zb, uint64_t db, int *status, cudaStream_t s) {
+cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
+                             const uint8_t *psitiles, uint64_t db, int *status, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
-  static_assert(TC_SMEM <= TC_SMEM_LAUNCH, "shared memory budget");
-  cudaError_t err = cudaFuncSetAttribute(chain_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         TC_SMEM_LAUNCH);
+  static_assert(T2_SMEM <= T2_SMEM_LAUNCH, "shared memory budget");
+  cudaError_t err = cudaFuncSetAttribute(chain_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         T2_SMEM_LAUNCH);
   if (err != cudaSuccess) return err;
-  chain_tc_kernel<<<ngroups, 128, TC_SMEM_LAUNCH, s>>>(e, g, xb, yb, zb, db, status);
+  add_kernel_launches(1);
+  chain_tc2_kernel<<<ngroups, T2_THREADS, T2_SMEM_LAUNCH, s>>>(e, g, optiles, psitiles, db, status);
   return cudaGetLastError();
 }
 

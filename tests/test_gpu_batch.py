@@ -1,8 +1,9 @@
 """Batched independent instances: one grouped, graph-replayed H.psi over several contexts.
 
 Each instance's block of the batched sigma must equal that instance's own
-dmrg_hpsi (same tasks, chunked differently: 1e-12 relative), on the first
-(direct) and later (CUDA-graph replay) calls.
+dmrg_hpsi (same tasks, chunked differently: 1e-12 relative in FP64, the
+working precision's rounding otherwise), on the first (direct) and later
+(CUDA-graph replay) calls.
 """
 import numpy as np
 import pytest
@@ -12,10 +13,10 @@ from paper_2001_04890_gb300 import binding, workloads
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("prec", [binding.PREC_FP64, binding.PREC_FP32])
+@pytest.mark.parametrize("prec", [binding.PREC_FP64, binding.PREC_FP32, binding.PREC_BF16X3])
 def test_batched_hpsi_equals_per_instance(prec):
     ctxs = []
-    for seed, (L, M) in enumerate([(8, 40), (10, 64), (7, 24), (12, 80)]):
+    for seed, (L, M) in enumerate([(8, 40), (10, 64), (7, 24), (12, 320)]):  # last: blocks > 32
         h, v = workloads.integrals(L, seed=seed)
         tsz = L % 2  # odd N: lowest |Sz|
         c = binding.DMRG(h, v, L, tsz, M, precision=prec)
@@ -30,7 +31,8 @@ def test_batched_hpsi_equals_per_instance(prec):
     batch = binding.Batch(ctxs)
     assert batch.offsets[-1] == sum(len(p) for p in psis)
     x = np.concatenate(psis)
-    tol = 1e-12 if prec == binding.PREC_FP64 else 1e-6
+    # FP32 / tensor-core partials are summed in another chunking: FP32 / split-BF16 rounding
+    tol = {binding.PREC_FP64: 1e-12, binding.PREC_FP32: 1e-6, binding.PREC_BF16X3: 1e-4}[prec]
     for _ in range(3):  # direct run, then graph replays
         y = batch.hpsi(x)
         for i, r in enumerate(refs):

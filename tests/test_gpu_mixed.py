@@ -72,3 +72,26 @@ def test_bf16x3_tensor_core_hpsi_matches_oracle():
     e64, _ = ctx64.davidson(tol=1e-8, max_iter=400)
     ctx64.close()
     assert abs(e - e64) < 1e-8, (e, e64)
+
+
+@pytest.mark.parametrize("L,M", [(12, 800), (14, 1100)])
+def test_bf16x3_tensor_core_hpsi_large_blocks(L, M):
+    """Output blocks up to 128 states (several 32-wide K chunks, ragged tails) on the
+    tensor cores: H.psi within split-BF16 accuracy of the FP64 path (itself pinned to
+    the oracle), over repeated calls (psi tiles rebuilt per call)."""
+    N, k = L, (L - 2) // 2
+    h, v = workloads.integrals(L, seed=0)
+    out = {}
+    for prec in (binding.PREC_FP64, binding.PREC_BF16X3):
+        ctx = binding.DMRG(h, v, N, 0, M, precision=prec)
+        workloads.grow_middle_bond(ctx, L, N // 2, N // 2, M, k, seed=0)
+        for side in (0, 1):
+            dims = ctx.block_sectors(side)[:, 2]
+            assert dims.max() > 64 and ((dims > 32) & (dims <= 128)).any()
+        _, dim = ctx.psi_layout()
+        ys = [ctx.hpsi(workloads.gaussian(dim, seed=s)) for s in (1, 2)]
+        out[prec] = ys
+        ctx.close()
+    for a, b in zip(out[binding.PREC_FP64], out[binding.PREC_BF16X3]):
+        err = np.max(np.abs(a - b)) / np.max(np.abs(a))
+        assert err < 2e-4, err
