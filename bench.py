@@ -50,7 +50,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, recipe table)
 
 # DRAM bytes (read + write) per launch of the dominant H.psi kernel, from one ncu
 # capture of the unchanged kernel at that workload and precision (else null)
-TRAFFIC_PER_LAUNCH = {("c2", 0, 512): 1.016e9 + 0.039e9}
+TRAFFIC_PER_LAUNCH = {
+    ("c2", 0, 512, (32768.0, 50000.0, 33, 0, 0)): 1.034e9 + 0.147e9,
+}
 
 
 def _clock_sampler():
@@ -127,6 +129,12 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
     torch.cuda.set_device(dev)
     stream = torch.cuda.Stream()
     ctx, k = _setup(wl, precision, stream, dev)
+    tune = None
+    if getattr(args, "tune", ""):
+        ctx.set_tune(**_fixed_tune(args.tune))
+        tune = ctx.get_tune()
+    elif getattr(args, "autotune", False):
+        tune_ms, tune = ctx.autotune(reps=2)  # plan-time choice of the launch shape (untimed)
     blocks, dim = ctx.psi_layout()
     flops_per_hpsi, ntasks = ctx.hpsi_flops()
     psi0_host = workloads.gaussian(dim, seed=1)
@@ -201,11 +209,22 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
         step_ms_max = float(t.item())
     ctx.close()
     return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st,
-                step_ms=step_ms_max, iters=iters, energy=energy, e2e_ms=e2e_ms,
+                step_ms=step_ms_max, iters=iters, energy=energy, e2e_ms=e2e_ms, tune=tune,
                 h2d=psi0_host.nbytes, d2h=d2h_bytes, clocks=clocks, k=k, e_mid=e_mid, psi_mid=psi_mid)
 
 
-def profile_hpsi(wl, precision, ncalls):
+def _shape_key(tune):
+    if not tune:
+        return None
+    return (tune["target_chunks"], tune["min_chunk"], tune["tc_min"], tune["by_work"], tune["flat_wide"])
+
+
+def _fixed_tune(spec):
+    t = [float(x) for x in spec.split(",")]
+    return dict(target_chunks=t[0], min_chunk=t[1], tc_min=int(t[2]), by_work=int(t[3]), flat_wide=int(t[4]))
+
+
+def profile_hpsi(wl, precision, ncalls, autotune=False, tune_spec=""):
     """Setup, then ncalls H.psi launches inside an NVTX range "hpsi" (for ncu --nvtx)."""
     import torch
     from paper_2001_04890_gb300 import workloads
@@ -216,7 +235,12 @@ def profile_hpsi(wl, precision, ncalls):
     setup_s = time.perf_counter() - t0
     _, dim = ctx.psi_layout()
     psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
+    if tune_spec:
+        ctx.set_tune(**_fixed_tune(tune_spec))
     ctx.hpsi(psi)  # builds the task list and temporaries outside the range
+    tune = ctx.autotune(reps=2)[1] if (autotune and not tune_spec) else ctx.get_tune()
+    ctx.hpsi(psi)
+    ctx.stats(reset=True)
     torch.cuda.synchronize()
     torch.cuda.nvtx.range_push("hpsi")
     for _ in range(ncalls):
@@ -225,7 +249,7 @@ def profile_hpsi(wl, precision, ncalls):
     torch.cuda.nvtx.range_pop()
     st = ctx.stats()
     print(json.dumps({"profile": wl["name"], "precision": precision, "hpsi_calls": ncalls,
-                      "setup_s": setup_s, "psi_dim": dim,
+                      "setup_s": setup_s, "psi_dim": dim, "tune": tune,
                       "hpsi_ms_avg": st["hpsi_ms"] / max(st["hpsi_calls"], 1),
                       "gflop_per_hpsi": ctx.hpsi_flops()[0] / 1e9}), flush=True)
     ctx.close()
@@ -256,6 +280,7 @@ def batched_workload(args, wl):
             ctxs.append(c)
         setup_s = time.perf_counter() - t0
         batch = binding.Batch(ctxs)
+        tune = batch.autotune(reps=2)[1] if args.autotune else None
         with torch.cuda.stream(stream):
             x = torch.from_numpy(workloads.gaussian(batch.offsets[-1], seed=1)).cuda()
         stream.synchronize()
@@ -288,7 +313,7 @@ def batched_workload(args, wl):
             its += it
             energies.append(e)
         dav_s = time.perf_counter() - t0
-        res[name] = {"setup_s": setup_s, "batched_hpsi_ms": t_batch,
+        res[name] = {"setup_s": setup_s, "launch_shape": tune, "batched_hpsi_ms": t_batch,
                      "batched_hpsi_tflops": batch.flops / (t_batch * 1e-3) / 1e12,
                      "per_instance_hpsi_ms": t_seq,
                      "per_instance_hpsi_tflops": batch.flops / (t_seq * 1e-3) / 1e12,
@@ -313,6 +338,103 @@ def batched_workload(args, wl):
         res[name]["max_abs_dE_vs_fp64_first16"] = float(np.max(np.abs(np.array(res[name]["energies_head"]) - e64)))
         del res[name]["energies_head"]
     out.update(res)
+    return out
+
+
+def sweep_workload(args, wl):
+    """Full two-site sweeps from the Aufbau start (Sec. 2.1) per working precision.
+
+    Reports the wall time per sweep (every Davidson to tol, truncation and
+    renormalization of every position, both directions), the lowest energy of
+    each sweep and, for the mixed precisions, |dE| against the FP64 run.
+    """
+    import torch
+    from paper_2001_04890_gb300 import binding, workloads
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    L, N, two_sz, M = wl["L"], wl["N"], wl["two_sz"], wl["M"]
+    h, v = workloads.integrals(L, seed=0)
+    out = {"workload": wl["name"], "sweeps": args.sweeps, "davidson_tol": wl["tol"],
+           "positions_per_sweep": 2 * (L - 2)}
+    ref = None
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16x3", 2)):
+        ctx = binding.DMRG(h, v, N, two_sz, M, prec, stream=stream.cuda_stream)
+        if args.tune:
+            ctx.set_tune(**_fixed_tune(args.tune))
+        torch.cuda.synchronize()
+        per = []
+        energies = []
+        for _ in range(args.sweeps):
+            t0 = time.perf_counter()
+            e = ctx.sweep(1, tol=wl["tol"])
+            torch.cuda.synchronize()
+            per.append(time.perf_counter() - t0)
+            energies.append(float(np.min(e)))
+        st = ctx.stats()
+        r = {"s_per_sweep": per, "min_energy_per_sweep": energies,
+             "davidson_iters": st["davidson_iters"], "davidson_iters_lowp": st["davidson_iters_lowp"]}
+        if ref is None:
+            ref = energies
+        else:
+            r["abs_dE_vs_fp64_per_sweep"] = [abs(a - b) for a, b in zip(energies, ref)]
+            r["speedup_vs_fp64_last_sweep"] = out["fp64"]["s_per_sweep"][-1] / per[-1]
+        out[name] = r
+        print(json.dumps({name: r}), flush=True)
+        ctx.close()
+    return out
+
+
+def mixed_step_workload(args, wl, tol):
+    """One middle-bond step per working precision on the same bases and start vector.
+
+    Davidson to tol (mixed: low-precision matvecs, then the FP64 defect-corrected
+    refinement), truncation and renormalization; wall time of each part, H.psi
+    counts, |dE| and the state overlap against the FP64 step.
+    """
+    import torch
+    from paper_2001_04890_gb300 import workloads
+    torch.cuda.set_device(0)
+    stream = torch.cuda.Stream()
+    out = {"workload": wl["name"], "davidson_tol": tol}
+    ref = None
+    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16x3", 2)):
+        t0 = time.perf_counter()
+        ctx, k = _setup(wl, prec, stream, 0)
+        setup_s = time.perf_counter() - t0
+        if args.tune:
+            ctx.set_tune(**_fixed_tune(args.tune))
+        elif args.autotune:
+            ctx.autotune(reps=1)
+        _, dim = ctx.psi_layout()
+        psi0 = workloads.gaussian(dim, seed=1)
+        psi0 /= np.linalg.norm(psi0)
+        ctx.set_position(k, 1)
+        ctx.set_psi(psi0)
+        ctx.stats(reset=True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        e, it = ctx.davidson(tol=tol, max_iter=400, allow_noconv=True)
+        torch.cuda.synchronize()
+        t_dav = time.perf_counter() - t0
+        st = ctx.stats(reset=True)
+        x = ctx.get_psi()
+        t0 = time.perf_counter()
+        ctx.renormalize(+1)
+        torch.cuda.synchronize()
+        t_ren = time.perf_counter() - t0
+        r = {"setup_s": setup_s, "launch_shape": ctx.get_tune(), "davidson_s": t_dav, "iters": it,
+             "iters_lowp": st["davidson_iters_lowp"], "iters_fp64": it - st["davidson_iters_lowp"],
+             "hpsi_ms_avg": st["hpsi_ms"] / max(st["hpsi_calls"], 1), "renormalize_s": t_ren,
+             "step_s": t_dav + t_ren, "energy": e}
+        if ref is None:
+            ref = (e, x, t_dav + t_ren)
+        else:
+            r["abs_dE_vs_fp64"] = abs(e - ref[0])
+            r["overlap_vs_fp64"] = float(abs(np.dot(x, ref[1])))
+            r["step_speedup_vs_fp64"] = ref[2] / (t_dav + t_ren)
+        out[name] = r
+        print(json.dumps({name: r}), flush=True)
+        ctx.close()
     return out
 
 
@@ -379,6 +501,14 @@ def main():
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="setup, then N H.psi calls in an NVTX range 'hpsi' (for ncu); no JSON line")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--no-autotune", dest="autotune", action="store_false",
+                    help="keep the default launch shape instead of timing candidates at plan time")
+    ap.add_argument("--mixed-step", type=float, default=0.0, metavar="TOL",
+                    help="one middle-bond step per precision to Davidson tolerance TOL (FP64 vs mixed)")
+    ap.add_argument("--sweeps", type=int, default=0, metavar="S",
+                    help="time S full sweeps from the start state per precision (instead of the step)")
+    ap.add_argument("--tune", default="", metavar="T,MIN,TC,ORDER,WIDE",
+                    help="fixed launch shape (target_chunks,min_chunk,tc_min,by_work,flat_wide); no autotuning")
     ap.add_argument("--M", type=int, default=0, help="override the workload's bond dimension (profiling)")
     ap.add_argument("--large", action="store_true",
                     help="middle-bond measurement of a large workload in every precision (JSON lines)")
@@ -403,8 +533,14 @@ def main():
     if args.large:
         print(json.dumps(large_workload(wl)))
         return 0
+    if args.sweeps:
+        print(json.dumps(sweep_workload(args, wl)))
+        return 0
+    if args.mixed_step:
+        print(json.dumps(mixed_step_workload(args, wl, args.mixed_step)))
+        return 0
     if args.profile_hpsi:
-        profile_hpsi(wl, prec, args.profile_hpsi)
+        profile_hpsi(wl, prec, args.profile_hpsi, args.autotune, args.tune)
         return 0
     if world > 1:
         import torch
@@ -434,6 +570,7 @@ def main():
         "config": {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"],
                    "M": wl["M"], "position": r["k"], "psi_dim": r["dim"], "hpsi_tasks": r["ntasks"],
                    "davidson_tol": wl["tol"], "l2": "flushed between timed steps (256 MB write)",
+                   "launch_shape": r["tune"],
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "davidson_s_per_iter": (r["step_ms"] * 1e-3) / max(dav_iters, 1),
         "davidson_iters_per_step": dav_iters / K,
@@ -448,7 +585,7 @@ def main():
             "peak_source": "nominal GB300 FP64 from the recipe table (no measured FP64 peak in MEASURED_PEAKS.json)",
             "unit": "TFLOP/s",
             "frac": (kernel_tflops / FP64_NOMINAL_TFLOPS) if kernel_tflops else None,
-            "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, prec, wl["M"])),
+            "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, prec, wl["M"], _shape_key(r["tune"]))),
         },
         "e2e": {"value": hpsi_flops / (r["e2e_ms"] * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},

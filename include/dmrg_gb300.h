@@ -229,33 +229,36 @@ int dmrg_batch_free(dmrg_batch *batch);
 /*
  * Launch-shape autotuning of the H.psi task list (the grouped launch of the
  * sector-pair products of Sec. 2.2.1, Eq. dgemm; the paper has no counterpart:
- * its task sizes are fixed by the MPI distribution).  Four parameters shape a
+ * its task sizes are fixed by the MPI distribution).  Five parameters shape a
  * task list: target_chunks (the work of all output blocks is cut into about
  * this many equal-work chunks), min_chunk (no chunk lighter than this many
  * FLOPs), tc_min (output blocks with a side >= tc_min and both sides <= 128
- * run on the tensor-core kernel in DMRG_PREC_BF16X3) and by_work (1: chunks
- * launched heaviest first; 0: in output-block order).  Defaults: 8192, 2e5,
- * 33, 0.
+ * run on the tensor-core kernel in DMRG_PREC_BF16X3), by_work (1: chunks
+ * launched heaviest first; 0: in output-block order) and flat_wide (1: the
+ * kernel for blocks of at most 32 x 32 runs one wide CTA per SM, 0: two
+ * narrower CTAs per SM).  Defaults: 8192, 2e5, 33, 0, 1.
  *
  * dmrg_autotune builds candidate task lists for the current position, times
  * `reps` complete H.psi launch sequences of each (CUDA events, on a seeded
  * vector; synchronizes the stream), keeps the fastest for this and later
  * positions and rebuilds the position's task lists with it.  best_ms (may be
  * NULL) receives the time of one H.psi with the chosen shape; params (may be
- * NULL, 4 doubles) the chosen target_chunks, min_chunk, tc_min, by_work.  Results of
+ * NULL, 5 doubles) the chosen target_chunks, min_chunk, tc_min, by_work,
+ * flat_wide.  Results of
  * H.psi differ between shapes only by floating-point summation order.
  * Errors: DMRG_EINVAL (NULL context, reps < 1), DMRG_ESTATE (blocks of the
  * position not built), DMRG_ETIMEOUT, DMRG_ECUDA.
  * dmrg_set_tune sets the parameters without timing (DMRG_EINVAL unless
- * target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, by_work 0 or 1);
- * the task lists are rebuilt on next use.  dmrg_get_tune writes the current
- * four parameters.
+ * target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, by_work and
+ * flat_wide 0 or 1); the task lists are rebuilt on next use.  dmrg_get_tune
+ * writes the current five parameters.
  * dmrg_batch_autotune does the same for a batch (every context still at the
  * position it had at dmrg_batch_create, else DMRG_ESTATE); the CUDA graph of
  * the batch is captured again on the next dmrg_batch_hpsi.
  */
 int dmrg_autotune(dmrg_ctx *ctx, int reps, double *best_ms, double *params);
-int dmrg_set_tune(dmrg_ctx *ctx, double target_chunks, double min_chunk, int tc_min, int by_work);
+int dmrg_set_tune(dmrg_ctx *ctx, double target_chunks, double min_chunk, int tc_min, int by_work,
+                  int flat_wide);
 int dmrg_get_tune(dmrg_ctx *ctx, double *params);
 int dmrg_batch_autotune(dmrg_batch *batch, int reps, double *best_ms, double *params);
 

@@ -67,7 +67,7 @@ def lib():
         "dmrg_batch_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
         "dmrg_batch_free": (C.c_int, [vp]),
         "dmrg_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
-        "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int]),
+        "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
         "dmrg_get_tune": (C.c_int, [vp, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -276,17 +276,19 @@ class DMRG:
     def autotune(self, reps=3):
         """Time candidate launch shapes of this position's H.psi task list; keep the fastest.
 
-        Returns (ms per H.psi with the chosen shape, {target_chunks, min_chunk, tc_min, by_work})."""
+        Returns (ms per H.psi with the chosen shape, {target_chunks, min_chunk, tc_min, by_work,
+        flat_wide})."""
         ms = C.c_double()
-        par = np.zeros(4)
+        par = np.zeros(5)
         _check(lib().dmrg_autotune(self.ctx, reps, C.byref(ms), _dptr(par)))
         return ms.value, _tune_dict(par)
 
-    def set_tune(self, target_chunks=8192.0, min_chunk=2.0e5, tc_min=33, by_work=0):
-        _check(lib().dmrg_set_tune(self.ctx, float(target_chunks), float(min_chunk), int(tc_min), int(by_work)))
+    def set_tune(self, target_chunks=8192.0, min_chunk=2.0e5, tc_min=33, by_work=0, flat_wide=1):
+        _check(lib().dmrg_set_tune(self.ctx, float(target_chunks), float(min_chunk), int(tc_min), int(by_work),
+                                   int(flat_wide)))
 
     def get_tune(self):
-        par = np.zeros(4)
+        par = np.zeros(5)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
 
@@ -300,7 +302,7 @@ class DMRG:
 
 def _tune_dict(par):
     return {"target_chunks": float(par[0]), "min_chunk": float(par[1]), "tc_min": int(par[2]),
-            "by_work": int(par[3])}
+            "by_work": int(par[3]), "flat_wide": int(par[4])}
 
 
 class Batch:
@@ -335,7 +337,7 @@ class Batch:
 
         Returns (ms per batched H.psi with the chosen shape, parameters)."""
         ms = C.c_double()
-        par = np.zeros(4)
+        par = np.zeros(5)
         _check(lib().dmrg_batch_autotune(self.h, reps, C.byref(ms), _dptr(par)))
         return ms.value, _tune_dict(par)
 

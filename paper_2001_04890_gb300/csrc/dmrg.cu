@@ -277,7 +277,9 @@ struct ChainTune {
   double target_chunks = 8192.0;
   double min_chunk = 2.0e5;
   int tc_min = 33;
-  int by_work = 0;  // 1: launch groups heaviest first; 0: in output-block order (operand locality)
+  int by_work = 0;     // 1: launch groups heaviest first; 0: in output-block order (operand locality)
+  int flat_wide = 1;   // flat kernel CTAs: 1 = one wide CTA per SM (6 FP64 / 12 FP32 warps),
+                       // 0 = two narrower CTAs per SM (4 / 8 warps each)
 };
 
 // A task list on the device.  Output blocks of at most 32 x 32 go to the
@@ -299,7 +301,9 @@ struct DevChain {
   DBuf<TcGroup> tcg;
   DBuf<PsiTileSpec> pts;
   DBuf<uint8_t> optiles, psitiles;
+  DBuf<int> tc_counter;  // work counter of the persistent tensor-core kernel
   int npts = 0;
+  int flat_wide = 1;
   int nall = 0, nbig = 0, nflat = 0, ntc = 0, ntiles = 0, nred = 0;
   int64_t nent = 0;
   int64_t red_total = 0, scratch_n = 0;
@@ -310,6 +314,7 @@ struct DevChain {
     std::vector<ChainGroup> vb, vf, vt;
     std::vector<ReduceGroup> vr;
     split = split_tasks;
+    flat_wide = tune.flat_wide;
     int tiles = 0;
     int64_t soff = 0, e0 = 0;
     // per-entry work for chunking
@@ -464,6 +469,7 @@ struct DevChain {
     pts.upload(ps, s);
     optiles.alloc((size_t)opbytes);
     psitiles.alloc((size_t)psibytes);
+    tc_counter.alloc(1);
     DBuf<TileSpec> tsd;
     tsd.upload(ts, s);
     CK(launch_build_tiles(tsd.p, (int)ts.size(), optiles.p, s));
@@ -474,7 +480,7 @@ struct DevChain {
     if (ntc == 0) return;
     if (!status) throw Fail{DMRG_EINVAL, "tensor-core task list launched without a status word"};
     CK(launch_psi_tiles(pts.p, npts, reinterpret_cast<const double *>(yb), psitiles.p, s));
-    CK(launch_chain_tc2(tce.p, tcg.p, ntc, optiles.p, psitiles.p, tb, status, s));
+    CK(launch_chain_tc2(tce.p, tcg.p, ntc, optiles.p, psitiles.p, tb, tc_counter.p, status, s));
   }
 
   void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s,
@@ -483,11 +489,11 @@ struct DevChain {
     if (split && scratch_n > 0) CK(cudaMemsetAsync(scratch.p, 0, scratch_n * sizeof(double), s));
     if (f32ops) {
       CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
       launch_tc(yb, tb, status, s);
     } else {
       CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
     }
     if (split) CK(launch_reduce_partials(red.p, nred, red_total, scratch.p, (double *)(uintptr_t)db, s));
   }
@@ -500,11 +506,11 @@ struct DevChain {
     if (scratch_n > 0) CK(cudaMemsetAsync(ext, 0, scratch_n * sizeof(double), s));
     if (f32ops) {
       CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
       launch_tc(yb, tb, status, s);
     } else {
       CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
     }
     CK(launch_reduce_partials(red.p, nred, red_total, ext, (double *)(uintptr_t)db, s));
   }
@@ -1493,23 +1499,164 @@ static void davidson_core(dmrg_ctx *c, double tol, double floor_rel, int max_ite
   if (iters) *iters = std::min(it, max_iter);
 }
 
+// Refinement of a low-precision Ritz vector x to an FP64 residual (defect
+// correction inside Davidson).  Each outer step applies H to x in FP64 (the
+// exact residual r = Hx - theta x, the convergence test and the Rayleigh
+// quotient theta), then expands the subspace [x, t_1, t_2, ...] with
+// low-precision matvecs only.  The coupling of x to the corrections is taken
+// from the exact Hx (G_0i = (Hx) . t_i, by symmetry), so the low-precision
+// error enters only through the t_i^T H t_j block, i.e. scaled by the size of
+// the correction: each outer step reduces the residual by about the
+// low-precision accuracy times ||H|| / gap instead of stalling at it.
+// Returns false if the exact residual stopped improving (the caller then
+// finishes with FP64 matvecs).
+static bool davidson_refine(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters,
+                            int *iters_lowp, bool &conv) {
+  build_hplan(c);
+  HPlan &P = c->plan;
+  const int64_t n = P.psi.dim;
+  const int kmax = (int)std::min<int64_t>(24, std::max<int64_t>(n, 1));
+  c->V.alloc((size_t)kmax * n);
+  c->AV.alloc((size_t)kmax * n);
+  c->r.alloc(n);
+  c->t.alloc(n);
+  c->hx.alloc(n);
+  c->partial.alloc((size_t)dots_partial_blocks(n) * 32);
+  c->small.alloc(4096);
+  double *G = c->small.p, *evals = c->small.p + 1024, *evecs = c->small.p + 1056;
+  double *dots = c->small.p + 2200, *scal = c->small.p + 2300, *dot0 = c->small.p + 2400;
+  cudaStream_t s = c->stream;
+  auto get = [&](const double *d) {
+    double v;
+    CK(cudaMemcpyAsync(&v, d, sizeof(double), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return v;
+  };
+  auto norm2 = [&](const double *x) {
+    CK(launch_dots(x, 1, n, x, c->partial.p, scal + 1, s));
+    return get(scal + 1);
+  };
+  CK(cudaMemcpyAsync(c->V.p, c->psi.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(launch_dots(c->V.p, 1, n, c->V.p, c->partial.p, scal + 1, s));
+  CK(launch_scale(c->V.p, scal + 1, 1, n, s));
+  int it = 0, itl = 0, stalls = 0;
+  double theta = 0.0, best = 1e300;
+  bool ok = true;
+  conv = false;
+  std::vector<double> Gh(32 * 32, 0.0);
+  for (;;) {
+    // ---- outer step: exact H x, theta, residual
+    hpsi_dev(c, c->V.p, c->AV.p, true);
+    ++it;
+    CK(launch_dots(c->V.p, 1, n, c->AV.p, c->partial.p, dots, s));
+    theta = get(dots);
+    CK(cudaMemcpyAsync(scal, &theta, sizeof(double), cudaMemcpyHostToDevice, s));
+    CK(launch_residual(c->r.p, c->AV.p, c->V.p, scal, n, s));
+    const double rnorm = std::sqrt(std::max(norm2(c->r.p), 0.0));
+    c->last_resid = rnorm;
+    if (rnorm <= tol) {
+      conv = true;
+      break;
+    }
+    if (rnorm < 0.5 * best) {
+      best = rnorm;
+      stalls = 0;
+    } else if (++stalls >= 2) {
+      ok = false;
+      break;
+    }
+    if (it >= max_iter) break;
+    std::fill(Gh.begin(), Gh.end(), 0.0);
+    Gh[0] = theta;
+    int k = 1;
+    // ---- inner expansion with low-precision matvecs
+    for (;;) {
+      CK(launch_precond(c->t.p, c->r.p, P.diag.p, scal, n, s));
+      double t2 = 0.0;
+      for (int attempt = 0; attempt < 2; ++attempt) {
+        if (attempt == 1) CK(cudaMemcpyAsync(c->t.p, c->r.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+        for (int pass = 0; pass < 2; ++pass) {
+          CK(launch_dots(c->V.p, k, n, c->t.p, c->partial.p, dots, s));
+          CK(launch_sub_proj(c->t.p, c->V.p, dots, k, n, s));
+        }
+        t2 = norm2(c->t.p);
+        if (t2 > 1e-28) break;
+      }
+      if (!(t2 > 1e-28)) break;  // nothing new to add: take the current Ritz vector
+      CK(launch_scale(c->t.p, scal + 1, 1, n, s));
+      CK(cudaMemcpyAsync(c->V.p + (int64_t)k * n, c->t.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      hpsi_dev(c, c->V.p + (int64_t)k * n, c->AV.p + (int64_t)k * n, false);
+      ++it;
+      ++itl;
+      CK(launch_dots(c->V.p, k + 1, n, c->AV.p + (int64_t)k * n, c->partial.p, dots, s));
+      CK(launch_dots(c->AV.p, 1, n, c->t.p, c->partial.p, dot0, s));  // exact (H x) . t
+      std::vector<double> col(k + 1);
+      CK(cudaMemcpyAsync(col.data(), dots, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(col.data(), dot0, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i <= k; ++i) {
+        Gh[i * 32 + k] = col[i];
+        Gh[k * 32 + i] = col[i];
+      }
+      ++k;
+      // Ritz pair of the subspace; estimated residual
+      CK(cudaMemcpyAsync(G, Gh.data(), 32 * 32 * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(launch_jacobi_eigh(G, k, 32, evals, evecs, s));
+      std::vector<double> Y((size_t)k * k);
+      double th;
+      CK(cudaMemcpyAsync(&th, evals, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(Y.data(), evecs, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      std::vector<double> y0(k);
+      for (int i = 0; i < k; ++i) y0[i] = Y[(size_t)i * k];
+      CK(cudaMemcpyAsync(dots, y0.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(cudaMemcpyAsync(scal, &th, sizeof(double), cudaMemcpyHostToDevice, s));
+      CK(launch_combine(c->psi.p, c->V.p, dots, k, n, 0.0, s));
+      CK(launch_combine(c->hx.p, c->AV.p, dots, k, n, 0.0, s));
+      CK(launch_residual(c->r.p, c->hx.p, c->psi.p, scal, n, s));
+      const double rest = std::sqrt(std::max(norm2(c->r.p), 0.0));
+      if (rest <= std::max(0.01 * rnorm, 0.5 * tol) || k == kmax || it >= max_iter) break;
+    }
+    if (k == 1) {
+      ok = false;  // the subspace could not grow
+      break;
+    }
+    // the Ritz vector becomes x of the next outer step
+    CK(cudaMemcpyAsync(c->V.p, c->psi.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+    CK(launch_dots(c->V.p, 1, n, c->V.p, c->partial.p, scal + 1, s));
+    CK(launch_scale(c->V.p, scal + 1, 1, n, s));
+  }
+  CK(cudaMemcpyAsync(c->psi.p, c->V.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+  CK(cudaStreamSynchronize(s));
+  c->psi_valid = true;
+  c->dav_iters += it;
+  if (energy) *energy = theta;
+  if (iters) *iters = it;
+  if (iters_lowp) *iters_lowp = itl;
+  return ok;
+}
+
 // Davidson at the working precision.  In mixed precision the low-precision
-// matvecs run down to their attainable residual (~1e-6 |E|), then Davidson
-// continues from that vector with FP64 matvecs to the requested tolerance
-// (iterative refinement), so the energy and vector are FP64 quality.
+// matvecs run down to their attainable residual (~1e-6 |E|), then the
+// defect-corrected refinement above reaches the requested tolerance with a
+// few FP64 matvecs (plain FP64 Davidson finishes if it stalls), so the
+// energy and vector are FP64 quality.
 static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters, bool &conv) {
   build_hplan(c);
   if (!c->plan.lowp) {
     davidson_core(c, tol, 0.0, max_iter, true, energy, iters, conv);
     return;
   }
-  int it1 = 0, it2 = 0;
+  int it1 = 0, it2 = 0, it2l = 0, it3 = 0;
   double e = 0.0;
   davidson_core(c, tol, 1e-8, max_iter, false, &e, &it1, conv);
   c->dav_iters_lowp += it1;
-  davidson_core(c, tol, 0.0, std::max(1, max_iter - it1), true, &e, &it2, conv);
+  const bool ok = davidson_refine(c, tol, std::max(1, max_iter - it1), &e, &it2, &it2l, conv);
+  c->dav_iters_lowp += it2l;
+  if (!ok && !conv && it1 + it2 < max_iter)
+    davidson_core(c, tol, 0.0, max_iter - it1 - it2, true, &e, &it3, conv);
   if (energy) *energy = e;
-  if (iters) *iters = it1 + it2;
+  if (iters) *iters = it1 + it2 + it3;
 }
 
 }  // namespace dmrg
@@ -2157,9 +2304,10 @@ static ChainTune autotune_chain(const ChainList &CL, bool tc, bool lowp, const d
         best = t;
       }
     }
-  {
+  for (int flip = 0; flip < 2; ++flip) {
     ChainTune t = best;
-    t.by_work = 1 - best.by_work;
+    if (flip == 0) t.by_work = 1 - best.by_work;
+    else t.flat_wide = 1 - best.flat_wide;
     const double ms = run(t);
     if (ms < best_ms) {
       best_ms = ms;
@@ -2167,7 +2315,7 @@ static ChainTune autotune_chain(const ChainList &CL, bool tc, bool lowp, const d
     }
   }
   if (tc) {
-    const int tcs[] = {17, 33, 49, 65};
+    const int tcs[] = {1, 9, 17, 33, 49, 65};
     for (int v : tcs) {
       if (v == best.tc_min) continue;
       ChainTune t = best;
@@ -2188,6 +2336,7 @@ static void tune_out(const ChainTune &t, double *params) {
   params[1] = t.min_chunk;
   params[2] = t.tc_min;
   params[3] = t.by_work;
+  params[4] = t.flat_wide;
 }
 
 }  // namespace dmrg
@@ -2221,12 +2370,14 @@ extern "C" int dmrg_autotune(dmrg_ctx *c, int reps, double *best_ms, double *par
   API_END
 }
 
-extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk, int tc_min, int by_work) {
+extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk, int tc_min, int by_work,
+                             int flat_wide) {
   API_BEGIN
   if (!c || !(target_chunks >= 1.0) || !(min_chunk >= 0.0) || tc_min < 1 || tc_min > 129 ||
-      (by_work != 0 && by_work != 1))
-    throw Fail{DMRG_EINVAL,
-               "dmrg_set_tune: target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, by_work 0 or 1"};
+      (by_work != 0 && by_work != 1) || (flat_wide != 0 && flat_wide != 1))
+    throw Fail{DMRG_EINVAL, "dmrg_set_tune: target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, "
+                            "by_work and flat_wide 0 or 1"};
+  c->tune.flat_wide = flat_wide;
   c->tune.target_chunks = target_chunks;
   c->tune.min_chunk = min_chunk;
   c->tune.tc_min = tc_min;

@@ -9,7 +9,7 @@
 //               the density matrix psi psi^T of Sec. 2.1.
 // lincomb_fp64: pre-summed operators (Sec. 2.2.3, Eq. presum) as a GEMM
 //               [K_out x K_src] x [K_src x block elements] per sector.
-// Davidson helpers, a one-warp Jacobi eigensolver for the small subspace
+// Davidson helpers, a round-robin parallel Jacobi eigensolver for the small subspace
 // matrix, and a column gather that builds O from eigenvectors.
 #include <cuda_runtime.h>
 
@@ -273,11 +273,9 @@ __global__ void __launch_bounds__(32 * WARPS) chain_flat_kernel(const ChainEntry
   }
 }
 
-template <typename TX, typename TY, typename TZ, typename TA>
-static cudaError_t launch_flat(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb, uint64_t yb,
-                               uint64_t zb, uint64_t db, cudaStream_t s) {
-  if (ngroups <= 0) return cudaSuccess;
-  constexpr int WARPS = sizeof(TA) == 8 ? 6 : 12;
+template <typename TX, typename TY, typename TZ, typename TA, int WARPS>
+static cudaError_t launch_flat_w(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
+                                 uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
   const int smem = WARPS * 3 * 32 * 33 * (int)sizeof(TA);
   auto kern = chain_flat_kernel<TX, TY, TZ, TA, WARPS>;
   cudaError_t err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
@@ -287,14 +285,20 @@ static cudaError_t launch_flat(const ChainEntry *e, const ChainGroup *g, int ngr
   return cudaGetLastError();
 }
 
+// warps per CTA: FP64 6 (one CTA per SM) or 4 (two CTAs, 8 warps per SM);
+// FP32 12 (one CTA) or 8 (two CTAs, 16 warps per SM)
 cudaError_t launch_chain_flat_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
-                                   uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
-  return launch_flat<double, double, double, double>(e, g, ngroups, xb, yb, zb, db, s);
+                                   uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s, int warps) {
+  if (ngroups <= 0) return cudaSuccess;
+  if (warps == 4) return launch_flat_w<double, double, double, double, 4>(e, g, ngroups, xb, yb, zb, db, s);
+  return launch_flat_w<double, double, double, double, 6>(e, g, ngroups, xb, yb, zb, db, s);
 }
 
 cudaError_t launch_chain_flat_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
-                                     uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s) {
-  return launch_flat<float, double, float, float>(e, g, ngroups, xb, yb, zb, db, s);
+                                     uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s, int warps) {
+  if (ngroups <= 0) return cudaSuccess;
+  if (warps == 8) return launch_flat_w<float, double, float, float, 8>(e, g, ngroups, xb, yb, zb, db, s);
+  return launch_flat_w<float, double, float, float, 12>(e, g, ngroups, xb, yb, zb, db, s);
 }
 
 // out[ red.d + ...] += sum over the task chunks of their partial blocks, in chunk order
@@ -623,80 +627,123 @@ cudaError_t launch_fill_guess(double *x, int64_t n, uint64_t seed, cudaStream_t 
   return cudaGetLastError();
 }
 
-// Cyclic Jacobi eigensolver for a small symmetric matrix (n <= 32) on one warp:
-// lane i owns row i; every lane evaluates the same rotation (Rutishauser's
-// stable tangent formula), so a rotation costs two warp barriers only.
-// Eigenvalues ascending; eigenvectors as columns of evecs (row-major n x n).
-__global__ void jacobi_eigh_kernel(const double *A, int n, int lda, double *evals, double *evecs) {
+// Symmetric eigensolver for the small Davidson subspace matrix (n <= 32):
+// two-sided Jacobi with the round-robin (circle) ordering, so each round
+// applies n/2 disjoint rotations at once (they commute), one thread per pair
+// for the angles and one thread per (row, pair) for the updates.  Rotation
+// angles as in the classical cyclic method (t = sgn(th)/(|th|+sqrt(th^2+1)),
+// th = (a_qq - a_pp)/(2 a_pq)); sweeps until the off-diagonal norm is below
+// 1e-16 of the diagonal norm.  Eigenvalues ascending; evecs row-major with
+// eigenvector j in column j.
+__global__ void __launch_bounds__(128) jacobi_eigh_kernel(const double *A, int n, int lda, double *evals,
+                                                          double *evecs) {
   __shared__ double a[32][33];
   __shared__ double v[32][33];
-  const int lane = threadIdx.x;
-  for (int j = 0; j < n; ++j) {
-    if (lane < n) {
-      a[lane][j] = A[(int64_t)lane * lda + j];
-      v[lane][j] = (lane == j) ? 1.0 : 0.0;
-    }
+  __shared__ double rc[16], rs[16];
+  __shared__ int rp[16], rq[16];
+  __shared__ int done;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int idx = tid; idx < n * n; idx += nt) {
+    const int i = idx / n, j = idx % n;
+    a[i][j] = A[(int64_t)i * lda + j];
+    v[i][j] = (i == j) ? 1.0 : 0.0;
   }
-  __syncwarp();
+  const int N = (n + 1) & ~1;  // an odd n gets a dummy index n (its pairs are skipped)
+  const int npair = N / 2;
+  __syncthreads();
   for (int sweep = 0; sweep < 60; ++sweep) {
-    double off = 0.0, dg = 0.0;
-    if (lane < n) {
-      dg = a[lane][lane] * a[lane][lane];
-      for (int j = lane + 1; j < n; ++j) off += a[lane][j] * a[lane][j];
-    }
-    for (int o = 16; o > 0; o >>= 1) {
-      off += __shfl_xor_sync(0xffffffffu, off, o);
-      dg += __shfl_xor_sync(0xffffffffu, dg, o);
-    }
-    if (off <= 1e-32 * (dg + 1e-300)) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const double apq = a[p][q];
-        if (fabs(apq) < 1e-300) continue;
-        const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
-        const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
-        const double c = 1.0 / sqrt(t * t + 1.0);
-        const double s = t * c;
-        __syncwarp();
-        if (lane < n) {
-          const double akp = a[lane][p], akq = a[lane][q];
-          a[lane][p] = c * akp - s * akq;
-          a[lane][q] = s * akp + c * akq;
-          const double vkp = v[lane][p], vkq = v[lane][q];
-          v[lane][p] = c * vkp - s * vkq;
-          v[lane][q] = s * vkp + c * vkq;
-        }
-        __syncwarp();
-        if (lane < n) {
-          const double apk = a[p][lane], aqk = a[q][lane];
-          a[p][lane] = c * apk - s * aqk;
-          a[q][lane] = s * apk + c * aqk;
-        }
-        __syncwarp();
+    if (tid < 32) {
+      double off = 0.0, dg = 0.0;
+      if (tid < n) {
+        dg = a[tid][tid] * a[tid][tid];
+        for (int j = tid + 1; j < n; ++j) off += a[tid][j] * a[tid][j];
       }
+      for (int o = 16; o > 0; o >>= 1) {
+        off += __shfl_xor_sync(0xffffffffu, off, o);
+        dg += __shfl_xor_sync(0xffffffffu, dg, o);
+      }
+      if (tid == 0) done = off <= 1e-32 * (dg + 1e-300);
+    }
+    __syncthreads();
+    if (done) break;
+    for (int r = 0; r < N - 1; ++r) {
+      if (tid < npair) {
+        const int i0 = tid, i1 = N - 1 - tid;
+        int p = i0 == 0 ? 0 : ((i0 - 1 + r) % (N - 1)) + 1;
+        int q = ((i1 - 1 + r) % (N - 1)) + 1;
+        if (p > q) {
+          const int x = p;
+          p = q;
+          q = x;
+        }
+        double c = 1.0, sn = 0.0;
+        if (q < n) {
+          const double apq = a[p][q];
+          if (fabs(apq) >= 1e-300) {
+            const double th = (a[q][q] - a[p][p]) / (2.0 * apq);
+            const double t = (th >= 0.0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+            c = 1.0 / sqrt(t * t + 1.0);
+            sn = t * c;
+          }
+        } else {
+          p = -1;
+        }
+        rp[tid] = p;
+        rq[tid] = q;
+        rc[tid] = c;
+        rs[tid] = sn;
+      }
+      __syncthreads();
+      for (int it = tid; it < n * npair; it += nt) {  // A <- A J, V <- V J
+        const int k = it % n, m = it / n, p = rp[m], q = rq[m];
+        if (p < 0) continue;
+        const double c = rc[m], sn = rs[m];
+        const double akp = a[k][p], akq = a[k][q];
+        a[k][p] = c * akp - sn * akq;
+        a[k][q] = sn * akp + c * akq;
+        const double vkp = v[k][p], vkq = v[k][q];
+        v[k][p] = c * vkp - sn * vkq;
+        v[k][q] = sn * vkp + c * vkq;
+      }
+      __syncthreads();
+      for (int it = tid; it < n * npair; it += nt) {  // A <- J^T A
+        const int k = it % n, m = it / n, p = rp[m], q = rq[m];
+        if (p < 0) continue;
+        const double c = rc[m], sn = rs[m];
+        const double apk = a[p][k], aqk = a[q][k];
+        a[p][k] = c * apk - sn * aqk;
+        a[q][k] = sn * apk + c * aqk;
+      }
+      __syncthreads();
+    }
   }
-  if (lane == 0) {
+  if (tid == 0) {
     for (int i = 0; i < n; ++i) {
       int m = i;
-      for (int j = i + 1; j < n; ++j) if (a[j][j] < a[m][m]) m = j;
+      for (int j = i + 1; j < n; ++j)
+        if (a[j][j] < a[m][m]) m = j;
       if (m != i) {
-        const double t = a[i][i]; a[i][i] = a[m][m]; a[m][m] = t;
-        for (int r = 0; r < n; ++r) { const double x = v[r][i]; v[r][i] = v[r][m]; v[r][m] = x; }
+        const double t = a[i][i];
+        a[i][i] = a[m][m];
+        a[m][m] = t;
+        for (int r = 0; r < n; ++r) {
+          const double x = v[r][i];
+          v[r][i] = v[r][m];
+          v[r][m] = x;
+        }
       }
     }
   }
-  __syncwarp();
-  if (lane < n) {
-    for (int j = 0; j < n; ++j) evecs[(int64_t)lane * n + j] = v[lane][j];
-    evals[lane] = a[lane][lane];
-  }
+  __syncthreads();
+  for (int idx = tid; idx < n * n; idx += nt) evecs[idx] = v[idx / n][idx % n];
+  if (tid < n) evals[tid] = a[tid][tid];
 }
 
 cudaError_t launch_jacobi_eigh(const double *A, int n, int lda, double *evals, double *evecs,
                                cudaStream_t s) {
   if (n > 32 || n < 1) return cudaErrorInvalidValue;
   COUNT(1);
-  jacobi_eigh_kernel<<<1, 32, 0, s>>>(A, n, lda, evals, evecs);
+  jacobi_eigh_kernel<<<1, 128, 0, s>>>(A, n, lda, evals, evecs);
   return cudaGetLastError();
 }
 

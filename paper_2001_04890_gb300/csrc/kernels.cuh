@@ -31,10 +31,11 @@ cudaError_t launch_chain_fp64(const ChainEntry *e, const ChainGroup *g, int ngro
 cudaError_t launch_chain_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, int ntiles,
                                 uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
 // one warp per output block of at most 32 x 32, lanes over flattened elements
+// warps per CTA: FP64 6 or 4, FP32 12 or 8 (other values: the first)
 cudaError_t launch_chain_flat_fp64(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
-                                   uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+                                   uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s, int warps = 6);
 cudaError_t launch_chain_flat_f32ops(const ChainEntry *e, const ChainGroup *g, int ngroups, uint64_t xb,
-                                     uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s);
+                                     uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s, int warps = 12);
 
 // Split task lists: every output block's entries are cut into chunks whose
 // partial blocks go to a scratch buffer; this adds them in chunk order.
@@ -116,9 +117,10 @@ cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, cu
 // Y^T tiles of FP64 psi blocks
 cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi, uint8_t *arena,
                              cudaStream_t s);
-// tensor-core H.psi chain (split-BF16 x3, FP32 accumulation, FP64 output blocks), one CTA per
-// group (m, q <= 128, every entry n, p <= 128); *status is raised if an mbarrier wait ran out
+// tensor-core H.psi chain (split-BF16 x3, FP32 accumulation, FP64 output blocks), persistent
+// CTAs taking groups (m, q <= 128, every entry n, p <= 128) from *counter (zeroed here on s);
+// *status is raised if an mbarrier wait ran out
 cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
-                             const uint8_t *psitiles, uint64_t db, int *status, cudaStream_t s);
+                             const uint8_t *psitiles, uint64_t db, int *counter, int *status, cudaStream_t s);
 
 }  // namespace dmrg

@@ -165,8 +165,13 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 }
 
 // ---------------------------------------------------------------------------
-// chain_tc2: D += sum_e f_e X_e Y_e Z_e for one output block per CTA on the
-// tensor cores (split-BF16 three-pass products, FP32 accumulation in TMEM).
+// chain_tc2: D += sum_e f_e X_e Y_e Z_e per output block on the tensor cores
+// (split-BF16 three-pass products, FP32 accumulation in TMEM).  Persistent:
+// two CTAs per SM, with TMEM, mbarriers and the zeroed stage ring set up once
+// per CTA; the producer takes the next output block from a global counter
+// (dynamic balance: a block's cost on the tensor cores is not its FLOP count)
+// and hands the indices to the other roles through a small ring (gfull /
+// gempty mbarriers; -1 ends the work).
 //
 // Work of one entry is a sequence of "jobs", one per K chunk:
 //   stage 1 (K = n):  T = X Y           A = X chunk, B = Y^T chunk, both bulk-copied
@@ -175,12 +180,14 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 // Identity X / Z are exact identity tiles.  Jobs run through a ring of T2_NS
 // shared-memory stages (A half | B half, 16 KB each) with warp roles:
 //   warps 0-3  converters: T (TMEM lanes = rows) -> f T split into bf16 hi/lo
-//              in stage 2 jobs; finally D (TMEM) -> FP64 output block
+//              in stage 2 jobs; at the end of a block D (TMEM) -> FP64 output
 //   warp 4     producer: bulk copies of the operand chunks
 //   warp 5     MMA issuer: one thread issues tcgen05.mma and commits
 // mbarriers per stage: full (copies landed), cvf (converters wrote A),
 // empty (MMAs that read the stage finished); per entry: tfull (T complete),
-// tempty (converters finished reading T); dfull (D complete).
+// tempty (converters finished reading T); per output block: dfull (D
+// complete), dempty (converters finished reading D).  Phases run on across
+// entries and blocks; every role derives the same job sequence.
 // Every wait is bounded: on time-out the CTA raises *status, all roles stop,
 // copies and MMAs in flight are waited for, and TMEM is released.
 // ---------------------------------------------------------------------------
@@ -190,10 +197,15 @@ static constexpr int T2_HALF = 16384;
 static constexpr int T2_STAGE = 2 * T2_HALF;
 static constexpr int T2_BAR_OFF = T2_NS * T2_STAGE;
 static constexpr int T2_THREADS = 192;
+static constexpr int T2_CTAS_PER_SM = 2;
+
+static constexpr int T2_GR = 4;  // ring of fetched output-block indices
 
 struct T2Bars {
   uint64_t full[T2_NS], cvf[T2_NS], empty[T2_NS];
-  uint64_t tfull, tempty, dfull, drain;
+  uint64_t tfull, tempty, dfull, dempty, drain;
+  uint64_t gfull[T2_GR], gempty[T2_GR];
+  int gidx[T2_GR];
   uint32_t tslot;
   int abort;
 };
@@ -229,14 +241,13 @@ __device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatil
 __device__ __forceinline__ int ceil16(int x) { return (x + 15) & ~15; }
 
 __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__restrict__ E,
-                                                               const TcGroup *__restrict__ G,
+                                                               const TcGroup *__restrict__ G, int ngroups,
                                                                const uint8_t *__restrict__ optiles,
                                                                const uint8_t *__restrict__ psitiles,
-                                                               uint64_t db, int *status) {
+                                                               uint64_t db, int *counter, int *status) {
   extern __shared__ __align__(1024) uint8_t smem[];
   T2Bars *B = reinterpret_cast<T2Bars *>(smem + T2_BAR_OFF);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const TcGroup g = G[blockIdx.x];
   if (warp == 0) {
     tc::tmem_alloc(&B->tslot, 256);
     tc::tmem_relinquish();
@@ -250,48 +261,70 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
     tc::mbar_init(&B->tfull, 1);
     tc::mbar_init(&B->tempty, 4);
     tc::mbar_init(&B->dfull, 1);
+    tc::mbar_init(&B->dempty, 4);
     tc::mbar_init(&B->drain, 1);
+    for (int r = 0; r < T2_GR; ++r) {
+      tc::mbar_init(&B->gfull[r], 1);
+      tc::mbar_init(&B->gempty[r], 5);  // MMA issuer + 4 converter warps
+    }
     B->abort = 0;
   }
-  // stale rows of an A operand only feed discarded TMEM lanes, but must be finite
-  for (int i = tid; i < T2_BAR_OFF / 16; i += T2_THREADS) reinterpret_cast<uint4 *>(smem)[i] = make_uint4(0, 0, 0, 0);
+  // A halves: rows beyond a block's 16-row padding only feed discarded TMEM lanes,
+  // but must hold finite values (B halves are read only where copied)
+  for (int i = tid; i < T2_NS * (T2_HALF / 16); i += T2_THREADS) {
+    const int s = i / (T2_HALF / 16), o = i % (T2_HALF / 16);
+    reinterpret_cast<uint4 *>(smem + s * T2_STAGE)[o] = make_uint4(0, 0, 0, 0);
+  }
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
   const uint32_t tbase = B->tslot, tT = tbase, tD = tbase + 128;
   volatile int *abort = &B->abort;
-  const int m = g.m, q = g.q, m16 = ceil16(m), q16 = ceil16(q);
-  const int e_end = g.first + g.count;
+  volatile int *gidx = B->gidx;
 
   if (warp == 4) {
     // ---------------- producer
     if (lane == 0) {
       int j = 0;
       bool ok = true;
-      for (int ei = g.first; ei < e_end && ok; ++ei) {
-        const TcEntry e = E[ei];
-        const int n16 = ceil16(e.n), p16 = ceil16(e.p);
-        const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-        for (int c = 0; c < nch1 + nch2 && ok; ++c, ++j) {
-          const int s = j % T2_NS;
-          const uint32_t u = (uint32_t)(j / T2_NS);
-          if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
-            ok = false;
-            break;
-          }
-          uint8_t *st = smem + s * T2_STAGE;
-          if (c < nch1) {
-            const int w = min(T2_W, n16 - c * T2_W);
-            const uint32_t bx = (uint32_t)(m16 * w * 4), by = (uint32_t)(p16 * w * 4);
-            tc::mbar_arrive_expect_tx(&B->full[s], bx + by);
-            tc::bulk_g2s(st, optiles + e.xt + (uint64_t)128 * m16 * c, bx, &B->full[s]);
-            tc::bulk_g2s(st + T2_HALF, psitiles + e.yt + (uint64_t)128 * p16 * c, by, &B->full[s]);
-          } else {
-            const int c2 = c - nch1, w = min(T2_W, p16 - c2 * T2_W);
-            const uint32_t bz = (uint32_t)(q16 * w * 4);
-            tc::mbar_arrive_expect_tx(&B->full[s], bz);
-            tc::bulk_g2s(st + T2_HALF, optiles + e.zt + (uint64_t)128 * q16 * c2, bz, &B->full[s]);
+      for (int gl = 0; ok; ++gl) {
+        // take the next output block and publish it to the other roles
+        const int r = gl % T2_GR;
+        if (!t2_wait1(&B->gempty[r], ((uint32_t)(gl / T2_GR) & 1u) ^ 1u, abort, status)) break;
+        const int gi0 = atomicAdd(counter, 1);
+        const int gi = gi0 < ngroups ? gi0 : -1;
+        gidx[r] = gi;
+        tc::mbar_arrive(&B->gfull[r]);  // release: the index is visible to the waiters
+        if (gi < 0) break;
+        const TcGroup g = G[gi];
+        const int m16 = ceil16(g.m), q16 = ceil16(g.q), e_end = g.first + g.count;
+        TcEntry nx = E[g.first];
+        for (int ei = g.first; ei < e_end && ok; ++ei) {
+          const TcEntry e = nx;
+          if (ei + 1 < e_end) nx = E[ei + 1];  // next entry's load overlaps this one's work
+          const int n16 = ceil16(e.n), p16 = ceil16(e.p);
+          const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+          for (int c = 0; c < nch1 + nch2 && ok; ++c, ++j) {
+            const int s = j % T2_NS;
+            const uint32_t u = (uint32_t)(j / T2_NS);
+            if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+              ok = false;
+              break;
+            }
+            uint8_t *st = smem + s * T2_STAGE;
+            if (c < nch1) {
+              const int w = min(T2_W, n16 - c * T2_W);
+              const uint32_t bx = (uint32_t)(m16 * w * 4), by = (uint32_t)(p16 * w * 4);
+              tc::mbar_arrive_expect_tx(&B->full[s], bx + by);
+              tc::bulk_g2s(st, optiles + e.xt + (uint64_t)128 * m16 * c, bx, &B->full[s]);
+              tc::bulk_g2s(st + T2_HALF, psitiles + e.yt + (uint64_t)128 * p16 * c, by, &B->full[s]);
+            } else {
+              const int c2 = c - nch1, w = min(T2_W, p16 - c2 * T2_W);
+              const uint32_t bz = (uint32_t)(q16 * w * 4);
+              tc::mbar_arrive_expect_tx(&B->full[s], bz);
+              tc::bulk_g2s(st + T2_HALF, optiles + e.zt + (uint64_t)128 * q16 * c2, bz, &B->full[s]);
+            }
           }
         }
       }
@@ -305,70 +338,90 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
   } else if (warp == 5) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      int j = 0, le = 0;
+      int j = 0, le = 0, gl = 0;
       uint32_t cvpar = 0;
-      bool dfirst = true, ok = true;
-      for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
-        const TcEntry e = E[ei];
-        const int n16 = ceil16(e.n), p16 = ceil16(e.p);
-        const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-        if (le > 0) {
-          if (!t2_wait1(&B->tempty, (uint32_t)(le - 1) & 1u, abort, status)) {
-            ok = false;
-            break;
+      bool ok = true;
+      for (; ok; ++gl) {
+        const int r = gl % T2_GR;
+        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status)) break;
+        const int gi = gidx[r];
+        tc::mbar_arrive(&B->gempty[r]);
+        if (gi < 0) break;
+        const TcGroup g = G[gi];
+        const int m16 = ceil16(g.m), q16 = ceil16(g.q), e_end = g.first + g.count;
+        const uint32_t id2 = tc::idesc_bf16(128, q16);
+        bool dfirst = true;
+        TcEntry nx = E[g.first];
+        for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
+          const TcEntry e = nx;
+          if (ei + 1 < e_end) nx = E[ei + 1];
+          const int n16 = ceil16(e.n), p16 = ceil16(e.p);
+          const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+          if (le > 0) {  // T of the previous entry has been read
+            if (!t2_wait1(&B->tempty, (uint32_t)(le - 1) & 1u, abort, status)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
           }
-          tc::fence_after();
+          const uint32_t id1 = tc::idesc_bf16(128, p16);
+          for (int c = 0; c < nch1 && ok; ++c, ++j) {
+            const int s = j % T2_NS;
+            const uint32_t u = (uint32_t)(j / T2_NS);
+            if (!t2_wait1(&B->full[s], u & 1u, abort, status)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+            const int w = min(T2_W, n16 - c * T2_W);
+            const uint32_t sbo = (uint32_t)(w / 8) * 128;
+            const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
+            const uint32_t alo = a + (uint32_t)(m16 * w * 2), blo = b + (uint32_t)(p16 * w * 2);
+            for (int ks = 0; ks < w / 16; ++ks) {
+              const uint32_t o = (uint32_t)ks * 256;
+              tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1,
+                           (c == 0 && ks == 0) ? 0u : 1u);
+              tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id1, 1u);
+              tc::mma_bf16(tT, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1, 1u);
+            }
+            tc::mma_commit(&B->empty[s]);
+          }
+          if (!ok) break;
+          tc::mma_commit(&B->tfull);
+          if (dfirst && gl > 0) {  // D of the previous block has been written out
+            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+          }
+          for (int c = 0; c < nch2 && ok; ++c, ++j) {
+            const int s = j % T2_NS;
+            const uint32_t u = (uint32_t)(j / T2_NS);
+            if (!t2_wait1(&B->full[s], u & 1u, abort, status) ||
+                !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status)) {
+              ok = false;
+              break;
+            }
+            cvpar ^= 1u << s;
+            tc::fence_after();
+            const int w = min(T2_W, p16 - c * T2_W);
+            const uint32_t sbo = (uint32_t)(w / 8) * 128;
+            const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
+            const uint32_t alo = a + 8192, blo = b + (uint32_t)(q16 * w * 2);
+            for (int ks = 0; ks < w / 16; ++ks) {
+              const uint32_t o = (uint32_t)ks * 256;
+              tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
+                           dfirst ? 0u : 1u);
+              dfirst = false;
+              tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
+              tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+            }
+            tc::mma_commit(&B->empty[s]);
+          }
         }
-        const uint32_t id1 = tc::idesc_bf16(128, p16), id2 = tc::idesc_bf16(128, q16);
-        for (int c = 0; c < nch1 && ok; ++c, ++j) {
-          const int s = j % T2_NS;
-          const uint32_t u = (uint32_t)(j / T2_NS);
-          if (!t2_wait1(&B->full[s], u & 1u, abort, status)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after();
-          const int w = min(T2_W, n16 - c * T2_W);
-          const uint32_t sbo = (uint32_t)(w / 8) * 128;
-          const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
-          const uint32_t alo = a + (uint32_t)(m16 * w * 2), blo = b + (uint32_t)(p16 * w * 2);
-          for (int ks = 0; ks < w / 16; ++ks) {
-            const uint32_t o = (uint32_t)ks * 256;
-            tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1,
-                         (c == 0 && ks == 0) ? 0u : 1u);
-            tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id1, 1u);
-            tc::mma_bf16(tT, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1, 1u);
-          }
-          tc::mma_commit(&B->empty[s]);
-        }
-        if (!ok) break;
-        tc::mma_commit(&B->tfull);
-        for (int c = 0; c < nch2 && ok; ++c, ++j) {
-          const int s = j % T2_NS;
-          const uint32_t u = (uint32_t)(j / T2_NS);
-          if (!t2_wait1(&B->full[s], u & 1u, abort, status) ||
-              !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status)) {
-            ok = false;
-            break;
-          }
-          cvpar ^= 1u << s;
-          tc::fence_after();
-          const int w = min(T2_W, p16 - c * T2_W);
-          const uint32_t sbo = (uint32_t)(w / 8) * 128;
-          const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
-          const uint32_t alo = a + 8192, blo = b + (uint32_t)(q16 * w * 2);
-          for (int ks = 0; ks < w / 16; ++ks) {
-            const uint32_t o = (uint32_t)ks * 256;
-            tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
-                         dfirst ? 0u : 1u);
-            dfirst = false;
-            tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
-            tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
-          }
-          tc::mma_commit(&B->empty[s]);
-        }
+        if (ok) tc::mma_commit(&B->dfull);
       }
-      if (ok) tc::mma_commit(&B->dfull);
       tc::mma_commit(&B->drain);  // every MMA issued above has finished before TMEM is released
       tc::mbar_wait(&B->drain, 0, kMaxWaitTries);
     }
@@ -376,54 +429,70 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
     // ---------------- converters (thread = row = TMEM lane)
     const int row = tid;
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    int j = 0, le = 0;
+    int j = 0, le = 0, gl = 0;
     bool ok = true;
-    for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
-      const TcEntry e = E[ei];
-      const int n16 = ceil16(e.n), p16 = ceil16(e.p);
-      const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-      const float f = e.f;
-      j += nch1;
-      if (!t2_waitw(&B->tfull, (uint32_t)le & 1u, abort, status)) {
-        ok = false;
-        break;
-      }
-      tc::fence_after();
-      for (int c = 0; c < nch2; ++c, ++j) {
-        const int s = j % T2_NS;
-        const uint32_t u = (uint32_t)(j / T2_NS);
-        if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+    for (; ok; ++gl) {
+      const int r = gl % T2_GR;
+      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status)) break;
+      const int gi = gidx[r];
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&B->gempty[r]);
+      if (gi < 0) break;
+      const TcGroup g = G[gi];
+      const int m = g.m, q = g.q, q16 = ceil16(q), e_end = g.first + g.count;
+      TcEntry nx = E[g.first];
+      for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
+        const TcEntry e = nx;
+        if (ei + 1 < e_end) nx = E[ei + 1];
+        const int n16 = ceil16(e.n), p16 = ceil16(e.p);
+        const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+        const float f = e.f;
+        j += nch1;
+        if (!t2_waitw(&B->tfull, (uint32_t)le & 1u, abort, status)) {
           ok = false;
           break;
         }
         tc::fence_after();
-        const int w = min(T2_W, p16 - c * T2_W);
-        uint8_t *A = smem + s * T2_STAGE;
-        for (int h = 0; h < w / 16; ++h) {
-          float v[16];
-          tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
-          if (row < m) {
+        for (int c = 0; c < nch2; ++c, ++j) {
+          const int s = j % T2_NS;
+          const uint32_t u = (uint32_t)(j / T2_NS);
+          if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const int w = min(T2_W, p16 - c * T2_W);
+          uint8_t *A = smem + s * T2_STAGE;
+          for (int h = 0; h < w / 16; ++h) {
+            float v[16];
+            tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
+            if (row < m) {
 #pragma unroll
-            for (int g2 = 0; g2 < 2; ++g2) {
-              __align__(16) __nv_bfloat16 hb[8], lb[8];
+              for (int g2 = 0; g2 < 2; ++g2) {
+                __align__(16) __nv_bfloat16 hb[8], lb[8];
 #pragma unroll
-              for (int i = 0; i < 8; ++i) tc::split_bf16(f * v[8 * g2 + i], hb[i], lb[i]);
-              uint8_t *dst = A + ((row >> 3) * (w >> 3) + 2 * h + g2) * 128 + (row & 7) * 16;
-              *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
-              *reinterpret_cast<uint4 *>(dst + 8192) = *reinterpret_cast<const uint4 *>(lb);
+                for (int i = 0; i < 8; ++i) tc::split_bf16(f * v[8 * g2 + i], hb[i], lb[i]);
+                uint8_t *dst = A + ((row >> 3) * (w >> 3) + 2 * h + g2) * 128 + (row & 7) * 16;
+                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
+                *reinterpret_cast<uint4 *>(dst + 8192) = *reinterpret_cast<const uint4 *>(lb);
+              }
             }
           }
+          tc::fence_async_smem();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
         }
-        tc::fence_async_smem();
+        if (!ok) break;
+        tc::fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
+        if (lane == 0) tc::mbar_arrive(&B->tempty);
       }
       if (!ok) break;
-      tc::fence_before();
-      __syncwarp();
-      if (lane == 0) tc::mbar_arrive(&B->tempty);
-    }
-    if (ok && t2_waitw(&B->dfull, 0, abort, status)) {
+      // ---- output block: D (TMEM) -> FP64 global, then release D
+      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status)) {
+        ok = false;
+        break;
+      }
       tc::fence_after();
       double *D = reinterpret_cast<double *>(db + g.d * 8ull);
       for (int c0 = 0; c0 < q16; c0 += 16) {
@@ -435,6 +504,9 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
             if (c0 + i < q) D[(int64_t)row * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
         }
       }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&B->dempty);
     }
   }
   __syncwarp();  // lanes 1-31 of the producer and MMA warps rejoin lane 0
@@ -444,14 +516,23 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
 }
 
 cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
-                             const uint8_t *psitiles, uint64_t db, int *status, cudaStream_t s) {
+                             const uint8_t *psitiles, uint64_t db, int *counter, int *status, cudaStream_t s) {
   if (ngroups <= 0) return cudaSuccess;
+  cudaError_t err0 = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (err0 != cudaSuccess) return err0;
   static_assert(T2_SMEM <= T2_SMEM_LAUNCH, "shared memory budget");
   cudaError_t err = cudaFuncSetAttribute(chain_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          T2_SMEM_LAUNCH);
   if (err != cudaSuccess) return err;
+  int dev = 0, sms = 0;
+  err = cudaGetDevice(&dev);
+  if (err != cudaSuccess) return err;
+  err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (err != cudaSuccess) return err;
+  const int grid = std::min(ngroups, T2_CTAS_PER_SM * std::max(sms, 1));
   add_kernel_launches(1);
-  chain_tc2_kernel<<<ngroups, T2_THREADS, T2_SMEM_LAUNCH, s>>>(e, g, optiles, psitiles, db, status);
+  chain_tc2_kernel<<<grid, T2_THREADS, T2_SMEM_LAUNCH, s>>>(e, g, ngroups, optiles, psitiles, db, counter,
+                                                             status);
   return cudaGetLastError();
 }
 

@@ -31,14 +31,15 @@ def test_autotune_keeps_hpsi(prec, tol):
     assert ms > 0
     assert par["target_chunks"] in (2048.0, 8192.0, 32768.0)
     assert par["min_chunk"] in (5.0e4, 2.0e5)
-    assert par["tc_min"] in ((17, 33, 49, 65) if prec == binding.PREC_BF16X3 else (33,))
+    assert par["tc_min"] in ((1, 9, 17, 33, 49, 65) if prec == binding.PREC_BF16X3 else (33,))
+    assert par["by_work"] in (0, 1) and par["flat_wide"] in (0, 1)
     assert ctx.get_tune() == par
     after = ctx.hpsi(psi)
     scale = np.max(np.abs(ref))
     assert np.max(np.abs(after - ref)) <= tol * scale
     assert np.max(np.abs(before - ref)) <= tol * scale
     # an explicit shape: everything on the tensor cores that fits (BF16X3), fine chunks
-    ctx.set_tune(target_chunks=32768, min_chunk=5e4, tc_min=1, by_work=1)
+    ctx.set_tune(target_chunks=32768, min_chunk=5e4, tc_min=1, by_work=1, flat_wide=0)
     again = ctx.hpsi(psi)
     assert np.max(np.abs(again - ref)) <= tol * scale
     ctx.close()
@@ -59,7 +60,7 @@ def test_batch_autotune_keeps_hpsi():
     x = np.concatenate(psis)
     y0 = batch.hpsi(x)
     ms, par = batch.autotune(reps=1)
-    assert ms > 0 and par["tc_min"] in (17, 33, 49, 65)
+    assert ms > 0 and par["tc_min"] in (1, 9, 17, 33, 49, 65)
     for _ in range(2):  # direct run after tuning, then a graph replay
         y = batch.hpsi(x)
         for i, r in enumerate(refs):
