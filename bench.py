@@ -109,7 +109,7 @@ def _flops_fn(wl):
     return f
 
 
-def _setup(wl, precision, stream, dev):
+def _setup(wl, precision, stream, dev, release=False):
     import torch
     from paper_2001_04890_gb300 import binding, workloads
     L, N, two_sz, M = wl["L"], wl["N"], wl["two_sz"], wl["M"]
@@ -117,7 +117,7 @@ def _setup(wl, precision, stream, dev):
     k = (L - 2) // 2
     h, v = workloads.integrals(L, seed=0)
     ctx = binding.DMRG(h, v, N, two_sz, M, precision, stream=stream.cuda_stream)
-    workloads.grow_middle_bond(ctx, L, nu, nd, M, k, seed=0)
+    workloads.grow_middle_bond(ctx, L, nu, nd, M, k, seed=0, release=release)
     return ctx, k
 
 
@@ -439,53 +439,65 @@ def mixed_step_workload(args, wl, tol):
 
 
 def large_workload(wl, iters=4):
-    """Middle bond of a large workload: one context per precision on the same bases.
+    """Middle bond of a large workload, grown once; each working precision in turn.
 
     Reports the block-growth time, H.psi time and TFLOP/s per precision, a few
-    Davidson iterations (s/iter) and one renormalization, plus the relative
-    difference of each low-precision sigma from the FP64 sigma.
+    Davidson iterations (s/iter) and one renormalization (on a copy of the
+    state: the renormalization itself is FP64 in every mode), plus the
+    relative difference of each low-precision sigma from the FP64 sigma.
     """
     import torch
-    from paper_2001_04890_gb300 import binding, workloads
+    from paper_2001_04890_gb300 import workloads
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
     out = {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"], "M": wl["M"]}
+    t0 = time.perf_counter()
+    ctx, k = _setup(wl, 0, stream, 0, release=True)  # only the middle-bond blocks stay resident
+    out["setup_s"] = time.perf_counter() - t0
+    _, dim = ctx.psi_layout()
+    out["psi_dim"] = dim
+    psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
     sig64 = None
     for name, prec in (("fp64", 0), ("fp32", 1), ("bf16x3", 2)):
-        t0 = time.perf_counter()
-        ctx, k = _setup(wl, prec, stream, 0)
-        setup_s = time.perf_counter() - t0
-        _, dim = ctx.psi_layout()
-        psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
+        ctx.set_precision(prec)
         t0 = time.perf_counter()
         sig = ctx.hpsi(psi)  # builds task list + temporaries
         torch.cuda.synchronize()
         plan_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        if prec == 0:  # FP64 H.psi takes seconds here: the shape tuned at L=24/M=512, not re-timed
+            ctx.set_tune(target_chunks=32768, min_chunk=5e4, tc_min=33, by_work=0, flat_wide=0)
+            ctx.hpsi(psi)
+            tune = ctx.get_tune()
+        else:
+            tune_ms, tune = ctx.autotune(reps=1)
+        tune_s = time.perf_counter() - t0
         ctx.stats(reset=True)
         for _ in range(3):
             sig = ctx.hpsi(psi)
         st = ctx.stats(reset=True)
         fl, tasks = ctx.hpsi_flops()
         ms = st["hpsi_ms"] / max(st["hpsi_calls"], 1)
-        r = {"setup_s": setup_s, "plan_s": plan_s, "hpsi_ms": ms, "hpsi_tflops": fl / (ms * 1e-3) / 1e12,
-             "gflop_per_hpsi": fl / 1e9, "tasks": tasks, "psi_dim": dim}
+        r = {"plan_s": plan_s, "autotune_s": tune_s, "launch_shape": tune, "hpsi_ms": ms,
+             "hpsi_tflops": fl / (ms * 1e-3) / 1e12, "gflop_per_hpsi": fl / 1e9, "tasks": tasks}
         s = sig.double().cpu().numpy()
         if sig64 is None:
             sig64 = s
         else:
             r["rel_diff_vs_fp64"] = float(np.max(np.abs(s - sig64)) / np.max(np.abs(sig64)))
-        t0 = time.perf_counter()
+        ctx.set_position(k, 1)
         ctx.set_psi(psi)
+        t0 = time.perf_counter()
         e, it = ctx.davidson(tol=1e-14, max_iter=iters, allow_noconv=True)
         torch.cuda.synchronize()
         r["davidson_s_per_iter"] = (time.perf_counter() - t0) / max(it, 1)
-        t0 = time.perf_counter()
-        dw, kept = ctx.renormalize(+1)
-        torch.cuda.synchronize()
-        r["renormalize_s"] = time.perf_counter() - t0
         out[name] = r
         print(json.dumps({name: r}), flush=True)
-        ctx.close()
+    t0 = time.perf_counter()
+    ctx.renormalize(+1)
+    torch.cuda.synchronize()
+    out["renormalize_s_fp64"] = time.perf_counter() - t0
+    ctx.close()
     return out
 
 

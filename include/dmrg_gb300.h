@@ -200,6 +200,26 @@ int dmrg_renormalize(dmrg_ctx *ctx, int direction, const int *kept, const double
 int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
 
 /*
+ * dmrg_set_precision -- change the working precision of the Davidson matvecs
+ * (DMRG_PREC_*) of an existing context; blocks and the wave function are kept,
+ * the H.psi task lists and low-precision operator copies are rebuilt on next
+ * use.  DMRG_EINVAL for an unknown precision.  Synchronizes the stream.
+ */
+int dmrg_set_precision(dmrg_ctx *ctx, int precision);
+
+/*
+ * dmrg_release_block -- free the stored block of `sites` sites on side 0 (left)
+ * or 1 (right) to bound device memory when only part of a sweep is needed (the
+ * paper keeps every block for later sweeps; this is a memory option).  A later
+ * position that needs a released block fails with DMRG_ESTATE until it is
+ * rebuilt by renormalization; wave-function prediction across a released block
+ * is skipped.  DMRG_EINVAL for a block the current position uses, a side other
+ * than 0/1 or sites outside 1..L-2; releasing an absent block is a no-op.
+ * Synchronizes the context stream.
+ */
+int dmrg_release_block(dmrg_ctx *ctx, int side, int sites);
+
+/*
  * dmrg_block_op -- introspection of one stored operator of the left (side 0)
  * or right (side 1) block at the current position, in its family layout:
  * for each ket sector a with a bra sector a' in order, the m_a' x m_a block.
@@ -292,6 +312,16 @@ int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, const double
  * bounded completion wait ran out.
  */
 int dmrg_selftest_tcgen05(int N, int K, const float *A, const float *B, float *C);
+
+/*
+ * dmrg_debug_tasks -- host-only dump of the H.psi task list the planner builds
+ * for the same arguments as dmrg_plan_hpsi_flops: per task 7 ints (output psi
+ * block index, m, n, p, q, identity flags (1: left identity, 2: right
+ * identity), element offset of the input psi block).  out may be NULL to query
+ * *ntasks; DMRG_EINVAL if cap < *ntasks.  No GPU is used.
+ */
+int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                     const int *sec_l, int nr, const int *sec_r, int *out, long long cap, long long *ntasks);
 
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */

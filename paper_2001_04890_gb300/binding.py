@@ -57,6 +57,8 @@ def lib():
         "dmrg_renormalize": (C.c_int, [vp, C.c_int, ip, dp, dp]),
         "dmrg_sweep": (C.c_int, [vp, C.c_int, C.c_double, dp]),
         "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
+        "dmrg_release_block": (C.c_int, [vp, C.c_int, C.c_int]),
+        "dmrg_set_precision": (C.c_int, [vp, C.c_int]),
         "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp, llp, dp]),
         "dmrg_plan_hpsi_flops": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip,
                                            C.c_int, ip, dp, llp]),
@@ -72,6 +74,8 @@ def lib():
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
+        "dmrg_debug_tasks": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
+                                       ip, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
     }
@@ -109,6 +113,20 @@ def _dump(fn, *args):
     buf = C.create_string_buffer(need.value)
     _check(fn(*args, buf, need.value, C.byref(need)))
     return buf.value.decode()
+
+
+def debug_tasks(h, v, N, two_sz, k, sec_l, sec_r):
+    """Host-only H.psi task list: (ntasks, 7) int array (group, m, n, p, q, identity flags, input offset)."""
+    h, v = _f64(h), _f64(v)
+    L = h.shape[0]
+    tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
+    tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
+    n = C.c_longlong()
+    args = (L, N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr), _iptr(tr))
+    _check(lib().dmrg_debug_tasks(*args, None, 0, C.byref(n)))
+    out = np.zeros((n.value, 7), dtype=np.int32)
+    _check(lib().dmrg_debug_tasks(*args, _iptr(out), n.value, C.byref(n)))
+    return out
 
 
 def plan_hpsi_flops(h, v, N, two_sz, k, sec_l, sec_r):
@@ -291,6 +309,14 @@ class DMRG:
         par = np.zeros(5)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
+
+    def set_precision(self, precision):
+        """Switch the working precision of the Davidson matvecs (PREC_FP64 / PREC_FP32 / PREC_BF16X3)."""
+        _check(lib().dmrg_set_precision(self.ctx, int(precision)))
+
+    def release_block(self, side, sites):
+        """Free the stored block of `sites` sites on side 0 (left) / 1 (right)."""
+        _check(lib().dmrg_release_block(self.ctx, side, sites))
 
     def block_op(self, side, kind, i=-1, j=-1):
         n = C.c_longlong()

@@ -278,6 +278,7 @@ struct ChainTune {
   double min_chunk = 2.0e5;
   int tc_min = 33;
   int by_work = 0;     // 1: launch groups heaviest first; 0: in output-block order (operand locality)
+  int orient = 1;      // run each entry in its cheaper association (split task lists)
   int flat_wide = 1;   // flat kernel CTAs: 1 = one wide CTA per SM (6 FP64 / 12 FP32 warps),
                        // 0 = two narrower CTAs per SM (4 / 8 warps each)
 };
@@ -291,7 +292,7 @@ struct ChainTune {
 // does not depend on scheduling (bitwise repeatable) while the grid has
 // thousands of independent tasks.
 struct DevChain {
-  DBuf<ChainEntry> ent;
+  DBuf<ChainEntry> ent, xent;
   DBuf<ChainGroup> all, big, flat;
   DBuf<ReduceGroup> red;
   DBuf<double> scratch;
@@ -317,26 +318,33 @@ struct DevChain {
     flat_wide = tune.flat_wide;
     int tiles = 0;
     int64_t soff = 0, e0 = 0;
-    // per-entry work for chunking
+    // Execution list: with split chunks, the entries of an output block whose
+    // other association is cheaper (n p q + m n q < m n p + m p q) run as the
+    // transposed product D^T += f Z^T Y^T X^T (same operands, swapped strides)
+    // in chunks of their own; their slot is written through transposed strides,
+    // so the ordered reduction is unchanged.
+    std::vector<ChainEntry> xs;
+    std::vector<double> w;
+    xs.reserve(CL.flat.size());
+    w.reserve(CL.flat.size());
+    auto tc_entry_ok = [&](const ChainEntry &e, int m, int q) {
+      // Y must be a whole row-major psi block; identity sides are square
+      return !(e.n < 1 || e.p < 1 || e.n > 128 || e.p > 128 || e.y == ~0ull || e.ycs != 1 || e.yrs != e.p ||
+               (e.x == ~0ull && e.n != m) || (e.z == ~0ull && e.p != q));
+    };
+    auto tc_shape_ok = [&](int m, int q) {
+      return tensor_cores && m <= 128 && q <= 128 && (m >= tune.tc_min || q >= tune.tc_min);
+    };
     double total = 0.0;
-    std::vector<double> w(CL.flat.size());
     for (const auto &g : CL.grp)
       for (int i = g.first; i < g.first + g.count; ++i) {
         const ChainEntry &e = CL.flat[i];
-        w[i] = 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
-        total += w[i];
+        total += 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
       }
     const double chunk_work = std::max(total / tune.target_chunks, tune.min_chunk);
     auto place = [&](ChainGroup t) {
-      bool tc_ok = tensor_cores && t.count > 0 && t.m <= 128 && t.q <= 128 &&
-                   (t.m >= tune.tc_min || t.q >= tune.tc_min);
-      for (int i = t.first; tc_ok && i < t.first + t.count; ++i) {
-        const ChainEntry &e = CL.flat[i];
-        // Y must be a whole row-major psi block; identity sides are square
-        if (e.n < 1 || e.p < 1 || e.n > 128 || e.p > 128 || e.y == ~0ull || e.ycs != 1 || e.yrs != e.p ||
-            (e.x == ~0ull && e.n != t.m) || (e.z == ~0ull && e.p != t.q))
-          tc_ok = false;
-      }
+      bool tc_ok = t.count > 0 && tc_shape_ok(t.m, t.q);
+      for (int i = t.first; tc_ok && i < t.first + t.count; ++i) tc_ok = tc_entry_ok(xs[i], t.m, t.q);
       if (tc_ok) {
         vt.push_back(t);
       } else if (t.m <= 32 && t.q <= 32) {
@@ -349,9 +357,53 @@ struct DevChain {
     };
     for (const auto &g : CL.grp) {
       if (!split) {
-        place(g);
+        ChainGroup t = g;
+        t.first = (int)xs.size();
+        for (int i = g.first; i < g.first + g.count; ++i) {
+          const ChainEntry &e = CL.flat[i];
+          xs.push_back(e);
+          w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull));
+        }
+        place(t);
         continue;
       }
+      // orientation of each entry (tensor-core blocks keep the stored one)
+      bool tc_group = tc_shape_ok(g.m, g.q);
+      for (int i = g.first; tc_group && i < g.first + g.count; ++i) tc_group = tc_entry_ok(CL.flat[i], g.m, g.q);
+      const int n0 = (int)xs.size();
+      std::vector<int> tr;
+      for (int i = g.first; i < g.first + g.count; ++i) {
+        const ChainEntry &e = CL.flat[i];
+        const bool xid = e.x == ~0ull, zid = e.z == ~0ull;
+        const double cn = (double)g.m * e.n * e.p + (double)g.m * e.p * g.q;
+        const double ct = (double)e.n * e.p * g.q + (double)g.m * e.n * g.q;
+        if (tune.orient && !tc_group && !xid && !zid && ct < cn) {
+          tr.push_back(i);
+          continue;
+        }
+        xs.push_back(e);
+        w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, xid, zid));
+      }
+      const int n1 = (int)xs.size();
+      for (int i : tr) {
+        const ChainEntry &e = CL.flat[i];
+        ChainEntry t{};
+        t.x = e.z;  // X' = Z^T
+        t.xrs = e.zcs;
+        t.xcs = e.zrs;
+        t.y = e.y;  // Y' = Y^T
+        t.yrs = e.ycs;
+        t.ycs = e.yrs;
+        t.z = e.x;  // Z' = X^T
+        t.zrs = e.xcs;
+        t.zcs = e.xrs;
+        t.n = e.p;
+        t.p = e.n;
+        t.f = e.f;
+        xs.push_back(t);
+        w.push_back(1.0 + entry_flops(g.q, t.n, t.p, g.m, false, false));
+      }
+      const int n2 = (int)xs.size();
       const int64_t mq = (int64_t)g.m * g.q;
       ReduceGroup r{};
       r.e0 = e0;
@@ -362,20 +414,30 @@ struct DevChain {
       r.m = g.m;
       r.q = g.q;
       int nsplit = 0;
-      int i = g.first;
-      while (i < g.first + g.count) {
-        double acc = 0.0;
-        int j = i;
-        while (j < g.first + g.count && (j == i || acc + w[j] <= chunk_work)) acc += w[j++];
-        ChainGroup t = g;
-        t.first = i;
-        t.count = j - i;
-        t.d = (uint64_t)(soff + (int64_t)nsplit * mq);
-        t.drs = g.q;
-        t.dcs = 1;
-        place(t);
-        ++nsplit;
-        i = j;
+      for (int part = 0; part < 2; ++part) {
+        const int lo = part == 0 ? n0 : n1, hi = part == 0 ? n1 : n2;
+        int i = lo;
+        while (i < hi) {
+          double acc = 0.0;
+          int j = i;
+          while (j < hi && (j == i || acc + w[j] <= chunk_work)) acc += w[j++];
+          ChainGroup t = g;
+          t.first = i;
+          t.count = j - i;
+          t.d = (uint64_t)(soff + (int64_t)nsplit * mq);  // slot: m x q row-major
+          if (part == 0) {
+            t.drs = g.q;
+            t.dcs = 1;
+          } else {  // transposed chunk: q x m output written into the m x q slot
+            t.m = g.q;
+            t.q = g.m;
+            t.drs = 1;
+            t.dcs = g.q;
+          }
+          place(t);
+          ++nsplit;
+          i = j;
+        }
       }
       r.nsplit = nsplit;
       vr.push_back(r);
@@ -402,12 +464,13 @@ struct DevChain {
       by_work(vf);
       by_work(vt);
     }
-    ent.upload(CL.flat, s);
+    ent.upload(CL.flat, s);  // the task list as built (diagonal, batching)
+    xent.upload(xs, s);      // the execution list of the chunk kernels
     nent = (int64_t)CL.flat.size();
     all.upload(CL.grp, s);
     big.upload(vb, s);
     flat.upload(vf, s);
-    build_tc(CL, vt, s);
+    build_tc(xs, vt, s);
     red.upload(vr, s);
     nall = (int)CL.grp.size();
     nbig = (int)vb.size();
@@ -422,7 +485,7 @@ struct DevChain {
   // Tensor-core entries: tile images of every X, Z^T operator view (deduplicated,
   // exact identity tiles for identity sides) and of every psi block read as Y^T.
   // Operator addresses are absolute (the task list is launched with x/z bases 0).
-  void build_tc(const ChainList &CL, const std::vector<ChainGroup> &vt, cudaStream_t s) {
+  void build_tc(const std::vector<ChainEntry> &xs, const std::vector<ChainGroup> &vt, cudaStream_t s) {
     std::vector<TcEntry> te;
     std::vector<TcGroup> tg;
     std::vector<TileSpec> ts;
@@ -444,7 +507,7 @@ struct DevChain {
     for (const auto &g : vt) {
       tg.push_back(TcGroup{g.d, g.drs, g.dcs, g.m, g.q, (int)te.size(), g.count});
       for (int i = g.first; i < g.first + g.count; ++i) {
-        const ChainEntry &e = CL.flat[i];
+        const ChainEntry &e = xs[i];
         TcEntry t{};
         t.n = e.n;
         t.p = e.p;
@@ -488,12 +551,12 @@ struct DevChain {
     const uint64_t tb = split ? (uint64_t)(uintptr_t)scratch.p : db;
     if (split && scratch_n > 0) CK(cudaMemsetAsync(scratch.p, 0, scratch_n * sizeof(double), s));
     if (f32ops) {
-      CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
+      CK(launch_chain_f32ops(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_f32ops(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
       launch_tc(yb, tb, status, s);
     } else {
-      CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
+      CK(launch_chain_fp64(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_fp64(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
     }
     if (split) CK(launch_reduce_partials(red.p, nred, red_total, scratch.p, (double *)(uintptr_t)db, s));
   }
@@ -505,12 +568,12 @@ struct DevChain {
     const uint64_t tb = (uint64_t)(uintptr_t)ext;
     if (scratch_n > 0) CK(cudaMemsetAsync(ext, 0, scratch_n * sizeof(double), s));
     if (f32ops) {
-      CK(launch_chain_f32ops(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_f32ops(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
+      CK(launch_chain_f32ops(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_f32ops(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
       launch_tc(yb, tb, status, s);
     } else {
-      CK(launch_chain_fp64(ent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_fp64(ent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
+      CK(launch_chain_fp64(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
+      CK(launch_chain_flat_fp64(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
     }
     CK(launch_reduce_partials(red.p, nred, red_total, ext, (double *)(uintptr_t)db, s));
   }
@@ -828,12 +891,15 @@ static void build_hplan(dmrg_ctx *c) {
 
 // Report a bounded device-side wait that ran out (the kernel skipped its work).
 static void check_status(dmrg_ctx *c) {
-  int st = 0;
-  CK(cudaMemcpyAsync(&st, c->dstatus.p, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  int st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  CK(cudaMemcpyAsync(st, c->dstatus.p, sizeof(st), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
-  if (st) {
-    CK(cudaMemsetAsync(c->dstatus.p, 0, sizeof(int), c->stream));
-    throw Fail{DMRG_ETIMEOUT, "a tensor-core completion wait ran out; results of that call are invalid"};
+  if (st[0]) {
+    CK(cudaMemsetAsync(c->dstatus.p, 0, sizeof(st), c->stream));
+    std::string where;
+    for (int i = 1; i < 8; ++i) where += (i > 1 ? "," : "") + std::to_string(st[i]);
+    throw Fail{DMRG_ETIMEOUT, "a tensor-core completion wait ran out; results of that call are invalid "
+                              "(site,parity,block,aux0,aux1,bar_lo,bar_hi = " + where + ")"};
   }
 }
 
@@ -1188,7 +1254,11 @@ static void predict_psi(dmrg_ctx *c, const Psi &old, const DBuf<double> &oldpsi,
   c->psi_valid = false;
   DevBlock *lb = lblock(c), *rb = rblock(c);  // position already moved
   if (!lb || !rb) return;
-  const DevBlock &other = direction > 0 ? *c->right[c->L - c->k - 1] : *c->left[c->k + 1];
+  const int on = direction > 0 ? c->L - c->k - 1 : c->k + 1;
+  const auto &store = direction > 0 ? c->right : c->left;
+  const DevBlock *otherp = on < (int)store.size() ? store[on].get() : nullptr;
+  if (!otherp) return;  // released by dmrg_release_block: no prediction
+  const DevBlock &other = *otherp;
   // "other" is the block whose parent enlarged layout splits into the new site + new block
   if (other.parent.empty()) return;
   Psi Y = psi_layout(lb->lay, rb->lay, c->nu, c->nd);
@@ -1649,7 +1719,12 @@ static void davidson(dmrg_ctx *c, double tol, int max_iter, double *energy, int 
   }
   int it1 = 0, it2 = 0, it2l = 0, it3 = 0;
   double e = 0.0;
-  davidson_core(c, tol, 1e-8, max_iter, false, &e, &it1, conv);
+  // the low-precision phase hands over well above its attainable residual
+  // (~1e-7 |E| for FP32, ~1e-5 |E| for split-BF16): the refinement below
+  // converges from there with a few FP64 matvecs, while iterating into the
+  // floor only burns low-precision matvecs
+  const double handover = c->prec == DMRG_PREC_BF16X3 ? 1e-4 : 1e-6;
+  davidson_core(c, tol, handover, max_iter, false, &e, &it1, conv);
   c->dav_iters_lowp += it1;
   const bool ok = davidson_refine(c, tol, std::max(1, max_iter - it1), &e, &it2, &it2l, conv);
   c->dav_iters_lowp += it2l;
@@ -1713,8 +1788,8 @@ extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double
   c->I.L = L;
   c->I.h.assign(h, h + L2);
   c->I.v.assign(v, v + L4);
-  c->dstatus.alloc(1);
-  CK(cudaMemsetAsync(c->dstatus.p, 0, sizeof(int), c->stream));
+  c->dstatus.alloc(8);  // flag + time-out record of the tensor-core kernel
+  CK(cudaMemsetAsync(c->dstatus.p, 0, 8 * sizeof(int), c->stream));
   c->left.resize(L);
   c->right.resize(L);
   c->left[0] = empty_block(0, L);
@@ -1757,6 +1832,33 @@ extern "C" int dmrg_free(dmrg_ctx *c) {
   for (auto e : c->ev) cudaEventDestroy(e);
   delete c;
   return DMRG_OK;
+}
+
+extern "C" int dmrg_set_precision(dmrg_ctx *c, int precision) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "context is NULL"};
+  if (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_FP32 && precision != DMRG_PREC_BF16X3)
+    throw Fail{DMRG_EINVAL, "unknown precision"};
+  if (precision != c->prec) {
+    CK(cudaStreamSynchronize(c->stream));
+    c->prec = precision;
+    c->plan.valid = false;  // task lists and low-precision copies are rebuilt on next use
+  }
+  API_END
+}
+
+extern "C" int dmrg_release_block(dmrg_ctx *c, int side, int sites) {
+  API_BEGIN
+  if (!c || (side != 0 && side != 1) || sites < 1 || sites > c->L - 2)
+    throw Fail{DMRG_EINVAL, "dmrg_release_block: side 0 or 1, 1 <= sites <= L-2"};
+  const int used = side == 0 ? c->k : c->L - c->k - 2;
+  if (sites == used) throw Fail{DMRG_EINVAL, "dmrg_release_block: the block is used at the current position"};
+  auto &store = side == 0 ? c->left : c->right;
+  if (sites < (int)store.size() && store[sites]) {
+    CK(cudaStreamSynchronize(c->stream));  // no launch in flight still reads it
+    store[sites].reset();
+  }
+  API_END
 }
 
 extern "C" int dmrg_set_position(dmrg_ctx *c, int k, int direction) {
@@ -2014,6 +2116,56 @@ extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, c
   expand_hpsi(rps, A, Y, lb, CL, f);
   if (flops) *flops = f;
   if (tasks) *tasks = (long long)CL.ent.size();
+  API_END
+}
+
+extern "C" int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                                const int *sec_l, int nr, const int *sec_r, int *out, long long cap,
+                                long long *ntasks) {
+  API_BEGIN
+  if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r || !ntasks)
+    throw Fail{DMRG_EINVAL, "dmrg_debug_tasks: bad arguments"};
+  if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
+  Integrals I;
+  I.L = L;
+  I.h.assign(h, h + (size_t)L * L);
+  I.v.assign(v, v + (size_t)L * L * L * L);
+  auto sectors = [](int n, const int *t) {
+    std::vector<Sector> o;
+    for (int i = 0; i < n; ++i) o.push_back({t[3 * i], t[3 * i + 1], t[3 * i + 2]});
+    return o;
+  };
+  std::vector<int> ls, rs;
+  for (int s = 0; s < k; ++s) ls.push_back(s);
+  for (int s = k + 2; s < L; ++s) rs.push_back(s);
+  BlockLayout lb, rb;
+  build_layout(lb, 0, L, ls, sectors(nl, sec_l));
+  build_layout(rb, 1, L, rs, sectors(nr, sec_r));
+  Psi Y = psi_layout(lb, rb, (N + two_sz) / 2, (N - two_sz) / 2);
+  TempSet temps;
+  auto rps = resolve_pieces(I, k, lb, rb, temps);
+  const BlockLayout *lay[2] = {&lb, &rb};
+  temps.layout(lay);
+  Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 8};
+  ChainList CL;
+  double f = 0.0;
+  expand_hpsi(rps, A, Y, lb, CL, f);
+  *ntasks = (long long)CL.ent.size();
+  if (out) {
+    if (cap < *ntasks) throw Fail{DMRG_EINVAL, "dmrg_debug_tasks: buffer too small"};
+    for (size_t i = 0; i < CL.ent.size(); ++i) {
+      const int g = CL.ent[i].first;
+      const ChainEntry &e = CL.ent[i].second;
+      int *o = out + 7 * i;
+      o[0] = g;
+      o[1] = Y.blk[g].ma;  // m
+      o[2] = e.n;
+      o[3] = e.p;
+      o[4] = Y.blk[g].md;  // q
+      o[5] = (e.x == ~0ull ? 1 : 0) | (e.z == ~0ull ? 2 : 0);
+      o[6] = (int)e.y;     // input block offset in psi
+    }
+  }
   API_END
 }
 
@@ -2290,7 +2442,7 @@ static ChainTune autotune_chain(const ChainList &CL, bool tc, bool lowp, const d
   };
   ChainTune best = start;
   best_ms = run(best);
-  const double targets[] = {2048.0, 8192.0, 32768.0};
+  const double targets[] = {2048.0, 8192.0, 32768.0, 131072.0};
   const double mins[] = {5.0e4, 2.0e5};
   for (double tg : targets)
     for (double mn : mins) {

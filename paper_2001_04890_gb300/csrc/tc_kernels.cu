@@ -213,26 +213,44 @@ static constexpr int T2_SMEM = T2_BAR_OFF + (int)sizeof(T2Bars);
 // at most two CTAs (2 x 256 TMEM columns) per SM
 static constexpr int T2_SMEM_LAUNCH = 100 * 1024;
 
+// Time-out record: status[0] = 1; the first CTA to time out also fills
+// status[1..7] = wait site, parity, block, aux0, aux1, raw mbarrier word (lo, hi)
+__device__ __noinline__ void t2_timeout(int *status, uint64_t *bar, int site, uint32_t parity, int aux0,
+                                        int aux1) {
+  atomicExch(status, 1);
+  if (atomicCAS(status + 1, 0, site) == 0) {
+    const unsigned long long w = *reinterpret_cast<volatile unsigned long long *>(bar);
+    status[2] = (int)parity;
+    status[3] = (int)blockIdx.x;
+    status[4] = aux0;
+    status[5] = aux1;
+    status[6] = (int)(w & 0xffffffffu);
+    status[7] = (int)(w >> 32);
+  }
+}
+
 // single-thread bounded wait that gives up early when another role aborted
-__device__ __forceinline__ bool t2_wait1(uint64_t *bar, uint32_t parity, volatile int *abort, int *status) {
+__device__ __forceinline__ bool t2_wait1(uint64_t *bar, uint32_t parity, volatile int *abort, int *status,
+                                         int site, int aux0, int aux1) {
   for (long long i = 0; i < kMaxWaitTries; ++i) {
     if (tc::mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 63 && *abort) return false;
   }
   *abort = 1;
-  atomicExch(status, 1);
+  t2_timeout(status, bar, site, parity, aux0, aux1);
   return false;
 }
 
 // warp-uniform bounded wait (all 32 lanes take the same decision)
-__device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatile int *abort, int *status) {
+__device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatile int *abort, int *status,
+                                         int site, int aux0, int aux1) {
   for (long long i = 0; i < kMaxWaitTries; ++i) {
     if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity))) return true;
     if ((i & 63) == 63 && __any_sync(0xffffffffu, *abort)) return false;
   }
   if ((threadIdx.x & 31) == 0) {
     *abort = 1;
-    atomicExch(status, 1);
+    t2_timeout(status, bar, site, parity, aux0, aux1);
   }
   __syncwarp();
   return false;
@@ -291,7 +309,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
       for (int gl = 0; ok; ++gl) {
         // take the next output block and publish it to the other roles
         const int r = gl % T2_GR;
-        if (!t2_wait1(&B->gempty[r], ((uint32_t)(gl / T2_GR) & 1u) ^ 1u, abort, status)) break;
+        if (!t2_wait1(&B->gempty[r], ((uint32_t)(gl / T2_GR) & 1u) ^ 1u, abort, status, 101, j, gl)) break;
         const int gi0 = atomicAdd(counter, 1);
         const int gi = gi0 < ngroups ? gi0 : -1;
         gidx[r] = gi;
@@ -308,7 +326,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           for (int c = 0; c < nch1 + nch2 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+            if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 102, j, (int)u)) {
               ok = false;
               break;
             }
@@ -343,7 +361,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
       bool ok = true;
       for (; ok; ++gl) {
         const int r = gl % T2_GR;
-        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status)) break;
+        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 103, j, le)) break;
         const int gi = gidx[r];
         tc::mbar_arrive(&B->gempty[r]);
         if (gi < 0) break;
@@ -358,7 +376,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           const int n16 = ceil16(e.n), p16 = ceil16(e.p);
           const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
           if (le > 0) {  // T of the previous entry has been read
-            if (!t2_wait1(&B->tempty, (uint32_t)(le - 1) & 1u, abort, status)) {
+            if (!t2_wait1(&B->tempty, (uint32_t)(le - 1) & 1u, abort, status, 104, j, le)) {
               ok = false;
               break;
             }
@@ -368,7 +386,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           for (int c = 0; c < nch1 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->full[s], u & 1u, abort, status)) {
+            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 105, j, le)) {
               ok = false;
               break;
             }
@@ -389,7 +407,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           if (!ok) break;
           tc::mma_commit(&B->tfull);
           if (dfirst && gl > 0) {  // D of the previous block has been written out
-            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status)) {
+            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 106, j, le)) {
               ok = false;
               break;
             }
@@ -398,8 +416,8 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           for (int c = 0; c < nch2 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->full[s], u & 1u, abort, status) ||
-                !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status)) {
+            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 107, j, le) ||
+                !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 108, j, le)) {
               ok = false;
               break;
             }
@@ -433,7 +451,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
     bool ok = true;
     for (; ok; ++gl) {
       const int r = gl % T2_GR;
-      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status)) break;
+      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 109, j, le)) break;
       const int gi = gidx[r];
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&B->gempty[r]);
@@ -448,7 +466,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
         const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
         const float f = e.f;
         j += nch1;
-        if (!t2_waitw(&B->tfull, (uint32_t)le & 1u, abort, status)) {
+        if (!t2_waitw(&B->tfull, (uint32_t)le & 1u, abort, status, 110, j, le)) {
           ok = false;
           break;
         }
@@ -456,7 +474,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
         for (int c = 0; c < nch2; ++c, ++j) {
           const int s = j % T2_NS;
           const uint32_t u = (uint32_t)(j / T2_NS);
-          if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status)) {
+          if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 111, j, le)) {
             ok = false;
             break;
           }
@@ -489,7 +507,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
       }
       if (!ok) break;
       // ---- output block: D (TMEM) -> FP64 global, then release D
-      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status)) {
+      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status, 112, j, le)) {
         ok = false;
         break;
       }

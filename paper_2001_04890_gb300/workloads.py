@@ -124,13 +124,16 @@ def sector_dims_profile(k: int, n_up_tot: int, n_dn_tot: int, L: int, M: int,
     return {key: int(m) for key, m in zip(keys, alloc) if m > 0}
 
 
-def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: int = 0):
+def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: int = 0,
+                     release: bool = False):
     """Grow the left blocks 0..k-1 and right blocks k+2..L-1 of a context with seeded random O.
 
     Each renormalization keeps, per enlarged sector, the number of states given
     by sector_dims_profile (normalised to M) and draws a random orthonormal O.
     Returns the list of (direction, kept, O_flat) applied, in order, so the same
-    bases can be replayed elsewhere.  Leaves ctx at position k.
+    bases can be replayed elsewhere.  Leaves ctx at position k.  With release,
+    each block is freed once the next one is built (ctx.release_block), so only
+    the middle-bond blocks stay resident.
     """
     rng = np.random.default_rng(seed)
     applied = []
@@ -143,6 +146,8 @@ def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: in
         O = np.concatenate([orthonormal_columns(int(d), m, rng).ravel() for (_, _, d), m in zip(lay, kept)])
         ctx.renormalize(+1, O, kept)
         applied.append((+1, kept, O))
+        if release and s >= 1:
+            ctx.release_block(0, s)
     ctx.set_position(L - 2, -1)
     for s in range(L - 1, k + 1, -1):
         n_sites = L - s
@@ -153,5 +158,7 @@ def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: in
         O = np.concatenate([orthonormal_columns(int(d), m, rng).ravel() for (_, _, d), m in zip(lay, kept)])
         ctx.renormalize(-1, O, kept)
         applied.append((-1, kept, O))
+        if release and n_sites >= 2:
+            ctx.release_block(1, n_sites - 1)
     ctx.set_position(k, 1)
     return applied

@@ -53,3 +53,30 @@ def test_tune_calls_reject_bad_arguments_without_a_gpu():
     assert lib.dmrg_autotune(None, 1, None, None) == binding.DMRG_EINVAL
     assert lib.dmrg_batch_autotune(None, 1, None, None) == binding.DMRG_EINVAL
     assert b"dmrg_batch_autotune" in lib.dmrg_last_error()
+
+
+def test_init_rejects_bad_problems_without_a_gpu():
+    import ctypes as C
+    import numpy as np
+    lib = binding.lib()
+    L = 4
+    h = np.eye(L)
+    v = np.zeros((L,) * 4)
+    hp = h.ctypes.data_as(C.POINTER(C.c_double))
+    vp = v.ctypes.data_as(C.POINTER(C.c_double))
+    out = C.c_void_p()
+    cases = [(1, 2, 0, 8, 0),      # L < 2
+             (L, 9, 1, 8, 0),      # N > 2L
+             (L, 4, 1, 8, 0),      # 2Sz parity differs from N
+             (L, 4, 6, 8, 0),      # |2Sz| > N
+             (L, 6, 4, 8, 0),      # 5 up electrons on 4 orbitals
+             (L, 4, 0, 0, 0),      # M < 1
+             (L, 4, 0, 8, 7)]      # unknown precision
+    for (l, n, sz, m, prec) in cases:
+        assert lib.dmrg_init(l, n, sz, hp, vp, m, prec, None, C.byref(out)) == binding.DMRG_EINVAL
+        assert not out.value
+    hbad = h.copy()
+    hbad[1, 2] = np.nan
+    assert lib.dmrg_init(L, 4, 0, hbad.ctypes.data_as(C.POINTER(C.c_double)), vp, 8, 0, None,
+                         C.byref(out)) == binding.DMRG_EINVAL
+    assert b"non-finite" in lib.dmrg_last_error()

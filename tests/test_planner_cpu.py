@@ -141,3 +141,25 @@ def test_new_block_operators_blocking(L, k, side):
         assert _maxdiff(ref, Z) < 1e-12, (op["kind"], op["i"], op["j"])
         kinds_seen.add(op["kind"])
     assert {0, 1}.issubset(kinds_seen)
+
+
+def test_task_dump_reproduces_the_flop_count():
+    """The algorithmic FLOPs the bench reports are the sum over the task list of
+    2 min(m n p + m p q, n p q + m n q) (identity sides cost nothing)."""
+    import numpy as np
+    from paper_2001_04890_gb300 import binding, workloads
+    L, N, k = 10, 10, 4
+    h, v = workloads.integrals(L, seed=3)
+    sec = [(a, b, 1 + (3 * a + b) % 5) for a in range(0, 5) for b in range(0, 5)]
+    sec_r = [(a, b, 1 + (a + 2 * b) % 4) for a in range(0, 5) for b in range(0, 5)]
+    flops, tasks = binding.plan_hpsi_flops(h, v, N, 0, k, sec, sec_r)
+    T = binding.debug_tasks(h, v, N, 0, k, sec, sec_r)
+    assert T.shape == (tasks, 7)
+    g, m, n, p, q, idf, yo = T.T.astype(np.float64)
+    xid, zid = (T[:, 5] & 1) > 0, (T[:, 5] & 2) > 0
+    f = np.where(xid & zid, 0.0, np.where(xid, 2 * n * p * q, np.where(zid, 2 * m * n * p,
+                 2 * np.minimum(m * n * p + m * p * q, n * p * q + m * n * q))))
+    assert abs(f.sum() - flops) <= 1e-9 * flops
+    # an identity side is square, and every task maps an input block to an output block of the layout
+    assert np.all(n[xid] == m[xid]) and np.all(p[zid] == q[zid])
+    assert np.all(T[:, 1:5] >= 1)
