@@ -92,6 +92,22 @@ def _clock_summary(path, gpu_index):
             "samples": len(sm)}
 
 
+def max_over_ranks(x, device):
+    """Max of a per-rank scalar over all ranks (replicas: the job takes as long as its slowest rank)."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return float(x)
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def whole_job_tflops(flops_per_rank, world, step_ms_max):
+    """Whole-job throughput of N replicas: all ranks' algorithmic FLOPs over the slowest rank's time."""
+    return flops_per_rank * world / (step_ms_max * 1e-3) / 1e12
+
+
 def _peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -202,11 +218,7 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
     ctx.set_psi(psi0_dev)
     e_mid, _ = ctx.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
     psi_mid = ctx.get_psi()
-    step_ms_max = step_ms
-    if world > 1:
-        t = torch.tensor([step_ms], device=f"cuda:{dev}")
-        torch.distributed.all_reduce(t, op=torch.distributed.ReduceOp.MAX)
-        step_ms_max = float(t.item())
+    step_ms_max = max_over_ranks(step_ms, f"cuda:{dev}")
     ctx.close()
     return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st,
                 step_ms=step_ms_max, iters=iters, energy=energy, e2e_ms=e2e_ms, tune=tune,
@@ -561,7 +573,7 @@ def main():
     st = r["stats"]
     K = args.steps
     hpsi_flops = st["hpsi_flops"]
-    value = hpsi_flops * world / (r["step_ms"] * 1e-3) / 1e12
+    value = whole_job_tflops(hpsi_flops, world, r["step_ms"])
     kernel_tflops = st["hpsi_flops"] / (st["hpsi_ms"] * 1e-3) / 1e12 if st["hpsi_ms"] > 0 else None
     dav_iters = st["davidson_iters"]
     peaks = _peaks()
@@ -606,20 +618,24 @@ def main():
         "cpu_baseline": None,
     }
     if not args.no_mixed and prec == 0:
-        m = run_gpu(args, wl, rank, world, 1, e2e=False, sample_clocks=False)
-        ms = m["stats"]
-        line["mixed_fp32"] = {
-            "what": "same step with FP32 operator copies for the Davidson matvecs, then FP64-matvec "
-                    "refinement to the same tolerance; FP64 renormalization and density matrix",
-            "value": ms["hpsi_flops"] / (m["step_ms"] * 1e-3) / 1e12,
-            "ms_per_step": m["step_ms"] / K,
-            "speedup_vs_fp64_step": r["step_ms"] / m["step_ms"],
-            "davidson_iters_per_step": ms["davidson_iters"] / K,
-            "fp32_matvec_iters_per_step": ms["davidson_iters_lowp"] / K,
-            "abs_dE_vs_fp64": abs(m["e_mid"] - r["e_mid"]),
-            "overlap_vs_fp64": float(abs(np.dot(m["psi_mid"], r["psi_mid"]))),
-            "energy": m["e_mid"],
-        }
+        for key, lp, what in (
+                ("mixed_fp32", 1, "FP32 operator copies for the Davidson matvecs"),
+                ("mixed_bf16x3", 2, "split-BF16x3 tensor-core matvecs (FP32 SIMT below the routing threshold)")):
+            m = run_gpu(args, wl, rank, world, lp, e2e=False, sample_clocks=False)
+            ms = m["stats"]
+            line[key] = {
+                "what": f"same step with {what}, then the FP64 defect-corrected refinement to the same "
+                        "tolerance; FP64 renormalization and density matrix",
+                "value": ms["hpsi_flops"] / (m["step_ms"] * 1e-3) / 1e12,
+                "ms_per_step": m["step_ms"] / K,
+                "speedup_vs_fp64_step": r["step_ms"] / m["step_ms"],
+                "davidson_iters_per_step": ms["davidson_iters"] / K,
+                "lowp_matvec_iters_per_step": ms["davidson_iters_lowp"] / K,
+                "launch_shape": m["tune"],
+                "abs_dE_vs_fp64": abs(m["e_mid"] - r["e_mid"]),
+                "overlap_vs_fp64": float(abs(np.dot(m["psi_mid"], r["psi_mid"]))),
+                "energy": m["e_mid"],
+            }
     if rank == 0 and not args.no_cpu_baseline:
         try:
             from oracle import baseline
