@@ -299,11 +299,11 @@ struct DevChain {
   // tensor-core groups: entries with pre-split operand tiles (operators tiled
   // once here, the psi blocks they read re-tiled at every launch)
   DBuf<TcEntry> tce;
-  DBuf<TcGroup> tcg;
+  DBuf<TcGroup> tcg;  // blocks ordered by kernel shape: 2, 1, 0 (ntc_shape[] of each)
   DBuf<PsiTileSpec> pts;
   DBuf<uint8_t> optiles, psitiles;
-  DBuf<int> tc_counter;  // work counter of the persistent tensor-core kernel
-  int npts = 0;
+  DBuf<int> tc_counter;  // work counters of the persistent tensor-core kernels (two shapes)
+  int npts = 0, ntc_shape[3] = {0, 0, 0};
   int flat_wide = 1;
   int nall = 0, nbig = 0, nflat = 0, ntc = 0, ntiles = 0, nred = 0;
   int64_t nent = 0;
@@ -504,7 +504,32 @@ struct DevChain {
       opbytes += c16(R) * c16(K) * 4;
       return at;
     };
-    for (const auto &g : vt) {
+    // kernel shape per block: 2 (m <= 64, q, p <= 32), 1 (m, q, p <= 64), 0 (the rest);
+    // groups ordered by shape.  Shape 2 is used only when every block fits it: each
+    // shape is its own launch with its own last-wave tail, and a third launch costs
+    // more than the extra resident CTAs gain when larger blocks are present.
+    auto fits = [&](const ChainGroup &g, int lim_q) {
+      int pmax = 0;
+      for (int i = g.first; i < g.first + g.count; ++i) pmax = std::max(pmax, xs[i].p);
+      return g.m <= 64 && g.q <= lim_q && pmax <= lim_q;
+    };
+    bool all_tiny = true;
+    for (const auto &g : vt) all_tiny = all_tiny && fits(g, 32);
+    auto shape_of = [&](const ChainGroup &g) {
+      if (all_tiny) return 2;
+      return fits(g, 64) ? 1 : 0;
+    };
+    std::vector<ChainGroup> order;
+    for (int sh : {2, 1, 0}) {
+      int cnt = 0;
+      for (const auto &g : vt)
+        if (shape_of(g) == sh) {
+          order.push_back(g);
+          ++cnt;
+        }
+      ntc_shape[sh] = cnt;
+    }
+    for (const auto &g : order) {
       tg.push_back(TcGroup{g.d, g.drs, g.dcs, g.m, g.q, (int)te.size(), g.count});
       for (int i = g.first; i < g.first + g.count; ++i) {
         const ChainEntry &e = xs[i];
@@ -532,7 +557,7 @@ struct DevChain {
     pts.upload(ps, s);
     optiles.alloc((size_t)opbytes);
     psitiles.alloc((size_t)psibytes);
-    tc_counter.alloc(1);
+    tc_counter.alloc(3);
     DBuf<TileSpec> tsd;
     tsd.upload(ts, s);
     CK(launch_build_tiles(tsd.p, (int)ts.size(), optiles.p, s));
@@ -543,7 +568,12 @@ struct DevChain {
     if (ntc == 0) return;
     if (!status) throw Fail{DMRG_EINVAL, "tensor-core task list launched without a status word"};
     CK(launch_psi_tiles(pts.p, npts, reinterpret_cast<const double *>(yb), psitiles.p, s));
-    CK(launch_chain_tc2(tce.p, tcg.p, ntc, optiles.p, psitiles.p, tb, tc_counter.p, status, s));
+    int first = 0;
+    for (int sh : {2, 1, 0}) {
+      CK(launch_chain_tc2(tce.p, tcg.p + first, ntc_shape[sh], optiles.p, psitiles.p, tb, tc_counter.p + sh,
+                          status, sh, s));
+      first += ntc_shape[sh];
+    }
   }
 
   void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s,

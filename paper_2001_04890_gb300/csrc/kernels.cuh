@@ -119,8 +119,11 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
                              cudaStream_t s);
 // tensor-core H.psi chain (split-BF16 x3, FP32 accumulation, FP64 output blocks), persistent
 // CTAs taking groups (m, q <= 128, every entry n, p <= 128) from *counter (zeroed here on s);
-// *status is raised if an mbarrier wait ran out
+// shape 1: every group has m, q <= 64 and every entry p <= 64 (MMA M = 64, four CTAs per SM);
+// shape 2: m <= 64, q and p <= 32 (five CTAs per SM); shape 0: the rest;
+// *status (8 ints) is raised if an mbarrier wait ran out
 cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
-                             const uint8_t *psitiles, uint64_t db, int *counter, int *status, cudaStream_t s);
+                             const uint8_t *psitiles, uint64_t db, int *counter, int *status, int shape,
+                             cudaStream_t s);
 
 }  // namespace dmrg

@@ -90,17 +90,18 @@ namespace dmrg {
 //
 // Every operand the tensor core reads from global memory is stored once as a
 // ready-made shared-memory image: rows padded to R16 = ceil16(R) and K to
-// K16 = ceil16(K) with zeros, cut into K chunks of T2_W = 32 columns (the last
-// chunk 16 wide when K16 % 32 == 16).  Chunk c starts at byte 128 * R16 * c and
-// holds the bf16 hi part (R16 x w, K-major core matrices, core matrix (rg, kg)
-// at (rg * w/8 + kg) * 128) followed by the lo part.  A chunk is one 1-D bulk
-// copy (cp.async.bulk) into shared memory, so staging costs no thread work.
+// K16 = ceil16(K) with zeros, cut into K chunks of T2_W columns (the last one
+// narrower when T2_W does not divide K16).  Chunk c starts at byte
+// 4 * T2_W * R16 * c and holds the bf16 hi part (R16 x w, K-major core
+// matrices, core matrix (rg, kg) at (rg * w/8 + kg) * 128) followed by the lo
+// part.  A chunk is one 1-D bulk copy (cp.async.bulk) into shared memory, so
+// staging costs no thread work.
 //
 // Operator blocks (X and Z^T views of the stored and pre-summed operators)
 // are tiled once per task list; the psi blocks (as Y^T) once per H.psi call.
 // ---------------------------------------------------------------------------
 
-static constexpr int T2_W = 32;
+static constexpr int T2_W = 32;  // K chunk width (elements); a chunk of R16 rows is 4 * T2_W * R16 bytes
 
 template <typename Load>
 __device__ __forceinline__ void write_tile(uint8_t *img, int R, int K, Load load, int t0, int nt) {
@@ -109,7 +110,7 @@ __device__ __forceinline__ void write_tile(uint8_t *img, int R, int K, Load load
   for (int u = t0; u < units; u += nt) {
     const int r = u % R16, kg = u / R16, k0 = kg * 8;
     const int c = k0 / T2_W, w = min(T2_W, K16 - c * T2_W), kgi = (k0 - c * T2_W) >> 3;
-    uint8_t *hi = img + (size_t)128 * R16 * c + ((r >> 3) * (w >> 3) + kgi) * 128 + (r & 7) * 16;
+    uint8_t *hi = img + (size_t)4 * T2_W * R16 * c + ((r >> 3) * (w >> 3) + kgi) * 128 + (r & 7) * 16;
     uint8_t *lo = hi + (size_t)R16 * w * 2;
     __align__(16) __nv_bfloat16 h[8], l[8];
 #pragma unroll
@@ -178,7 +179,7 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 //   stage 2 (K = p):  D += (f T) Z      A = f T chunk written by the converter
 //                                        warps from TMEM, B = Z^T chunk bulk-copied
 // Identity X / Z are exact identity tiles.  Jobs run through a ring of T2_NS
-// shared-memory stages (A half | B half, 16 KB each) with warp roles:
+// shared-memory stages (A half | B half, 128 rows x T2_W hi + lo each) with warp roles:
 //   warps 0-3  converters: T (TMEM lanes = rows) -> f T split into bf16 hi/lo
 //              in stage 2 jobs; at the end of a block D (TMEM) -> FP64 output
 //   warp 4     producer: bulk copies of the operand chunks
@@ -193,11 +194,30 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 // ---------------------------------------------------------------------------
 
 static constexpr int T2_NS = 3;
-static constexpr int T2_HALF = 16384;
-static constexpr int T2_STAGE = 2 * T2_HALF;
-static constexpr int T2_BAR_OFF = T2_NS * T2_STAGE;
 static constexpr int T2_THREADS = 192;
-static constexpr int T2_CTAS_PER_SM = 2;
+
+// Three shapes of the kernel, by the size of the output blocks they take:
+//   T2Shape<128, 128, 2>: MMA M = 128, T and D 128 TMEM columns each, two CTAs per SM
+//   T2Shape< 64,  64, 4>: m <= 64, q and every task's p <= 64, four CTAs per SM
+//   T2Shape< 64,  32, 5>: m <= 64, q and every task's p <= 32, five CTAs per SM
+// More resident CTAs hide more of the per-task latency of small blocks.  With
+// M = 64 the accumulator row r sits in TMEM lane 32 (r / 16) + r % 16.
+template <int MR, int TC, int CTAS>
+struct T2Shape {
+  static constexpr int AHALF = MR * T2_W * 4;  // A operand of a stage: MR rows, hi + lo
+  static constexpr int BHALF = TC * T2_W * 4;  // B operand: at most TC rows, hi + lo
+  static constexpr int ALO = MR * T2_W * 2;    // lo part of the converter-written A operand
+  static constexpr int STAGE = AHALF + BHALF;
+  static constexpr int BAR_OFF = T2_NS * STAGE;
+  static constexpr int TCOLS = TC;             // T and D regions of TMEM
+  static constexpr int CTAS_PER_SM = CTAS;
+  static constexpr int SMEM_LAUNCH = CTAS == 2 ? 100 * 1024 : CTAS == 4 ? 50 * 1024 : 40 * 1024;
+  // accumulator row held by TMEM lane L (-1: none)
+  __device__ static __forceinline__ int row_of_lane(int L) {
+    if (MR == 128) return L;
+    return (L & 31) < 16 ? (L >> 5) * 16 + (L & 31) : -1;
+  }
+};
 
 static constexpr int T2_GR = 4;  // ring of fetched output-block indices
 
@@ -209,9 +229,6 @@ struct T2Bars {
   uint32_t tslot;
   int abort;
 };
-static constexpr int T2_SMEM = T2_BAR_OFF + (int)sizeof(T2Bars);
-// at most two CTAs (2 x 256 TMEM columns) per SM
-static constexpr int T2_SMEM_LAUNCH = 100 * 1024;
 
 // Time-out record: status[0] = 1; the first CTA to time out also fills
 // status[1..7] = wait site, parity, block, aux0, aux1, raw mbarrier word (lo, hi)
@@ -258,16 +275,18 @@ __device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatil
 
 __device__ __forceinline__ int ceil16(int x) { return (x + 15) & ~15; }
 
+template <int MR, int TC, int CTAS>
 __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__restrict__ E,
                                                                const TcGroup *__restrict__ G, int ngroups,
                                                                const uint8_t *__restrict__ optiles,
                                                                const uint8_t *__restrict__ psitiles,
                                                                uint64_t db, int *counter, int *status) {
   extern __shared__ __align__(1024) uint8_t smem[];
-  T2Bars *B = reinterpret_cast<T2Bars *>(smem + T2_BAR_OFF);
+  using S = T2Shape<MR, TC, CTAS>;
+  T2Bars *B = reinterpret_cast<T2Bars *>(smem + S::BAR_OFF);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
-    tc::tmem_alloc(&B->tslot, 256);
+    tc::tmem_alloc(&B->tslot, 2 * S::TCOLS);
     tc::tmem_relinquish();
   }
   if (tid == 0) {
@@ -289,15 +308,15 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
   }
   // A halves: rows beyond a block's 16-row padding only feed discarded TMEM lanes,
   // but must hold finite values (B halves are read only where copied)
-  for (int i = tid; i < T2_NS * (T2_HALF / 16); i += T2_THREADS) {
-    const int s = i / (T2_HALF / 16), o = i % (T2_HALF / 16);
-    reinterpret_cast<uint4 *>(smem + s * T2_STAGE)[o] = make_uint4(0, 0, 0, 0);
+  for (int i = tid; i < T2_NS * (S::AHALF / 16); i += T2_THREADS) {
+    const int s = i / (S::AHALF / 16), o = i % (S::AHALF / 16);
+    reinterpret_cast<uint4 *>(smem + s * S::STAGE)[o] = make_uint4(0, 0, 0, 0);
   }
   tc::fence_async_smem();
   tc::fence_before();
   __syncthreads();
   tc::fence_after();
-  const uint32_t tbase = B->tslot, tT = tbase, tD = tbase + 128;
+  const uint32_t tbase = B->tslot, tT = tbase, tD = tbase + S::TCOLS;
   volatile int *abort = &B->abort;
   volatile int *gidx = B->gidx;
 
@@ -330,18 +349,18 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
               ok = false;
               break;
             }
-            uint8_t *st = smem + s * T2_STAGE;
+            uint8_t *st = smem + s * S::STAGE;
             if (c < nch1) {
               const int w = min(T2_W, n16 - c * T2_W);
               const uint32_t bx = (uint32_t)(m16 * w * 4), by = (uint32_t)(p16 * w * 4);
               tc::mbar_arrive_expect_tx(&B->full[s], bx + by);
-              tc::bulk_g2s(st, optiles + e.xt + (uint64_t)128 * m16 * c, bx, &B->full[s]);
-              tc::bulk_g2s(st + T2_HALF, psitiles + e.yt + (uint64_t)128 * p16 * c, by, &B->full[s]);
+              tc::bulk_g2s(st, optiles + e.xt + (uint64_t)4 * T2_W * m16 * c, bx, &B->full[s]);
+              tc::bulk_g2s(st + S::AHALF, psitiles + e.yt + (uint64_t)4 * T2_W * p16 * c, by, &B->full[s]);
             } else {
               const int c2 = c - nch1, w = min(T2_W, p16 - c2 * T2_W);
               const uint32_t bz = (uint32_t)(q16 * w * 4);
               tc::mbar_arrive_expect_tx(&B->full[s], bz);
-              tc::bulk_g2s(st + T2_HALF, optiles + e.zt + (uint64_t)128 * q16 * c2, bz, &B->full[s]);
+              tc::bulk_g2s(st + S::AHALF, optiles + e.zt + (uint64_t)4 * T2_W * q16 * c2, bz, &B->full[s]);
             }
           }
         }
@@ -367,7 +386,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
         if (gi < 0) break;
         const TcGroup g = G[gi];
         const int m16 = ceil16(g.m), q16 = ceil16(g.q), e_end = g.first + g.count;
-        const uint32_t id2 = tc::idesc_bf16(128, q16);
+        const uint32_t id2 = tc::idesc_bf16(MR, q16);
         bool dfirst = true;
         TcEntry nx = E[g.first];
         for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
@@ -382,7 +401,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
             }
             tc::fence_after();
           }
-          const uint32_t id1 = tc::idesc_bf16(128, p16);
+          const uint32_t id1 = tc::idesc_bf16(MR, p16);
           for (int c = 0; c < nch1 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
@@ -393,7 +412,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
             tc::fence_after();
             const int w = min(T2_W, n16 - c * T2_W);
             const uint32_t sbo = (uint32_t)(w / 8) * 128;
-            const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
+            const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
             const uint32_t alo = a + (uint32_t)(m16 * w * 2), blo = b + (uint32_t)(p16 * w * 2);
             for (int ks = 0; ks < w / 16; ++ks) {
               const uint32_t o = (uint32_t)ks * 256;
@@ -425,8 +444,8 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
             tc::fence_after();
             const int w = min(T2_W, p16 - c * T2_W);
             const uint32_t sbo = (uint32_t)(w / 8) * 128;
-            const uint32_t a = tc::smem_u32(smem + s * T2_STAGE), b = a + T2_HALF;
-            const uint32_t alo = a + 8192, blo = b + (uint32_t)(q16 * w * 2);
+            const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
+            const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(q16 * w * 2);
             for (int ks = 0; ks < w / 16; ++ks) {
               const uint32_t o = (uint32_t)ks * 256;
               tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
@@ -444,8 +463,8 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
       tc::mbar_wait(&B->drain, 0, kMaxWaitTries);
     }
   } else {
-    // ---------------- converters (thread = row = TMEM lane)
-    const int row = tid;
+    // ---------------- converters (thread = TMEM lane = accumulator row, if any)
+    const int row = S::row_of_lane(tid);
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
     int j = 0, le = 0, gl = 0;
     bool ok = true;
@@ -480,11 +499,11 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           }
           tc::fence_after();
           const int w = min(T2_W, p16 - c * T2_W);
-          uint8_t *A = smem + s * T2_STAGE;
+          uint8_t *A = smem + s * S::STAGE;
           for (int h = 0; h < w / 16; ++h) {
             float v[16];
             tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
-            if (row < m) {
+            if (row >= 0 && row < m) {
 #pragma unroll
               for (int g2 = 0; g2 < 2; ++g2) {
                 __align__(16) __nv_bfloat16 hb[8], lb[8];
@@ -492,7 +511,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
                 for (int i = 0; i < 8; ++i) tc::split_bf16(f * v[8 * g2 + i], hb[i], lb[i]);
                 uint8_t *dst = A + ((row >> 3) * (w >> 3) + 2 * h + g2) * 128 + (row & 7) * 16;
                 *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
-                *reinterpret_cast<uint4 *>(dst + 8192) = *reinterpret_cast<const uint4 *>(lb);
+                *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
               }
             }
           }
@@ -516,7 +535,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
       for (int c0 = 0; c0 < q16; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tD + lane_off + (uint32_t)c0, v);
-        if (row < m) {
+        if (row >= 0 && row < m) {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
             if (c0 + i < q) D[(int64_t)row * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
@@ -530,28 +549,41 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
   __syncwarp();  // lanes 1-31 of the producer and MMA warps rejoin lane 0
   tc::fence_before();
   __syncthreads();
-  if (warp == 0) tc::tmem_dealloc(tbase, 256);
+  if (warp == 0) tc::tmem_dealloc(tbase, 2 * S::TCOLS);
 }
 
-cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
-                             const uint8_t *psitiles, uint64_t db, int *counter, int *status, cudaStream_t s) {
-  if (ngroups <= 0) return cudaSuccess;
-  cudaError_t err0 = cudaMemsetAsync(counter, 0, sizeof(int), s);
-  if (err0 != cudaSuccess) return err0;
-  static_assert(T2_SMEM <= T2_SMEM_LAUNCH, "shared memory budget");
-  cudaError_t err = cudaFuncSetAttribute(chain_tc2_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         T2_SMEM_LAUNCH);
+template <int MR, int TC, int CTAS>
+static cudaError_t launch_tc2_shape(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
+                                   const uint8_t *psitiles, uint64_t db, int *counter, int *status,
+                                   cudaStream_t s) {
+  using S = T2Shape<MR, TC, CTAS>;
+  static_assert(S::BAR_OFF + (int)sizeof(T2Bars) <= S::SMEM_LAUNCH, "shared memory budget");
+  // the launch size caps resident CTAs per SM at CTAS, so their TMEM fits the SM's 512 columns
+  static_assert((CTAS + 1) * (S::SMEM_LAUNCH + 1024) > 228 * 1024, "more resident CTAs than intended");
+  static_assert(CTAS * 2 * TC <= 512, "TMEM oversubscription");
+  cudaError_t err = cudaMemsetAsync(counter, 0, sizeof(int), s);
+  if (err != cudaSuccess) return err;
+  auto kern = chain_tc2_kernel<MR, TC, CTAS>;
+  err = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, S::SMEM_LAUNCH);
   if (err != cudaSuccess) return err;
   int dev = 0, sms = 0;
   err = cudaGetDevice(&dev);
   if (err != cudaSuccess) return err;
   err = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   if (err != cudaSuccess) return err;
-  const int grid = std::min(ngroups, T2_CTAS_PER_SM * std::max(sms, 1));
+  const int grid = std::min(ngroups, CTAS * std::max(sms, 1));
   add_kernel_launches(1);
-  chain_tc2_kernel<<<grid, T2_THREADS, T2_SMEM_LAUNCH, s>>>(e, g, ngroups, optiles, psitiles, db, counter,
-                                                             status);
+  kern<<<grid, T2_THREADS, S::SMEM_LAUNCH, s>>>(e, g, ngroups, optiles, psitiles, db, counter, status);
   return cudaGetLastError();
+}
+
+cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
+                             const uint8_t *psitiles, uint64_t db, int *counter, int *status, int shape,
+                             cudaStream_t s) {
+  if (ngroups <= 0) return cudaSuccess;
+  if (shape == 2) return launch_tc2_shape<64, 32, 5>(e, g, ngroups, optiles, psitiles, db, counter, status, s);
+  if (shape == 1) return launch_tc2_shape<64, 64, 4>(e, g, ngroups, optiles, psitiles, db, counter, status, s);
+  return launch_tc2_shape<128, 128, 2>(e, g, ngroups, optiles, psitiles, db, counter, status, s);
 }
 
 }  // namespace dmrg
