@@ -531,9 +531,25 @@ struct DevChain {
     }
     for (const auto &g : order) {
       tg.push_back(TcGroup{g.d, g.drs, g.dcs, g.m, g.q, (int)te.size(), g.count});
-      for (int i = g.first; i < g.first + g.count; ++i) {
+      // tasks of this output block that read the same psi block run as stacks: their X
+      // along the MMA's M in one stage 1 (at most MR / m16 of them, MR the shape's M)
+      const int mr = shape_of(g) == 0 ? 128 : 64;
+      const int cap = std::max(1, std::min(8, mr / (int)c16(g.m)));
+      std::vector<int> idx(g.count);
+      std::iota(idx.begin(), idx.end(), g.first);
+      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return xs[a].y < xs[b].y; });
+      int remaining = 0;
+      for (size_t k = 0; k < idx.size(); ++k) {
+        const int i = idx[k];
         const ChainEntry &e = xs[i];
         TcEntry t{};
+        if (remaining == 0) {  // first member of a stack: the run of tasks on this psi block
+          int run = 1;
+          while (run < cap && k + run < idx.size() && xs[idx[k + run]].y == e.y) ++run;
+          t.stack = run;
+          remaining = run;
+        }
+        --remaining;
         t.n = e.n;
         t.p = e.p;
         t.f = (float)e.f;

@@ -102,9 +102,10 @@ struct PsiTileSpec {
 // One task of the pipelined tensor-core chain: D += f X Y Z with X, Y^T, Z^T given as tiles
 struct TcEntry {
   uint64_t xt, yt, zt;  // byte offsets: X tile (op arena), Y^T tile (psi tiles), Z^T tile (op arena)
-  int n, p;             // inner dims (<= 64)
+  int n, p;             // inner dims (<= 128)
   float f;
-  int pad;
+  int stack;            // first task of a stack: the number of consecutive tasks (same Y, same
+                        // output block) whose X run stacked along M in one stage 1; others 0
 };
 struct TcGroup {
   uint64_t d;       // element offset of the output block (or scratch slot)

@@ -194,6 +194,7 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 // ---------------------------------------------------------------------------
 
 static constexpr int T2_NS = 3;
+static constexpr int T2_MAXSTACK = 8;  // tasks stacked along M in one stage 1 (128 rows / 16)
 static constexpr int T2_THREADS = 192;
 
 // Three shapes of the kernel, by the size of the output blocks they take:
@@ -276,7 +277,7 @@ __device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatil
 __device__ __forceinline__ int ceil16(int x) { return (x + 15) & ~15; }
 
 template <int MR, int TC, int CTAS>
-__global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__restrict__ E,
+__global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEntry *__restrict__ E,
                                                                const TcGroup *__restrict__ G, int ngroups,
                                                                const uint8_t *__restrict__ optiles,
                                                                const uint8_t *__restrict__ psitiles,
@@ -336,13 +337,20 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
         if (gi < 0) break;
         const TcGroup g = G[gi];
         const int m16 = ceil16(g.m), q16 = ceil16(g.q), e_end = g.first + g.count;
-        TcEntry nx = E[g.first];
-        for (int ei = g.first; ei < e_end && ok; ++ei) {
-          const TcEntry e = nx;
-          if (ei + 1 < e_end) nx = E[ei + 1];  // next entry's load overlaps this one's work
+        for (int ei = g.first; ei < e_end && ok;) {
+          const TcEntry e = E[ei];
+          const int ns = min(max(e.stack, 1), T2_MAXSTACK);
+          uint64_t xts[T2_MAXSTACK], zts[T2_MAXSTACK];
+#pragma unroll
+          for (int i = 0; i < T2_MAXSTACK; ++i)
+            if (i < ns) {
+              xts[i] = E[ei + i].xt;
+              zts[i] = E[ei + i].zt;
+            }
           const int n16 = ceil16(e.n), p16 = ceil16(e.p);
           const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-          for (int c = 0; c < nch1 + nch2 && ok; ++c, ++j) {
+          // stage 1 of the stack: the X chunks of every member, rows stacked, and one Y^T chunk
+          for (int c = 0; c < nch1 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
             if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 102, j, (int)u)) {
@@ -350,19 +358,32 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
               break;
             }
             uint8_t *st = smem + s * S::STAGE;
-            if (c < nch1) {
-              const int w = min(T2_W, n16 - c * T2_W);
-              const uint32_t bx = (uint32_t)(m16 * w * 4), by = (uint32_t)(p16 * w * 4);
-              tc::mbar_arrive_expect_tx(&B->full[s], bx + by);
-              tc::bulk_g2s(st, optiles + e.xt + (uint64_t)4 * T2_W * m16 * c, bx, &B->full[s]);
-              tc::bulk_g2s(st + S::AHALF, psitiles + e.yt + (uint64_t)4 * T2_W * p16 * c, by, &B->full[s]);
-            } else {
-              const int c2 = c - nch1, w = min(T2_W, p16 - c2 * T2_W);
+            const int w = min(T2_W, n16 - c * T2_W);
+            const uint32_t bx = (uint32_t)(m16 * w * 2), by = (uint32_t)(p16 * w * 4);
+            tc::mbar_arrive_expect_tx(&B->full[s], 2 * bx * ns + by);
+            for (int i = 0; i < ns; ++i) {
+              const uint8_t *src = optiles + xts[i] + (uint64_t)4 * T2_W * m16 * c;
+              tc::bulk_g2s(st + i * bx, src, bx, &B->full[s]);                 // hi rows
+              tc::bulk_g2s(st + S::ALO + i * bx, src + bx, bx, &B->full[s]);   // lo rows
+            }
+            tc::bulk_g2s(st + S::AHALF, psitiles + e.yt + (uint64_t)4 * T2_W * p16 * c, by, &B->full[s]);
+          }
+          // stage 2 of each member: its Z^T chunks
+          for (int i = 0; i < ns && ok; ++i)
+            for (int c = 0; c < nch2 && ok; ++c, ++j) {
+              const int s = j % T2_NS;
+              const uint32_t u = (uint32_t)(j / T2_NS);
+              if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 103, j, (int)u)) {
+                ok = false;
+                break;
+              }
+              const int w = min(T2_W, p16 - c * T2_W);
               const uint32_t bz = (uint32_t)(q16 * w * 4);
               tc::mbar_arrive_expect_tx(&B->full[s], bz);
-              tc::bulk_g2s(st + S::AHALF, optiles + e.zt + (uint64_t)4 * T2_W * q16 * c2, bz, &B->full[s]);
+              tc::bulk_g2s(smem + s * S::STAGE + S::AHALF, optiles + zts[i] + (uint64_t)4 * T2_W * q16 * c, bz,
+                           &B->full[s]);
             }
-          }
+          ei += ns;
         }
       }
       // copies in flight land before the CTA exits (bounded)
@@ -375,27 +396,26 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
   } else if (warp == 5) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      int j = 0, le = 0, gl = 0;
+      int j = 0, ls = 0, gl = 0;
       uint32_t cvpar = 0;
       bool ok = true;
       for (; ok; ++gl) {
         const int r = gl % T2_GR;
-        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 103, j, le)) break;
+        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 104, j, ls)) break;
         const int gi = gidx[r];
         tc::mbar_arrive(&B->gempty[r]);
         if (gi < 0) break;
         const TcGroup g = G[gi];
-        const int m16 = ceil16(g.m), q16 = ceil16(g.q), e_end = g.first + g.count;
+        const int q16 = ceil16(g.q), e_end = g.first + g.count;
         const uint32_t id2 = tc::idesc_bf16(MR, q16);
         bool dfirst = true;
-        TcEntry nx = E[g.first];
-        for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
-          const TcEntry e = nx;
-          if (ei + 1 < e_end) nx = E[ei + 1];
+        for (int ei = g.first; ei < e_end && ok; ++ls) {
+          const TcEntry e = E[ei];
+          const int ns = min(max(e.stack, 1), T2_MAXSTACK);
           const int n16 = ceil16(e.n), p16 = ceil16(e.p);
           const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-          if (le > 0) {  // T of the previous entry has been read
-            if (!t2_wait1(&B->tempty, (uint32_t)(le - 1) & 1u, abort, status, 104, j, le)) {
+          if (ls > 0) {  // T of the previous stack has been read
+            if (!t2_wait1(&B->tempty, (uint32_t)(ls - 1) & 1u, abort, status, 105, j, ls)) {
               ok = false;
               break;
             }
@@ -405,7 +425,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           for (int c = 0; c < nch1 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 105, j, le)) {
+            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 106, j, ls)) {
               ok = false;
               break;
             }
@@ -413,7 +433,7 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
             const int w = min(T2_W, n16 - c * T2_W);
             const uint32_t sbo = (uint32_t)(w / 8) * 128;
             const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
-            const uint32_t alo = a + (uint32_t)(m16 * w * 2), blo = b + (uint32_t)(p16 * w * 2);
+            const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(p16 * w * 2);
             for (int ks = 0; ks < w / 16; ++ks) {
               const uint32_t o = (uint32_t)ks * 256;
               tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1,
@@ -426,36 +446,38 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
           if (!ok) break;
           tc::mma_commit(&B->tfull);
           if (dfirst && gl > 0) {  // D of the previous block has been written out
-            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 106, j, le)) {
+            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 107, j, ls)) {
               ok = false;
               break;
             }
             tc::fence_after();
           }
-          for (int c = 0; c < nch2 && ok; ++c, ++j) {
-            const int s = j % T2_NS;
-            const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 107, j, le) ||
-                !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 108, j, le)) {
-              ok = false;
-              break;
+          for (int i = 0; i < ns && ok; ++i)
+            for (int c = 0; c < nch2 && ok; ++c, ++j) {
+              const int s = j % T2_NS;
+              const uint32_t u = (uint32_t)(j / T2_NS);
+              if (!t2_wait1(&B->full[s], u & 1u, abort, status, 108, j, ls) ||
+                  !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 109, j, ls)) {
+                ok = false;
+                break;
+              }
+              cvpar ^= 1u << s;
+              tc::fence_after();
+              const int w = min(T2_W, p16 - c * T2_W);
+              const uint32_t sbo = (uint32_t)(w / 8) * 128;
+              const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
+              const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(q16 * w * 2);
+              for (int ks = 0; ks < w / 16; ++ks) {
+                const uint32_t o = (uint32_t)ks * 256;
+                tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
+                             dfirst ? 0u : 1u);
+                dfirst = false;
+                tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
+                tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+              }
+              tc::mma_commit(&B->empty[s]);
             }
-            cvpar ^= 1u << s;
-            tc::fence_after();
-            const int w = min(T2_W, p16 - c * T2_W);
-            const uint32_t sbo = (uint32_t)(w / 8) * 128;
-            const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
-            const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(q16 * w * 2);
-            for (int ks = 0; ks < w / 16; ++ks) {
-              const uint32_t o = (uint32_t)ks * 256;
-              tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
-                           dfirst ? 0u : 1u);
-              dfirst = false;
-              tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
-              tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
-            }
-            tc::mma_commit(&B->empty[s]);
-          }
+          ei += ns;
         }
         if (ok) tc::mma_commit(&B->dfull);
       }
@@ -464,69 +486,74 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
     }
   } else {
     // ---------------- converters (thread = TMEM lane = accumulator row, if any)
-    const int row = S::row_of_lane(tid);
+    const int R = S::row_of_lane(tid);
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    int j = 0, le = 0, gl = 0;
+    int j = 0, ls = 0, gl = 0;
     bool ok = true;
     for (; ok; ++gl) {
       const int r = gl % T2_GR;
-      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 109, j, le)) break;
+      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 110, j, ls)) break;
       const int gi = gidx[r];
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&B->gempty[r]);
       if (gi < 0) break;
       const TcGroup g = G[gi];
-      const int m = g.m, q = g.q, q16 = ceil16(q), e_end = g.first + g.count;
-      TcEntry nx = E[g.first];
-      for (int ei = g.first; ei < e_end && ok; ++ei, ++le) {
-        const TcEntry e = nx;
-        if (ei + 1 < e_end) nx = E[ei + 1];
+      const int m = g.m, q = g.q, m16 = ceil16(m), q16 = ceil16(q), e_end = g.first + g.count;
+      // this thread's T row belongs to stack member R / m16, output row R % m16
+      const int mine = R >= 0 ? R / m16 : -1, orow = R >= 0 ? R % m16 : 0;
+      for (int ei = g.first; ei < e_end && ok; ++ls) {
+        const TcEntry e = E[ei];
+        const int ns = min(max(e.stack, 1), T2_MAXSTACK);
         const int n16 = ceil16(e.n), p16 = ceil16(e.p);
         const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-        const float f = e.f;
+        const float f = mine >= 0 && mine < ns ? E[ei + mine].f : 0.f;
         j += nch1;
-        if (!t2_waitw(&B->tfull, (uint32_t)le & 1u, abort, status, 110, j, le)) {
+        if (!t2_waitw(&B->tfull, (uint32_t)ls & 1u, abort, status, 111, j, ls)) {
           ok = false;
           break;
         }
         tc::fence_after();
-        for (int c = 0; c < nch2; ++c, ++j) {
-          const int s = j % T2_NS;
-          const uint32_t u = (uint32_t)(j / T2_NS);
-          if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 111, j, le)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after();
-          const int w = min(T2_W, p16 - c * T2_W);
-          uint8_t *A = smem + s * S::STAGE;
-          for (int h = 0; h < w / 16; ++h) {
-            float v[16];
-            tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
-            if (row >= 0 && row < m) {
+        for (int i = 0; i < ns && ok; ++i) {
+          const bool writes = mine == i && orow < m;
+          for (int c = 0; c < nch2; ++c, ++j) {
+            const int s = j % T2_NS;
+            const uint32_t u = (uint32_t)(j / T2_NS);
+            if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 112, j, (int)u)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+            const int w = min(T2_W, p16 - c * T2_W);
+            uint8_t *A = smem + s * S::STAGE;
+            for (int h = 0; h < w / 16; ++h) {
+              float v[16];
+              tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
+              if (writes) {
 #pragma unroll
-              for (int g2 = 0; g2 < 2; ++g2) {
-                __align__(16) __nv_bfloat16 hb[8], lb[8];
+                for (int g2 = 0; g2 < 2; ++g2) {
+                  __align__(16) __nv_bfloat16 hb[8], lb[8];
 #pragma unroll
-                for (int i = 0; i < 8; ++i) tc::split_bf16(f * v[8 * g2 + i], hb[i], lb[i]);
-                uint8_t *dst = A + ((row >> 3) * (w >> 3) + 2 * h + g2) * 128 + (row & 7) * 16;
-                *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
-                *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
+                  for (int k = 0; k < 8; ++k) tc::split_bf16(f * v[8 * g2 + k], hb[k], lb[k]);
+                  uint8_t *dst = A + ((orow >> 3) * (w >> 3) + 2 * h + g2) * 128 + (orow & 7) * 16;
+                  *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
+                  *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
+                }
               }
             }
+            tc::fence_async_smem();
+            __syncwarp();
+            if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
           }
-          tc::fence_async_smem();
-          __syncwarp();
-          if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
         }
         if (!ok) break;
         tc::fence_before();
         __syncwarp();
         if (lane == 0) tc::mbar_arrive(&B->tempty);
+        ei += ns;
       }
       if (!ok) break;
       // ---- output block: D (TMEM) -> FP64 global, then release D
-      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status, 112, j, le)) {
+      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status, 113, j, ls)) {
         ok = false;
         break;
       }
@@ -535,10 +562,10 @@ __global__ void __launch_bounds__(T2_THREADS) chain_tc2_kernel(const TcEntry *__
       for (int c0 = 0; c0 < q16; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tD + lane_off + (uint32_t)c0, v);
-        if (row >= 0 && row < m) {
+        if (R >= 0 && R < m) {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            if (c0 + i < q) D[(int64_t)row * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
+            if (c0 + i < q) D[(int64_t)R * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
         }
       }
       tc::fence_before();
