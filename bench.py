@@ -52,6 +52,9 @@ FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, recipe table)
 # capture of the unchanged kernel at that workload and precision (else null)
 TRAFFIC_PER_LAUNCH = {
     ("c2", 0, 512, (32768.0, 50000.0, 33, 0, 0)): 1.034e9 + 0.147e9,
+    ("c2", 0, 512, (32768.0, 200000.0, 33, 0, 0)): 1.0293e9 + 0.1472e9,
+    ("c2", 0, 512, (131072.0, 50000.0, 33, 0, 0)): 1.8010e9 + 0.7325e9,
+    ("c2", 0, 512, (131072.0, 200000.0, 33, 0, 0)): 1.4767e9 + 0.4892e9,
 }
 
 
