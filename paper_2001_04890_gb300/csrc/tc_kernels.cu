@@ -168,27 +168,32 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 // ---------------------------------------------------------------------------
 // chain_tc2: D += sum_e f_e X_e Y_e Z_e per output block on the tensor cores
 // (split-BF16 three-pass products, FP32 accumulation in TMEM).  Persistent:
-// two CTAs per SM, with TMEM, mbarriers and the zeroed stage ring set up once
+// CTAS CTAs per SM, with TMEM, mbarriers and the zeroed stage ring set up once
 // per CTA; the producer takes the next output block from a global counter
 // (dynamic balance: a block's cost on the tensor cores is not its FLOP count)
 // and hands the indices to the other roles through a small ring (gfull /
 // gempty mbarriers; -1 ends the work).
 //
-// Work of one entry is a sequence of "jobs", one per K chunk:
-//   stage 1 (K = n):  T = X Y           A = X chunk, B = Y^T chunk, both bulk-copied
-//   stage 2 (K = p):  D += (f T) Z      A = f T chunk written by the converter
-//                                        warps from TMEM, B = Z^T chunk bulk-copied
-// Identity X / Z are exact identity tiles.  Jobs run through a ring of T2_NS
-// shared-memory stages (A half | B half, 128 rows x T2_W hi + lo each) with warp roles:
+// The tasks of an output block come in stacks: consecutive tasks that read the
+// same psi block Y (TcEntry::stack on the first).  The work of a stack is a
+// sequence of "jobs", one per K chunk:
+//   stage 1 (K = n):  [T_1; T_2; ..] = [X_1; X_2; ..] Y
+//                     A = the members' X chunks stacked along M, B = Y^T chunk
+//   stage 2 (K = p), for each member i:  D += (f_i T_i) Z_i
+//                     A = f_i T_i chunk written by the converter warps from
+//                     TMEM (rows of member i), B = Z_i^T chunk
+// Operand chunks are bulk-copied; identity X / Z are exact identity tiles.
+// Jobs run through a ring of T2_NS shared-memory stages (A half, MR rows, |
+// B half, TC rows; T2_W columns hi + lo) with warp roles:
 //   warps 0-3  converters: T (TMEM lanes = rows) -> f T split into bf16 hi/lo
 //              in stage 2 jobs; at the end of a block D (TMEM) -> FP64 output
 //   warp 4     producer: bulk copies of the operand chunks
 //   warp 5     MMA issuer: one thread issues tcgen05.mma and commits
 // mbarriers per stage: full (copies landed), cvf (converters wrote A),
-// empty (MMAs that read the stage finished); per entry: tfull (T complete),
+// empty (MMAs that read the stage finished); per stack: tfull (T complete),
 // tempty (converters finished reading T); per output block: dfull (D
 // complete), dempty (converters finished reading D).  Phases run on across
-// entries and blocks; every role derives the same job sequence.
+// stacks and blocks; every role derives the same job sequence.
 // Every wait is bounded: on time-out the CTA raises *status, all roles stop,
 // copies and MMAs in flight are waited for, and TMEM is released.
 // ---------------------------------------------------------------------------
