@@ -284,7 +284,10 @@ def batched_workload(args, wl):
     n = wl["instances"]
     out = {"workload": wl["name"], "instances": n}
     res = {}
-    for name, prec in (("fp32", 1), ("bf16x3", 2)):
+    pairs = (("fp32", 1), ("bf16x3", 2))
+    if args.precision != "fp64":  # one low precision only
+        pairs = tuple(pr for pr in pairs if pr[0] == args.precision)
+    for name, prec in pairs:
         ctxs = []
         t0 = time.perf_counter()
         for seed in range(n):
