@@ -375,9 +375,7 @@ struct DevChain {
       for (int i = g.first; i < g.first + g.count; ++i) {
         const ChainEntry &e = CL.flat[i];
         const bool xid = e.x == ~0ull, zid = e.z == ~0ull;
-        const double cn = (double)g.m * e.n * e.p + (double)g.m * e.p * g.q;
-        const double ct = (double)e.n * e.p * g.q + (double)g.m * e.n * g.q;
-        if (tune.orient && !tc_group && !xid && !zid && ct < cn) {
+        if (tune.orient && !tc_group && !xid && !zid && prefer_transposed(g.m, e.n, e.p, g.q)) {
           tr.push_back(i);
           continue;
         }
@@ -538,16 +536,18 @@ struct DevChain {
       std::vector<int> idx(g.count);
       std::iota(idx.begin(), idx.end(), g.first);
       std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return xs[a].y < xs[b].y; });
+      std::vector<uint64_t> keys(idx.size());
+      for (size_t k = 0; k < idx.size(); ++k) keys[k] = xs[idx[k]].y;
+      const std::vector<int> runs = stack_runs(keys, cap);
+      size_t run_i = 0;
       int remaining = 0;
       for (size_t k = 0; k < idx.size(); ++k) {
         const int i = idx[k];
         const ChainEntry &e = xs[i];
         TcEntry t{};
         if (remaining == 0) {  // first member of a stack: the run of tasks on this psi block
-          int run = 1;
-          while (run < cap && k + run < idx.size() && xs[idx[k + run]].y == e.y) ++run;
-          t.stack = run;
-          remaining = run;
+          t.stack = runs[run_i++];
+          remaining = t.stack;
         }
         --remaining;
         t.n = e.n;

@@ -899,4 +899,23 @@ Ref resolve(const OpRef &op, int side, const BlockLayout &b, TempSet &temps, boo
   return temps.make(side, b, op, zero);
 }
 
+bool prefer_transposed(int m, int n, int p, int q) {
+  const double cn = (double)m * n * p + (double)m * p * q;
+  const double ct = (double)n * p * q + (double)m * n * q;
+  return ct < cn;
+}
+
+std::vector<int> stack_runs(const std::vector<uint64_t> &sorted_keys, int cap) {
+  std::vector<int> runs;
+  if (cap < 1) cap = 1;
+  size_t k = 0;
+  while (k < sorted_keys.size()) {
+    int run = 1;
+    while (run < cap && k + run < sorted_keys.size() && sorted_keys[k + run] == sorted_keys[k]) ++run;
+    runs.push_back(run);
+    k += run;
+  }
+  return runs;
+}
+
 }  // namespace dmrg

@@ -251,4 +251,15 @@ struct ChainGroup {
   int tile0;
 };
 
+// Launch-shape decisions of the task lists (pure host logic).
+
+// Association of one task D += f X Y Z (X m x n, Y n x p, Z p x q): true when the
+// transposed product D^T += f Z^T Y^T X^T (n p q + m n q multiply-adds) is
+// strictly cheaper than (X Y) Z (m n p + m p q).
+bool prefer_transposed(int m, int n, int p, int q);
+
+// Stacks of a key list sorted so that equal keys are adjacent: the lengths of
+// the runs of equal keys, each run cut into pieces of at most cap, in order.
+std::vector<int> stack_runs(const std::vector<uint64_t> &sorted_keys, int cap);
+
 }  // namespace dmrg
