@@ -317,11 +317,14 @@ int dmrg_selftest_tcgen05(int N, int K, const float *A, const float *B, float *C
  * dmrg_debug_tasks -- host-only dump of the H.psi task list the planner builds
  * for the same arguments as dmrg_plan_hpsi_flops: per task 7 ints (output psi
  * block index, m, n, p, q, identity flags (1: left identity, 2: right
- * identity), element offset of the input psi block).  out may be NULL to query
- * *ntasks; DMRG_EINVAL if cap < *ntasks.  No GPU is used.
+ * identity), element offset of the input psi block), in build order
+ * (grouped = 0) or grouped by output block as the GPU task list runs it
+ * (grouped = 1).  out may be NULL to query *ntasks; DMRG_EINVAL if
+ * cap < *ntasks.  No GPU is used.
  */
 int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
-                     const int *sec_l, int nr, const int *sec_r, int *out, long long cap, long long *ntasks);
+                     const int *sec_l, int nr, const int *sec_r, int grouped, int *out, long long cap,
+                     long long *ntasks);
 
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */

@@ -75,7 +75,7 @@ def lib():
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_tasks": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
-                                       ip, C.c_longlong, llp]),
+                                       C.c_int, ip, C.c_longlong, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
     }
@@ -115,14 +115,15 @@ def _dump(fn, *args):
     return buf.value.decode()
 
 
-def debug_tasks(h, v, N, two_sz, k, sec_l, sec_r):
-    """Host-only H.psi task list: (ntasks, 7) int array (group, m, n, p, q, identity flags, input offset)."""
+def debug_tasks(h, v, N, two_sz, k, sec_l, sec_r, grouped=False):
+    """Host-only H.psi task list: (ntasks, 7) int array (group, m, n, p, q, identity flags, input offset),
+    in build order or grouped by output block (the GPU order)."""
     h, v = _f64(h), _f64(v)
     L = h.shape[0]
     tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
     tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
     n = C.c_longlong()
-    args = (L, N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr), _iptr(tr))
+    args = (L, N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr), _iptr(tr), int(grouped))
     _check(lib().dmrg_debug_tasks(*args, None, 0, C.byref(n)))
     out = np.zeros((n.value, 7), dtype=np.int32)
     _check(lib().dmrg_debug_tasks(*args, _iptr(out), n.value, C.byref(n)))

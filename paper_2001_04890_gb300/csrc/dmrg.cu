@@ -8,15 +8,18 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <functional>
 #include <map>
 #include <cstring>
+#include <exception>
 #include <memory>
 #include <mutex>
 #include <numeric>
 #include <stdexcept>
 #include <string>
+#include <thread>
 #include <vector>
 
 #include "../../include/dmrg_gb300.h"
@@ -140,6 +143,11 @@ struct Psi {
     if (a < 0 || d < 0 || a >= nl || d >= nr) return -1;
     return index[((a * 4 + b) * 4 + c) * nr + d];
   }
+  int find_block(uint64_t off) const {  // block index by element offset (-1 if none)
+    const auto it = std::lower_bound(blk.begin(), blk.end(), (int64_t)off,
+                                     [](const PsiBlock &b, int64_t o) { return b.off < o; });
+    return it != blk.end() && it->off == (int64_t)off ? (int)(it - blk.begin()) : -1;
+  }
 };
 
 static Psi psi_layout(const BlockLayout &l, const BlockLayout &r, int nu, int nd) {
@@ -243,26 +251,28 @@ struct ChainList {
   std::vector<ChainEntry> flat;
   int ntiles = 0;
   double flops = 0.0;
+  // Group the tasks by output block: a stable counting sort on the group key
+  // (keys index protos), groups in key order, tasks in build order within one.
   void finish(const std::vector<ChainGroup> &protos) {
-    std::stable_sort(ent.begin(), ent.end(),
-                     [](const std::pair<int, ChainEntry> &x, const std::pair<int, ChainEntry> &y) {
-                       return x.first < y.first;
-                     });
-    flat.clear();
+    const size_t ng = protos.size();
+    std::vector<int64_t> start(ng + 1, 0);
+    for (const auto &pe : ent) ++start[(size_t)pe.first + 1];
+    for (size_t k = 0; k < ng; ++k) start[k + 1] += start[k];
+    flat.assign(ent.size(), ChainEntry{});
+    std::vector<int64_t> pos(start.begin(), start.end() - 1);
+    for (const auto &pe : ent) flat[(size_t)pos[pe.first]++] = pe.second;
+    std::vector<std::pair<int, ChainEntry>>().swap(ent);  // the grouped copy is all that is used
     grp.clear();
     ntiles = 0;
-    size_t i = 0;
-    while (i < ent.size()) {
-      size_t j = i;
-      while (j < ent.size() && ent[j].first == ent[i].first) ++j;
-      ChainGroup g = protos[ent[i].first];
-      g.first = (int)flat.size();
-      g.count = (int)(j - i);
+    for (size_t k = 0; k < ng; ++k) {
+      const int64_t cnt = start[k + 1] - start[k];
+      if (cnt == 0) continue;
+      ChainGroup g = protos[k];
+      g.first = (int)start[k];
+      g.count = (int)cnt;
       g.tile0 = ntiles;
       ntiles += ((g.m + 31) / 32) * ((g.q + 31) / 32);
-      for (size_t t = i; t < j; ++t) flat.push_back(ent[t].second);
       grp.push_back(g);
-      i = j;
     }
   }
 };
@@ -488,12 +498,27 @@ struct DevChain {
     std::vector<TcGroup> tg;
     std::vector<TileSpec> ts;
     std::vector<PsiTileSpec> ps;
-    std::map<std::tuple<uint64_t, int, int, int, int>, uint64_t> opmap;
+    struct ViewKey {
+      uint64_t src;
+      int rs, cs, R, K;
+      bool operator==(const ViewKey &o) const {
+        return src == o.src && rs == o.rs && cs == o.cs && R == o.R && K == o.K;
+      }
+    };
+    struct ViewHash {
+      size_t operator()(const ViewKey &k) const {
+        uint64_t h = k.src * 0x9E3779B97F4A7C15ull;
+        h ^= ((uint64_t)(uint32_t)k.rs << 32 | (uint32_t)k.cs) + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+        h ^= ((uint64_t)(uint32_t)k.R << 32 | (uint32_t)k.K) + 0x8CB92BA72F3D8DD7ull + (h << 6) + (h >> 2);
+        return (size_t)h;
+      }
+    };
+    std::unordered_map<ViewKey, uint64_t, ViewHash> opmap;  // operator view -> tile offset
     std::unordered_map<uint64_t, uint64_t> psimap;
     uint64_t opbytes = 0, psibytes = 0;
     auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
     auto op_tile = [&](uint64_t src, int rs, int cs, int R, int K) -> uint64_t {
-      const auto key = std::make_tuple(src, rs, cs, R, K);
+      const ViewKey key{src, rs, cs, R, K};
       auto it = opmap.find(key);
       if (it != opmap.end()) return it->second;
       ts.push_back(TileSpec{src, opbytes, rs, cs, R, K});
@@ -797,11 +822,14 @@ static std::vector<RPiece> resolve_pieces(const Integrals &I, int k, const Block
 
 // Expand pieces over the psi blocks of Eq. wf_sec into the H.psi task list
 // (Sec. 2.2.1): one entry per (piece, s -> s'), plus the transposed entry of
-// Hermitian-conjugate pieces.  Also counts the algorithmic FLOPs.
-static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const Psi &Y,
-                        const BlockLayout &lb, ChainList &CL, double &flops) {
+// Hermitian-conjugate pieces.  Also counts the algorithmic FLOPs.  This part:
+// the pieces [r0, r1).
+static void expand_hpsi_range(const std::vector<RPiece> &rps, size_t r0, size_t r1, const Arenas &A,
+                              const Psi &Y, const BlockLayout &lb,
+                              std::vector<std::pair<int, ChainEntry>> &out, double &flops) {
   flops = 0.0;
-  for (auto &rp : rps) {
+  for (size_t ri = r0; ri < r1; ++ri) {
+    const RPiece &rp = rps[ri];
     const Piece &p = rp.p;
     const int psl = mat_parity(p.sl), psr = mat_parity(p.sr);
     for (size_t si = 0; si < Y.blk.size(); ++si) {
@@ -835,7 +863,7 @@ static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const P
       e.n = s.ma;
       e.p = s.md;
       e.f = f;
-      CL.ent.push_back({(int)so, e});
+      out.push_back({(int)so, e});
       flops += entry_flops(t.ma, s.ma, s.md, t.md, xid, zid);
       if (p.hc) {
         ChainEntry h{};
@@ -851,10 +879,49 @@ static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const P
         h.n = t.ma;
         h.p = t.md;
         h.f = f;
-        CL.ent.push_back({(int)si, h});
+        out.push_back({(int)si, h});
         flops += entry_flops(s.ma, t.ma, t.md, s.md, xid, zid);
       }
     }
+  }
+}
+
+// The whole expansion, in piece order: a fixed cut of the pieces into ranges
+// (independent of the host's core count) expanded by worker threads, then
+// concatenated in range order, so the task list is the same as a sequential
+// expansion and the FLOP sum (exact integers) is identical.
+static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const Psi &Y,
+                        const BlockLayout &lb, ChainList &CL, double &flops) {
+  const size_t nr = std::min<size_t>(rps.size(), 64);
+  std::vector<std::vector<std::pair<int, ChainEntry>>> part(nr);
+  std::vector<double> fl(nr, 0.0);
+  std::atomic<size_t> next{0};
+  std::mutex err_mu;
+  std::exception_ptr err;  // the first failure of a worker (e.g. host allocation), rethrown here
+  auto worker = [&]() {
+    try {
+      for (size_t c = next.fetch_add(1); c < nr; c = next.fetch_add(1))
+        expand_hpsi_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb, part[c], fl[c]);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(nr);
+    }
+  };
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned t = 1; t < hw && t < nr; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+  size_t total = CL.ent.size();
+  for (const auto &v : part) total += v.size();
+  CL.ent.reserve(total);
+  flops = 0.0;
+  for (size_t c = 0; c < nr; ++c) {
+    CL.ent.insert(CL.ent.end(), part[c].begin(), part[c].end());
+    std::vector<std::pair<int, ChainEntry>>().swap(part[c]);
+    flops += fl[c];
   }
 }
 
@@ -2166,8 +2233,8 @@ extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, c
 }
 
 extern "C" int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
-                                const int *sec_l, int nr, const int *sec_r, int *out, long long cap,
-                                long long *ntasks) {
+                                const int *sec_l, int nr, const int *sec_r, int grouped, int *out,
+                                long long cap, long long *ntasks) {
   API_BEGIN
   if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r || !ntasks)
     throw Fail{DMRG_EINVAL, "dmrg_debug_tasks: bad arguments"};
@@ -2197,11 +2264,19 @@ extern "C" int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const
   double f = 0.0;
   expand_hpsi(rps, A, Y, lb, CL, f);
   *ntasks = (long long)CL.ent.size();
+  std::vector<std::pair<int, ChainEntry>> tasks;
+  if (grouped) {  // the order the GPU task list uses: grouped by output block
+    CL.finish(psi_protos(Y));
+    for (const auto &g : CL.grp)
+      for (int i = g.first; i < g.first + g.count; ++i) tasks.push_back({Y.find_block(g.d), CL.flat[i]});
+  } else {
+    tasks.swap(CL.ent);
+  }
   if (out) {
     if (cap < *ntasks) throw Fail{DMRG_EINVAL, "dmrg_debug_tasks: buffer too small"};
-    for (size_t i = 0; i < CL.ent.size(); ++i) {
-      const int g = CL.ent[i].first;
-      const ChainEntry &e = CL.ent[i].second;
+    for (size_t i = 0; i < tasks.size(); ++i) {
+      const int g = tasks[i].first;
+      const ChainEntry &e = tasks[i].second;
       int *o = out + 7 * i;
       o[0] = g;
       o[1] = Y.blk[g].ma;  // m

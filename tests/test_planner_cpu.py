@@ -163,3 +163,20 @@ def test_task_dump_reproduces_the_flop_count():
     # an identity side is square, and every task maps an input block to an output block of the layout
     assert np.all(n[xid] == m[xid]) and np.all(p[zid] == q[zid])
     assert np.all(T[:, 1:5] >= 1)
+
+
+def test_grouped_task_list_is_a_stable_sort_by_output_block():
+    """The GPU task list is the build-order list grouped by output psi block, tasks
+    of one block in build order (the ordered sigma accumulation relies on it)."""
+    import numpy as np
+    from paper_2001_04890_gb300 import binding, workloads
+    L, N, k = 10, 10, 4
+    h, v = workloads.integrals(L, seed=3)
+    sec = [(a, b, 1 + (3 * a + b) % 5) for a in range(0, 5) for b in range(0, 5)]
+    sec_r = [(a, b, 1 + (a + 2 * b) % 4) for a in range(0, 5) for b in range(0, 5)]
+    T0 = binding.debug_tasks(h, v, N, 0, k, sec, sec_r)
+    T1 = binding.debug_tasks(h, v, N, 0, k, sec, sec_r, grouped=True)
+    assert T1.shape == T0.shape
+    order = np.argsort(T0[:, 0], kind="stable")
+    assert np.array_equal(T1, T0[order])
+    assert np.all(np.diff(T1[:, 0]) >= 0)
