@@ -642,7 +642,7 @@ def main():
                 "overlap_vs_fp64": float(abs(np.dot(m["psi_mid"], r["psi_mid"]))),
                 "energy": m["e_mid"],
             }
-    if rank == 0 and not args.no_cpu_baseline:
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline at N = 1 only
         try:
             from oracle import baseline
             line["cpu_baseline"] = baseline.cpu_baseline(wl, _flops_fn(wl))
