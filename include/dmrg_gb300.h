@@ -50,10 +50,12 @@ enum {
 
 /* FP64: every operation in FP64.  FP32: FP64 block operators, renormalization and
  * density matrices; FP32 copies of the operators for the Davidson matvecs (FP32
- * CUDA-core arithmetic).  BF16X3: as FP32, but H.psi output blocks of 33..128
- * rows/columns run on the tcgen05 tensor cores as three-pass split-BF16
- * products with FP32 accumulation in tensor memory.  In both mixed modes
- * Davidson finishes with FP64 matvecs (iterative refinement). */
+ * CUDA-core arithmetic).  BF16X3: as FP32, but H.psi output blocks with both
+ * sides <= 128 and one side >= tc_min (33 by default; see dmrg_set_tune) run on
+ * the tcgen05 tensor cores as three-pass split-BF16 products with FP32
+ * accumulation in tensor memory.  In both mixed modes Davidson finishes with a
+ * defect-corrected refinement that applies H in FP64 to the current vector
+ * (see dmrg_davidson), so energies are FP64 quality. */
 enum { DMRG_PREC_FP64 = 0, DMRG_PREC_FP32 = 1, DMRG_PREC_BF16X3 = 2 };
 
 typedef struct dmrg_ctx dmrg_ctx; /* opaque, library-owned */
@@ -160,9 +162,13 @@ int dmrg_get_psi(dmrg_ctx *ctx, double *psi, int device_ptr);
 /*
  * dmrg_davidson -- lowest eigenpair of Eq. h_mat at the current position by
  * Davidson's method (Sec. 2.2.1); vectors, orthogonalisation, the subspace
- * eigenproblem and residuals are FP64 on the GPU.  In DMRG_PREC_FP32 the
- * matvecs use FP32 operator copies until the residual reaches ~1e-6 |E|, then
- * continue with FP64 matvecs to tol (iterative refinement).  Diagonal preconditioner
+ * eigenproblem and residuals are FP64 on the GPU.  In the mixed precisions the
+ * matvecs use the low-precision operators until the residual reaches 1e-6 |E|
+ * (FP32) or 1e-4 |E| (BF16X3); then each refinement step applies H in FP64 to
+ * the current vector (exact residual and Rayleigh quotient) and expands the
+ * subspace with low-precision matvecs only, to tol; if the exact residual stops
+ * improving, plain FP64 Davidson finishes.  *iters counts all H.psi
+ * applications (dmrg_stats separates the low-precision ones).  Diagonal preconditioner
  * (E - diag H)^-1 with |denominator| >= 1e-8, subspace <= 24, thick restart
  * with 2 vectors, converged when ||H psi - E psi|| <= tol for normalized psi.
  * Starts from the current psi when one is set, else from a fixed pseudo-random
