@@ -206,6 +206,15 @@ int dmrg_renormalize(dmrg_ctx *ctx, int direction, const int *kept, const double
 int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
 
 /*
+ * dmrg_set_bond_dims -- asymmetric bond dimensions: later RDM truncations of
+ * dmrg_renormalize keep at most m_forward states in new left blocks
+ * (direction +1) and m_backward in new right blocks (direction -1), e.g. the
+ * larger M on the enlarged half and the smaller on the environment of the
+ * paper's largest case.  dmrg_init sets both to M.  DMRG_EINVAL if either < 1.
+ */
+int dmrg_set_bond_dims(dmrg_ctx *ctx, int m_forward, int m_backward);
+
+/*
  * dmrg_set_precision -- change the working precision of the Davidson matvecs
  * (DMRG_PREC_*) of an existing context; blocks and the wave function are kept,
  * the H.psi task lists and low-precision operator copies are rebuilt on next

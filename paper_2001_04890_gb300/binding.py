@@ -59,6 +59,7 @@ def lib():
         "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
         "dmrg_release_block": (C.c_int, [vp, C.c_int, C.c_int]),
         "dmrg_set_precision": (C.c_int, [vp, C.c_int]),
+        "dmrg_set_bond_dims": (C.c_int, [vp, C.c_int, C.c_int]),
         "dmrg_stats": (C.c_int, [vp, C.c_int, dp, llp, dp, llp, llp, llp, dp]),
         "dmrg_plan_hpsi_flops": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip,
                                            C.c_int, ip, dp, llp]),
@@ -310,6 +311,10 @@ class DMRG:
         par = np.zeros(5)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
+
+    def set_bond_dims(self, m_forward, m_backward):
+        """Kept states of new left blocks (forward) and new right blocks (backward) in RDM truncations."""
+        _check(lib().dmrg_set_bond_dims(self.ctx, int(m_forward), int(m_backward)))
 
     def set_precision(self, precision):
         """Switch the working precision of the Davidson matvecs (PREC_FP64 / PREC_FP32 / PREC_BF16X3)."""

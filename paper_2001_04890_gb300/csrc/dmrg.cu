@@ -755,6 +755,7 @@ struct HPlan {
 
 struct dmrg_ctx {
   int L = 0, N = 0, nu = 0, nd = 0, M = 0, prec = 0;
+  int M_bwd = 0;  // kept states of right blocks (backward renormalizations); M for left blocks
   cudaStream_t stream = nullptr;
   dmrg::Integrals I;
   std::vector<std::unique_ptr<dmrg::DevBlock>> left, right;  // by size
@@ -1327,7 +1328,8 @@ static void rdm_truncate(dmrg_ctx *c, int direction, const Enlarged &enl, std::v
   kept.assign(ne, 0);
   double kw = 0.0;
   std::vector<std::vector<int>> cols(ne);
-  for (int i = 0; i < (int)cand.size() && i < c->M; ++i) {
+  const int mkeep = direction > 0 ? c->M : c->M_bwd;  // kept states of the new left / right block
+  for (int i = 0; i < (int)cand.size() && i < mkeep; ++i) {
     if (cand[i].v <= 1e-13) break;
     kept[cand[i].e]++;
     kw += cand[i].v;
@@ -1896,6 +1898,7 @@ extern "C" int dmrg_init(int L, int N, int two_sz, const double *h, const double
   c->nu = nu;
   c->nd = nd;
   c->M = M;
+  c->M_bwd = M;
   c->prec = precision;
   c->stream = (cudaStream_t)cuda_stream;
   c->I.L = L;
@@ -1945,6 +1948,14 @@ extern "C" int dmrg_free(dmrg_ctx *c) {
   for (auto e : c->ev) cudaEventDestroy(e);
   delete c;
   return DMRG_OK;
+}
+
+extern "C" int dmrg_set_bond_dims(dmrg_ctx *c, int m_forward, int m_backward) {
+  API_BEGIN
+  if (!c || m_forward < 1 || m_backward < 1) throw Fail{DMRG_EINVAL, "dmrg_set_bond_dims: NULL or M < 1"};
+  c->M = m_forward;
+  c->M_bwd = m_backward;
+  API_END
 }
 
 extern "C" int dmrg_set_precision(dmrg_ctx *c, int precision) {

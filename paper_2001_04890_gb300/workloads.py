@@ -125,7 +125,7 @@ def sector_dims_profile(k: int, n_up_tot: int, n_dn_tot: int, L: int, M: int,
 
 
 def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: int = 0,
-                     release: bool = False):
+                     release: bool = False, M_right: int | None = None):
     """Grow the left blocks 0..k-1 and right blocks k+2..L-1 of a context with seeded random O.
 
     Each renormalization keeps, per enlarged sector, the number of states given
@@ -133,8 +133,11 @@ def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: in
     Returns the list of (direction, kept, O_flat) applied, in order, so the same
     bases can be replayed elsewhere.  Leaves ctx at position k.  With release,
     each block is freed once the next one is built (ctx.release_block), so only
-    the middle-bond blocks stay resident.
+    the middle-bond blocks stay resident.  M_right (default M) is the bond
+    dimension of the right blocks (asymmetric M).
     """
+    if M_right is None:
+        M_right = M
     rng = np.random.default_rng(seed)
     applied = []
     ctx.set_position(0, 1)
@@ -153,7 +156,7 @@ def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: in
         n_sites = L - s
         lay = ctx.enlarged_layout(-1)
         caps = {(int(a), int(b)): int(d) for a, b, d in lay}
-        prof = sector_dims_profile(n_sites, n_up, n_dn, L, M, caps)
+        prof = sector_dims_profile(n_sites, n_up, n_dn, L, M_right, caps)
         kept = [prof.get((int(a), int(b)), 0) for a, b, _ in lay]
         O = np.concatenate([orthonormal_columns(int(d), m, rng).ravel() for (_, _, d), m in zip(lay, kept)])
         ctx.renormalize(-1, O, kept)

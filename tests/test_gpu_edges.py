@@ -120,3 +120,33 @@ def test_set_precision_switches_the_matvec_path():
     with pytest.raises(binding.DMRGError):
         ctx.set_precision(9)
     ctx.close()
+
+
+def test_asymmetric_bond_dimensions():
+    """RDM truncation keeps at most M_forward states in a new left block and
+    M_backward in a new right block (dmrg_set_bond_dims); energies variational."""
+    L, N = 8, 8
+    h, v = workloads.integrals(L, seed=15)
+    e_fci = fock.fci_ground(h, v, 4, 4)[0]
+    ctx = binding.DMRG(h, v, N, 0, 48)
+    ctx.set_bond_dims(48, 20)
+    E = ctx.sweep(2, tol=1e-10)
+    assert np.all(E >= e_fci - 1e-10)
+    ctx.set_position(3, 1)
+    assert ctx.block_sectors(0)[:, 2].sum() <= 48
+    assert ctx.block_sectors(1)[:, 2].sum() <= 20
+    ctx.close()
+    # a grown middle bond with a smaller right bond dimension, then one truncation each way
+    L, N, M, MR, k = 10, 10, 120, 60, 4
+    h, v = workloads.integrals(L, seed=16)
+    ctx = binding.DMRG(h, v, N, 0, M)
+    workloads.grow_middle_bond(ctx, L, 5, 5, M, k, seed=2, M_right=MR)
+    assert ctx.block_sectors(0)[:, 2].sum() == M and ctx.block_sectors(1)[:, 2].sum() == MR
+    ctx.set_bond_dims(9, 7)
+    ctx.davidson(tol=1e-8, max_iter=300, allow_noconv=True)
+    dw, kept = ctx.renormalize(-1)  # new right block: 7 states
+    assert kept.sum() == 7 and dw > 0
+    ctx.davidson(tol=1e-8, max_iter=300, allow_noconv=True)
+    dw, kept = ctx.renormalize(+1)  # new left block: 9 states
+    assert kept.sum() == 9 and dw > 0
+    ctx.close()
