@@ -293,10 +293,11 @@ struct ChainTune {
                        // 0 = two narrower CTAs per SM (4 / 8 warps each)
 };
 
-// A task list on the device.  Output blocks of at most 32 x 32 go to the
-// flattened-lane warp kernel, blocks of 33..128 to the tensor-core kernel when
-// enabled (and all their entries have n, p <= 128), the rest to the 32 x 32
-// tile kernel.  With split_tasks, every output block's entry list is cut into
+// A task list on the device.  When the tensor cores are enabled, output blocks
+// with both sides <= 128, one side >= tc_min and every entry's n, p <= 128 go
+// to the tensor-core kernel; of the rest, blocks of at most 32 x 32 go to the
+// flattened-lane warp kernel and larger ones to the 32 x 32 tile kernel.  With
+// split_tasks, every output block's entry list is cut into
 // chunks of about equal work; each chunk accumulates into its own slot of a
 // scratch buffer and a reduction adds the slots in chunk order, so the result
 // does not depend on scheduling (bitwise repeatable) while the grid has
