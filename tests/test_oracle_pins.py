@@ -254,3 +254,41 @@ def test_renormalized_product_equals_product_on_complete_basis():
         mid = (ka[0] + 1, ka[1])  # mode 2 is site 1 up: B raises n_up first
         prod = rA[(kb, mid)] @ rB[(mid, ka)]
         assert np.allclose(prod, blk, atol=1e-13)
+
+
+def test_truncation_rule_on_a_known_spectrum():
+    """Reading of "keep the M largest eigenvalues": global order, ties by (sector
+    order, in-sector order), eigenvalues <= 1e-13 never kept, discarded weight =
+    trace - kept.  Checked on density matrices with known eigenpairs."""
+    import numpy as np
+    from oracle import blocks as ob
+    rng = np.random.default_rng(5)
+
+    # diagonal density matrices: eigenvalues exact, so the ties below are exact ties
+    spectra = {(0, 0): [0.30, 0.05, 1e-14], (0, 1): [0.20, 0.05], (1, 0): [0.30, 0.10, 0.0]}
+    rho = {E: np.diag(ev) for E, ev in spectra.items()}
+    # M = 4: 0.30 (sector 0), 0.30 (sector 2: later sector), 0.20, 0.10 -> the two 0.05 are cut
+    O, kept, dw, _ = ob.truncate(rho, 4)
+    assert kept == [1, 1, 2]
+    trace = sum(sum(ev) for ev in spectra.values())
+    assert abs(dw - (trace - 0.90)) < 1e-12
+    # M = 5: the tie at 0.05 goes to the earlier sector
+    O, kept, dw, _ = ob.truncate(rho, 5)
+    assert kept == [2, 1, 2]
+    # M large: 1e-14 and 0.0 are never kept
+    O, kept, dw, _ = ob.truncate(rho, 100)
+    assert kept == [2, 2, 2]
+    assert abs(dw - 1e-14) < 1e-12
+    # rotated density matrices (distinct eigenvalues): the kept columns span the
+    # eigenvectors of the kept eigenvalues
+    spectra = {(0, 0): [0.40, 0.06, 0.01], (1, 1): [0.35, 0.12, 0.06]}
+    rho, vecs = {}, {}
+    for E, ev in spectra.items():
+        Q, _ = np.linalg.qr(rng.standard_normal((3, 3)))
+        rho[E], vecs[E] = (Q * np.asarray(ev)) @ Q.T, Q
+    O, kept, dw, _ = ob.truncate(rho, 3)
+    assert kept == [1, 2]
+    for (E, ev), k in zip(spectra.items(), kept):
+        order = np.argsort(ev)[::-1][:k]
+        assert np.allclose(O[E] @ O[E].T, vecs[E][:, order] @ vecs[E][:, order].T, atol=1e-10)
+    assert abs(dw - (0.06 + 0.01 + 0.06)) < 1e-12
