@@ -70,3 +70,44 @@ def test_operator_oracle_sweeps_reach_fci():
     E = dm.sweep(4)
     assert np.all(E >= e_fci - 1e-10)
     assert abs(E[2 * 2 * (L - 2):].min() - e_fci) < 1e-10
+
+
+def test_baseline_builder_replays_on_explicit_bases():
+    """The CPU baseline's middle-bond builder (oracle/baseline.py, driven by
+    workloads.grow_middle_bond) against the explicit Fock-space oracle: the same
+    recorded O sequence replayed on explicit bases gives the same H.psi."""
+    from oracle import baseline
+    L, N, M, k = 6, 6, 20, 2
+    h, v = workloads.integrals(L, seed=0)
+    b = baseline.OracleBuilder(h, v)
+    applied = workloads.grow_middle_bond(b, L, 3, 3, M, k, seed=4)
+    lo, ro = b._blocks()
+    it = iter(applied)
+
+    def split(O, dims, kept):
+        out, pos = [], 0
+        for d, m in zip(dims, kept):
+            out.append(np.asarray(O[pos:pos + d * m]).reshape(d, m))
+            pos += d * m
+        assert pos == len(O)
+        return out
+
+    lb, rb = ob.empty_block(), ob.empty_block()
+    for s in range(k):
+        d, kept, O = next(it)
+        assert d == +1
+        lay = ob.enlarged_left(lb)
+        blocks = split(O, [ob.enlarged_dims(lay)[E] for E in lay], kept)
+        lb = ob.grow_left(lb, s, {E: blk for E, blk in zip(lay, blocks)})
+    for s in range(L - 1, k + 1, -1):
+        d, kept, O = next(it)
+        assert d == -1
+        lay = ob.enlarged_right(rb)
+        blocks = split(O, [ob.enlarged_dims(lay)[E] for E in lay], kept)
+        rb = ob.grow_right(rb, s, {E: blk for E, blk in zip(lay, blocks)})
+    P = ob.Projected(h, v, lb, rb, 3, 3)
+    hp = od.HPsi(b.I, k, lo, ro, 3, 3)
+    assert hp.dim == P.dim
+    psi = workloads.gaussian(P.dim, seed=9)
+    ref = P.apply(psi)
+    assert np.max(np.abs(hp.apply(psi) - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
