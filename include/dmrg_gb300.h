@@ -197,6 +197,20 @@ int dmrg_renormalize(dmrg_ctx *ctx, int direction, const int *kept, const double
                      double *discarded_weight);
 
 /*
+ * dmrg_truncation_stats -- record of the density-matrix truncations
+ * (dmrg_renormalize with O NULL, and the steps of dmrg_sweep) since dmrg_init.
+ * The gap of one truncation is the smallest kept eigenvalue minus the largest
+ * eigenvalue above 1e-13 that was cut (+infinity when no such eigenvalue was
+ * cut).  A gap below 1e-10 means a near-degenerate cluster straddles the cut:
+ * the kept space, and the energies after it, then depend on rounding (the
+ * paper's rule names no order for equal eigenvalues).  Outputs (host, each
+ * may be NULL): the last gap, the smallest gap, the number of truncations and
+ * the number with gap < 1e-10.  Errors: DMRG_EINVAL (NULL context).
+ */
+int dmrg_truncation_stats(dmrg_ctx *ctx, double *last_gap, double *min_gap, long long *truncations,
+                          long long *straddled);
+
+/*
  * dmrg_sweep -- nsweeps two-site sweeps (Sec. 2.1, Fig. dmrg_blocks): forward
  * over positions 0..L-3 (Davidson then dmrg_renormalize(+1)), backward over
  * L-2..1 (Davidson then dmrg_renormalize(-1)).  Starts from position 0 in the
@@ -347,6 +361,21 @@ int dmrg_debug_pieces(int L, const double *h, const double *v, int k, int l_empt
                       int compress, char *buf, long long buflen, long long *needed);
 int dmrg_debug_newops(int L, const double *h, const double *v, int k, int side, int old_empty,
                       char *buf, long long buflen, long long *needed);
+
+/*
+ * dmrg_debug_truncation -- host-only run of the truncation rule that
+ * dmrg_renormalize applies to the density-matrix spectrum (Sec. 2.1): the
+ * mkeep largest eigenvalues over all sectors, ties by (sector, in-sector rank
+ * from the top), eigenvalues <= 1e-13 never kept.  In: nsectors, dims (one
+ * int per sector), ev_ascending (sum of dims doubles: each sector's spectrum in
+ * ascending order, sectors concatenated).  Out: kept (one int per sector),
+ * cols (may be NULL; sum of kept ints: per sector, the kept columns as indices
+ * into the ascending order, largest eigenvalue first), out3 = {trace, kept
+ * weight, cut gap as in dmrg_truncation_stats}.  DMRG_EINVAL on bad arguments.
+ * No GPU is used.
+ */
+int dmrg_debug_truncation(int nsectors, const int *dims, const double *ev_ascending, int mkeep,
+                          int *kept, int *cols, double *out3);
 
 #ifdef __cplusplus
 }

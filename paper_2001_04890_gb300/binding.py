@@ -72,6 +72,8 @@ def lib():
         "dmrg_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
         "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
         "dmrg_get_tune": (C.c_int, [vp, dp]),
+        "dmrg_truncation_stats": (C.c_int, [vp, dp, dp, llp, llp]),
+        "dmrg_debug_truncation": (C.c_int, [C.c_int, ip, dp, C.c_int, ip, ip, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
@@ -140,6 +142,26 @@ def plan_hpsi_flops(h, v, N, two_sz, k, sec_l, sec_r):
     _check(lib().dmrg_plan_hpsi_flops(h.shape[0], N, two_sz, _dptr(h), _dptr(v), k, len(sl), _iptr(sl),
                                       len(sr), _iptr(sr), C.byref(f), C.byref(t)))
     return f.value, t.value
+
+
+def debug_truncation(spectra, mkeep):
+    """Host-only truncation rule of the library on per-sector spectra (each in ascending
+    order): (kept per sector, kept columns per sector as ascending-order indices with the
+    largest eigenvalue first, trace, kept weight, cut gap)."""
+    dims = np.array([len(s) for s in spectra], dtype=np.int32)
+    ev = np.ascontiguousarray(np.concatenate([np.asarray(s, dtype=np.float64) for s in spectra])
+                              if len(spectra) else np.zeros(0))
+    kept = np.zeros(max(len(dims), 1), dtype=np.int32)
+    cols = np.zeros(max(int(dims.sum()), 1), dtype=np.int32)
+    out3 = np.zeros(3)
+    _check(lib().dmrg_debug_truncation(len(dims), _iptr(dims), _dptr(ev), int(mkeep), _iptr(kept), _iptr(cols),
+                                       _dptr(out3)))
+    kept = kept[:len(dims)]
+    per, pos = [], 0
+    for n in kept:
+        per.append(cols[pos:pos + n].copy())
+        pos += n
+    return kept, per, out3[0], out3[1], out3[2]
 
 
 def selftest_tcgen05(A, B):
@@ -311,6 +333,14 @@ class DMRG:
         par = np.zeros(5)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
+
+    def truncation_stats(self):
+        """Record of the density-matrix truncations since init: gap at the cut of the
+        last one and the smallest, their count, and how many had a gap below 1e-10."""
+        last, low = C.c_double(), C.c_double()
+        n, straddled = C.c_longlong(), C.c_longlong()
+        _check(lib().dmrg_truncation_stats(self.ctx, C.byref(last), C.byref(low), C.byref(n), C.byref(straddled)))
+        return dict(last_gap=last.value, min_gap=low.value, truncations=n.value, straddled=straddled.value)
 
     def set_bond_dims(self, m_forward, m_backward):
         """Kept states of new left blocks (forward) and new right blocks (backward) in RDM truncations."""

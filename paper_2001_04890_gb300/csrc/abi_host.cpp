@@ -76,3 +76,43 @@ extern "C" int dmrg_debug_newops(int L, const double *h, const double *v, int k,
     return DMRG_EINVAL;
   }
 }
+
+extern "C" int dmrg_debug_truncation(int nsectors, const int *dims, const double *ev_ascending, int mkeep,
+                                     int *kept, int *cols, double *out3) {
+  try {
+    if (nsectors < 0 || mkeep < 0 || (nsectors > 0 && (!dims || !kept)) || !out3) {
+      dmrg::set_error("dmrg_debug_truncation: bad arguments");
+      return DMRG_EINVAL;
+    }
+    std::vector<std::vector<double>> ev(nsectors);
+    long long pos = 0;
+    for (int e = 0; e < nsectors; ++e) {
+      if (dims[e] < 0) {
+        dmrg::set_error("dmrg_debug_truncation: negative sector dimension");
+        return DMRG_EINVAL;
+      }
+      if (dims[e] > 0 && !ev_ascending) {
+        dmrg::set_error("dmrg_debug_truncation: NULL eigenvalues");
+        return DMRG_EINVAL;
+      }
+      ev[e].assign(ev_ascending + pos, ev_ascending + pos + dims[e]);
+      pos += dims[e];
+    }
+    const dmrg::KeptSet ks = dmrg::choose_kept(ev, mkeep, 1e-13);
+    long long c = 0;
+    for (int e = 0; e < nsectors; ++e) {
+      kept[e] = ks.kept[e];
+      for (int j : ks.cols[e]) {
+        if (cols) cols[c] = j;
+        ++c;
+      }
+    }
+    out3[0] = ks.trace;
+    out3[1] = ks.kept_weight;
+    out3[2] = ks.cut_gap;
+    return DMRG_OK;
+  } catch (const std::exception &e) {
+    dmrg::set_error(e.what());
+    return DMRG_EINVAL;
+  }
+}

@@ -11,6 +11,7 @@
 #include <atomic>
 #include <cmath>
 #include <functional>
+#include <limits>
 #include <map>
 #include <cstring>
 #include <exception>
@@ -782,6 +783,11 @@ struct dmrg_ctx {
   long long dav_iters_lowp = 0;
   dmrg::DBuf<int> dstatus;  // set by bounded device waits that ran out
   dmrg::ChainTune tune;     // launch shape of H.psi task lists (dmrg_autotune)
+  // density-matrix truncations: gap at the cut of the last one, smallest gap,
+  // count, and how many had a near-degenerate cluster across the cut
+  double cut_gap = std::numeric_limits<double>::infinity();
+  double min_cut_gap = std::numeric_limits<double>::infinity();
+  long long truncations = 0, straddled = 0;
 };
 
 namespace dmrg {
@@ -1309,40 +1315,22 @@ static void rdm_truncate(dmrg_ctx *c, int direction, const Enlarged &enl, std::v
   CK(cudaMemcpyAsync(evh.data(), ev.p, etot * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
   CK(cudaStreamSynchronize(c->stream));
   // global top-M selection: descending eigenvalue, ties by (sector, in-sector order)
-  struct Cand {
-    double v;
-    int e, j;
-  };
-  std::vector<Cand> cand;
-  double trace = 0.0;
-  for (int e = 0; e < ne; ++e)
-    for (int j = 0; j < enl[e].dim; ++j) {
-      const double x = evh[eoff[e] + (enl[e].dim - 1 - j)];  // j-th largest in the sector
-      cand.push_back({x, e, j});
-      trace += x;
-    }
-  std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) {
-    if (x.v != y.v) return x.v > y.v;
-    if (x.e != y.e) return x.e < y.e;
-    return x.j < y.j;
-  });
-  kept.assign(ne, 0);
-  double kw = 0.0;
-  std::vector<std::vector<int>> cols(ne);
+  std::vector<std::vector<double>> evs(ne);
+  for (int e = 0; e < ne; ++e) evs[e].assign(evh.begin() + eoff[e], evh.begin() + eoff[e] + enl[e].dim);
   const int mkeep = direction > 0 ? c->M : c->M_bwd;  // kept states of the new left / right block
-  for (int i = 0; i < (int)cand.size() && i < mkeep; ++i) {
-    if (cand[i].v <= 1e-13) break;
-    kept[cand[i].e]++;
-    kw += cand[i].v;
-    cols[cand[i].e].push_back(enl[cand[i].e].dim - 1 - cand[i].j);  // column in ascending order
-  }
-  dw = trace - kw;
+  KeptSet ks = choose_kept(evs, mkeep, 1e-13);
+  kept = ks.kept;
+  std::vector<std::vector<int>> &cols = ks.cols;
+  dw = ks.trace - ks.kept_weight;
+  c->cut_gap = ks.cut_gap;
+  c->min_cut_gap = std::min(c->min_cut_gap, ks.cut_gap);
+  c->truncations++;
+  if (ks.cut_gap < 1e-10) c->straddled++;
   Ooff.assign(ne, 0);
   int64_t otot = 0;
   for (int e = 0; e < ne; ++e) {
     Ooff[e] = otot;
     otot += (int64_t)enl[e].dim * kept[e];
-    std::sort(cols[e].begin(), cols[e].end(), std::greater<int>());  // descending eigenvalue
   }
   Odev.alloc((size_t)std::max<int64_t>(otot, 1));
   std::vector<int> allcols;
@@ -2668,6 +2656,17 @@ extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk
   c->tune.tc_min = tc_min;
   c->tune.by_work = by_work;
   c->plan.valid = false;
+  API_END
+}
+
+extern "C" int dmrg_truncation_stats(dmrg_ctx *c, double *last_gap, double *min_gap,
+                                     long long *truncations, long long *straddled) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "NULL context"};
+  if (last_gap) *last_gap = c->cut_gap;
+  if (min_gap) *min_gap = c->min_cut_gap;
+  if (truncations) *truncations = c->truncations;
+  if (straddled) *straddled = c->straddled;
   API_END
 }
 

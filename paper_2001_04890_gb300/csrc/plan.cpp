@@ -6,6 +6,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <functional>
+#include <limits>
 #include <sstream>
 #include <stdexcept>
 
@@ -916,6 +918,43 @@ std::vector<int> stack_runs(const std::vector<uint64_t> &sorted_keys, int cap) {
     k += run;
   }
   return runs;
+}
+
+KeptSet choose_kept(const std::vector<std::vector<double>> &ev_ascending, int mkeep, double drop) {
+  struct Cand {
+    double v;
+    int e, j;
+  };
+  const int ne = (int)ev_ascending.size();
+  KeptSet r;
+  std::vector<Cand> cand;
+  for (int e = 0; e < ne; ++e) {
+    const int n = (int)ev_ascending[e].size();
+    for (int j = 0; j < n; ++j) {
+      const double x = ev_ascending[e][n - 1 - j];  // j-th largest in the sector
+      cand.push_back({x, e, j});
+      r.trace += x;
+    }
+  }
+  std::stable_sort(cand.begin(), cand.end(), [](const Cand &x, const Cand &y) {
+    if (x.v != y.v) return x.v > y.v;
+    if (x.e != y.e) return x.e < y.e;
+    return x.j < y.j;
+  });
+  r.kept.assign(ne, 0);
+  r.cols.assign(ne, {});
+  int nk = 0;
+  while (nk < (int)cand.size() && nk < mkeep && cand[nk].v > drop) {
+    const Cand &c = cand[nk];
+    r.kept[c.e]++;
+    r.kept_weight += c.v;
+    r.cols[c.e].push_back((int)ev_ascending[c.e].size() - 1 - c.j);
+    ++nk;
+  }
+  r.cut_gap = std::numeric_limits<double>::infinity();
+  if (nk > 0 && nk < (int)cand.size() && cand[nk].v > drop) r.cut_gap = cand[nk - 1].v - cand[nk].v;
+  for (auto &c : r.cols) std::sort(c.begin(), c.end(), std::greater<int>());
+  return r;
 }
 
 }  // namespace dmrg

@@ -262,4 +262,20 @@ bool prefer_transposed(int m, int n, int p, int q);
 // the runs of equal keys, each run cut into pieces of at most cap, in order.
 std::vector<int> stack_runs(const std::vector<uint64_t> &sorted_keys, int cap);
 
+// Truncation of the reduced density matrix (Sec. 2.1): keep the mkeep
+// eigenvectors with the largest eigenvalues over all sectors.  Input: per sector,
+// the eigenvalues in ascending order (as a symmetric eigensolver returns them).
+// Order: descending eigenvalue, ties by (sector, in-sector rank from the top);
+// eigenvalues <= drop are never kept.  cols[e] lists the kept columns of sector e
+// (indices into the ascending order) by descending eigenvalue.  cut_gap is the
+// smallest kept eigenvalue minus the largest eigenvalue above drop that was not
+// kept (+infinity when nothing above drop was cut, or nothing was kept): a gap
+// below 1e-10 means a near-degenerate cluster straddles the cut.
+struct KeptSet {
+  std::vector<int> kept;
+  std::vector<std::vector<int>> cols;
+  double trace = 0.0, kept_weight = 0.0, cut_gap = 0.0;
+};
+KeptSet choose_kept(const std::vector<std::vector<double>> &ev_ascending, int mkeep, double drop);
+
 }  // namespace dmrg
