@@ -124,6 +124,33 @@ def sector_dims_profile(k: int, n_up_tot: int, n_dn_tot: int, L: int, M: int,
     return {key: int(m) for key, m in zip(keys, alloc) if m > 0}
 
 
+def middle_bond_sectors(L: int, n_up: int, n_dn: int, M: int, k: int, M_right: int | None = None):
+    """Sector tables {(nu, nd): dim} of the two middle-bond blocks grow_middle_bond builds.
+
+    Dimensions only (no operators): each enlarged block offers, per sector, the
+    sum of the old block's sector dimensions over the four site states, and the
+    kept dimensions follow sector_dims_profile.  Returns (left, right): the
+    left block of sites 0..k-1 and the right block of sites k+2..L-1.
+    """
+    if M_right is None:
+        M_right = M
+    site = ((0, 0), (1, 0), (0, 1), (1, 1))
+
+    def grow(blk, n_sites, m):
+        caps = {}
+        for (a, b), d in blk.items():
+            for su, sd in site:
+                caps[(a + su, b + sd)] = caps.get((a + su, b + sd), 0) + d
+        return sector_dims_profile(n_sites, n_up, n_dn, L, m, caps)
+
+    left, right = {(0, 0): 1}, {(0, 0): 1}
+    for s in range(k):
+        left = grow(left, s + 1, M)
+    for s in range(L - 1, k + 1, -1):
+        right = grow(right, L - s, M_right)
+    return left, right
+
+
 def grow_middle_bond(ctx, L: int, n_up: int, n_dn: int, M: int, k: int, seed: int = 0,
                      release: bool = False, M_right: int | None = None):
     """Grow the left blocks 0..k-1 and right blocks k+2..L-1 of a context with seeded random O.

@@ -111,3 +111,17 @@ def test_baseline_builder_replays_on_explicit_bases():
     psi = workloads.gaussian(P.dim, seed=9)
     ref = P.apply(psi)
     assert np.max(np.abs(hp.apply(psi) - ref)) < 1e-12 * max(1.0, np.max(np.abs(ref)))
+
+
+@pytest.mark.parametrize("L,nu,nd,M,k", [(8, 4, 4, 30, 3), (9, 5, 3, 24, 3), (10, 4, 5, 40, 2)])
+def test_middle_bond_sector_tables_match_the_grown_blocks(L, nu, nd, M, k):
+    """The dimension-only sector tables (used to describe the large workloads) equal
+    those of blocks actually grown by renormalization with the seeded O."""
+    from oracle import baseline
+    h, v = workloads.integrals(L, seed=0)
+    b = baseline.OracleBuilder(h, v)
+    workloads.grow_middle_bond(b, L, nu, nd, M, k, seed=2)
+    lb, rb = b._blocks()
+    left, right = workloads.middle_bond_sectors(L, nu, nd, M, k)
+    assert {tuple(s): d for s, d in zip(lb.sectors, lb.dims) if d > 0} == left
+    assert {tuple(s): d for s, d in zip(rb.sectors, rb.dims) if d > 0} == right
