@@ -355,6 +355,28 @@ int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const double *v,
                      const int *sec_l, int nr, const int *sec_r, int grouped, int *out, long long cap,
                      long long *ntasks);
 
+/*
+ * dmrg_debug_exec -- host-only dump of the execution plan the GPU runs for the
+ * H.psi task list of dmrg_debug_tasks (the grouped products of Eq. dgemm,
+ * Sec. 2.2.1): each output block's tasks in their cheaper association, cut
+ * into chunks of about equal work that accumulate into scratch slots, then an
+ * ordered reduction of the slots into sigma.  tensor_cores: 1 routes blocks to
+ * the tensor-core kernel as DMRG_PREC_BF16X3 does; tune: NULL (defaults) or 4
+ * doubles target_chunks, min_chunk, tc_min, by_work as in dmrg_set_tune.
+ * counts (8): execution entries, chunks of the 32 x 32 tile kernel, of the
+ * flattened-lane kernel, of the tensor-core kernel, reduction groups, tiles,
+ * scratch elements, reduced elements.  Optional arrays (NULL to skip; sizes
+ * from counts): xs_out 8 per entry (psi offset of Y, n, p, Y row stride, Y
+ * column stride, identity flags, X offset, Z offset; -1 for identity),
+ * grp_out 8 per chunk (kernel 0/1/2, slot offset, slot row stride, slot column
+ * stride, m, q, first entry, entry count), red_out 8 per output block (first
+ * reduced element, first slot offset, sigma offset, row stride, column stride,
+ * m, q, chunk count).  Operator offsets are relative to each arena.
+ */
+int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                    const int *sec_l, int nr, const int *sec_r, int tensor_cores, const double *tune,
+                    long long *counts, long long *xs_out, long long *grp_out, long long *red_out);
+
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */
 int dmrg_debug_pieces(int L, const double *h, const double *v, int k, int l_empty, int r_empty,

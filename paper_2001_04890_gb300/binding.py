@@ -79,6 +79,8 @@ def lib():
                                         C.c_char_p, C.c_longlong, llp]),
         "dmrg_debug_tasks": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
                                        C.c_int, ip, C.c_longlong, llp]),
+        "dmrg_debug_exec": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
+                                      C.c_int, dp, llp, llp, llp, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
     }
@@ -131,6 +133,28 @@ def debug_tasks(h, v, N, two_sz, k, sec_l, sec_r, grouped=False):
     out = np.zeros((n.value, 7), dtype=np.int32)
     _check(lib().dmrg_debug_tasks(*args, _iptr(out), n.value, C.byref(n)))
     return out
+
+
+def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
+    """Host-only execution plan of the H.psi task list: dict of counts and the arrays
+    xs (n, 8), chunks (n, 8) and reduce (n, 8) described in the header."""
+    h, v = _f64(h), _f64(v)
+    L = h.shape[0]
+    tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
+    tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
+    tune_arr = None if tune is None else np.ascontiguousarray(tune, dtype=np.float64)
+    tp = None if tune_arr is None else _dptr(tune_arr)
+    cnt = np.zeros(8, dtype=np.int64)
+    llp = C.POINTER(C.c_longlong)
+    args = (L, N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr), _iptr(tr), int(tensor_cores), tp)
+    _check(lib().dmrg_debug_exec(*args, cnt.ctypes.data_as(llp), None, None, None))
+    xs = np.zeros((cnt[0], 8), dtype=np.int64)
+    ch = np.zeros((cnt[1] + cnt[2] + cnt[3], 8), dtype=np.int64)
+    red = np.zeros((cnt[4], 8), dtype=np.int64)
+    _check(lib().dmrg_debug_exec(*args, cnt.ctypes.data_as(llp), xs.ctypes.data_as(llp), ch.ctypes.data_as(llp),
+                                 red.ctypes.data_as(llp)))
+    keys = ("entries", "tile_chunks", "flat_chunks", "tc_chunks", "reduce_groups", "tiles", "scratch", "reduced")
+    return dict(zip(keys, (int(x) for x in cnt))), xs, ch, red
 
 
 def plan_hpsi_flops(h, v, N, two_sz, k, sec_l, sec_r):

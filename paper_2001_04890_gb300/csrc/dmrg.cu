@@ -246,31 +246,82 @@ static inline int npart(const Sector &s) { return s.nu + s.nd; }
 static inline int nsite(int b) { return SITE_NU[b] + SITE_ND[b]; }
 
 // task list grouped by output block
+// Run fn(i) for i in [0, n) on up to 16 host threads (work handed out one index
+// at a time); the first exception of any worker is rethrown here.
+template <class F>
+static void parallel_for(size_t n, F fn) {
+  std::atomic<size_t> next{0};
+  std::mutex err_mu;
+  std::exception_ptr err;
+  auto worker = [&]() {
+    try {
+      for (size_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
+    }
+  };
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned t = 1; t < hw && t < n; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+}
+
 struct ChainList {
-  std::vector<std::pair<int, ChainEntry>> ent;  // (group key, entry)
-  std::vector<ChainGroup> grp;                  // one per key, filled by finish()
+  using Keyed = std::vector<std::pair<int, ChainEntry>>;  // (group key, entry)
+  Keyed ent;                    // entries in build order
+  std::vector<Keyed> parts;     // further entries, built after ent, in part order
+  std::vector<ChainGroup> grp;  // one per key, filled by finish()
   std::vector<ChainEntry> flat;
   int ntiles = 0;
   double flops = 0.0;
+  size_t size() const {
+    size_t n = ent.size();
+    for (const auto &p : parts) n += p.size();
+    return n;
+  }
   // Group the tasks by output block: a stable counting sort on the group key
-  // (keys index protos), groups in key order, tasks in build order within one.
+  // (keys index protos), groups in key order, tasks in build order within one
+  // (ent, then the parts in order).  Each part is counted and scattered by its
+  // own thread: per (part, key) write offsets keep the order of a serial sort.
   void finish(const std::vector<ChainGroup> &protos) {
     const size_t ng = protos.size();
-    std::vector<int64_t> start(ng + 1, 0);
-    for (const auto &pe : ent) ++start[(size_t)pe.first + 1];
-    for (size_t k = 0; k < ng; ++k) start[k + 1] += start[k];
-    flat.assign(ent.size(), ChainEntry{});
-    std::vector<int64_t> pos(start.begin(), start.end() - 1);
-    for (const auto &pe : ent) flat[(size_t)pos[pe.first]++] = pe.second;
-    std::vector<std::pair<int, ChainEntry>>().swap(ent);  // the grouped copy is all that is used
+    std::vector<const Keyed *> src{&ent};
+    for (const auto &p : parts) src.push_back(&p);
+    const size_t ns = src.size();
+    std::vector<int64_t> cnt(ns * ng, 0);
+    parallel_for(ns, [&](size_t s) {
+      int64_t *c = cnt.data() + s * ng;
+      for (const auto &pe : *src[s]) ++c[(size_t)pe.first];
+    });
+    std::vector<int64_t> start(ng + 1, 0), off(ns * ng);
+    int64_t run = 0;
+    for (size_t k = 0; k < ng; ++k) {
+      start[k] = run;
+      for (size_t s = 0; s < ns; ++s) {
+        off[s * ng + k] = run;
+        run += cnt[s * ng + k];
+      }
+    }
+    start[ng] = run;
+    flat.assign((size_t)run, ChainEntry{});
+    parallel_for(ns, [&](size_t s) {
+      int64_t *o = off.data() + s * ng;
+      for (const auto &pe : *src[s]) flat[(size_t)o[(size_t)pe.first]++] = pe.second;
+    });
+    Keyed().swap(ent);  // the grouped copy is all that is used
+    std::vector<Keyed>().swap(parts);
     grp.clear();
     ntiles = 0;
     for (size_t k = 0; k < ng; ++k) {
-      const int64_t cnt = start[k + 1] - start[k];
-      if (cnt == 0) continue;
+      const int64_t c = start[k + 1] - start[k];
+      if (c == 0) continue;
       ChainGroup g = protos[k];
       g.first = (int)start[k];
-      g.count = (int)cnt;
+      g.count = (int)c;
       g.tile0 = ntiles;
       ntiles += ((g.m + 31) / 32) * ((g.q + 31) / 32);
       grp.push_back(g);
@@ -293,6 +344,174 @@ struct ChainTune {
   int flat_wide = 1;   // flat kernel CTAs: 1 = one wide CTA per SM (6 FP64 / 12 FP32 warps),
                        // 0 = two narrower CTAs per SM (4 / 8 warps each)
 };
+
+// Host half of a task list's upload: the execution list (entries in their
+// cheaper association, cut into equal-work chunks when split_tasks), the launch
+// groups of the three chunk kernels (32 x 32 tiles, flattened lanes, tensor
+// cores) and the ordered reduction of the chunk slots.
+struct ExecPlan {
+  std::vector<ChainEntry> xs;
+  std::vector<double> w;
+  std::vector<ChainGroup> vb, vf, vt;
+  std::vector<ReduceGroup> vr;
+  int tiles = 0;
+  int64_t soff = 0, e0 = 0;
+};
+
+static void plan_exec(const ChainList &CL, bool tensor_cores, bool split_tasks, const ChainTune &tune,
+                      ExecPlan &X) {
+  std::vector<ChainGroup> &vb = X.vb, &vf = X.vf, &vt = X.vt;
+  std::vector<ReduceGroup> &vr = X.vr;
+  const bool split = split_tasks;
+  int &tiles = X.tiles;
+  int64_t &soff = X.soff, &e0 = X.e0;
+  tiles = 0;
+  soff = e0 = 0;
+  // Execution list: with split chunks, the entries of an output block whose
+  // other association is cheaper (n p q + m n q < m n p + m p q) run as the
+  // transposed product D^T += f Z^T Y^T X^T (same operands, swapped strides)
+  // in chunks of their own; their slot is written through transposed strides,
+  // so the ordered reduction is unchanged.
+  std::vector<ChainEntry> &xs = X.xs;
+  std::vector<double> &w = X.w;
+  xs.reserve(CL.flat.size());
+  w.reserve(CL.flat.size());
+  auto tc_entry_ok = [&](const ChainEntry &e, int m, int q) {
+    // Y must be a whole row-major psi block; identity sides are square
+    return !(e.n < 1 || e.p < 1 || e.n > 128 || e.p > 128 || e.y == ~0ull || e.ycs != 1 || e.yrs != e.p ||
+             (e.x == ~0ull && e.n != m) || (e.z == ~0ull && e.p != q));
+  };
+  auto tc_shape_ok = [&](int m, int q) {
+    return tensor_cores && m <= 128 && q <= 128 && (m >= tune.tc_min || q >= tune.tc_min);
+  };
+  double total = 0.0;
+  for (const auto &g : CL.grp)
+    for (int i = g.first; i < g.first + g.count; ++i) {
+      const ChainEntry &e = CL.flat[i];
+      total += 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
+    }
+  const double chunk_work = std::max(total / tune.target_chunks, tune.min_chunk);
+  auto place = [&](ChainGroup t) {
+    bool tc_ok = t.count > 0 && tc_shape_ok(t.m, t.q);
+    for (int i = t.first; tc_ok && i < t.first + t.count; ++i) tc_ok = tc_entry_ok(xs[i], t.m, t.q);
+    if (tc_ok) {
+      vt.push_back(t);
+    } else if (t.m <= 32 && t.q <= 32) {
+      vf.push_back(t);
+    } else {
+      t.tile0 = tiles;
+      tiles += ((t.m + 31) / 32) * ((t.q + 31) / 32);
+      vb.push_back(t);
+    }
+  };
+  for (const auto &g : CL.grp) {
+    if (!split) {
+      ChainGroup t = g;
+      t.first = (int)xs.size();
+      for (int i = g.first; i < g.first + g.count; ++i) {
+        const ChainEntry &e = CL.flat[i];
+        xs.push_back(e);
+        w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull));
+      }
+      place(t);
+      continue;
+    }
+    // orientation of each entry (tensor-core blocks keep the stored one)
+    bool tc_group = tc_shape_ok(g.m, g.q);
+    for (int i = g.first; tc_group && i < g.first + g.count; ++i) tc_group = tc_entry_ok(CL.flat[i], g.m, g.q);
+    const int n0 = (int)xs.size();
+    std::vector<int> tr;
+    for (int i = g.first; i < g.first + g.count; ++i) {
+      const ChainEntry &e = CL.flat[i];
+      const bool xid = e.x == ~0ull, zid = e.z == ~0ull;
+      if (tune.orient && !tc_group && !xid && !zid && prefer_transposed(g.m, e.n, e.p, g.q)) {
+        tr.push_back(i);
+        continue;
+      }
+      xs.push_back(e);
+      w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, xid, zid));
+    }
+    const int n1 = (int)xs.size();
+    for (int i : tr) {
+      const ChainEntry &e = CL.flat[i];
+      ChainEntry t{};
+      t.x = e.z;  // X' = Z^T
+      t.xrs = e.zcs;
+      t.xcs = e.zrs;
+      t.y = e.y;  // Y' = Y^T
+      t.yrs = e.ycs;
+      t.ycs = e.yrs;
+      t.z = e.x;  // Z' = X^T
+      t.zrs = e.xcs;
+      t.zcs = e.xrs;
+      t.n = e.p;
+      t.p = e.n;
+      t.f = e.f;
+      xs.push_back(t);
+      w.push_back(1.0 + entry_flops(g.q, t.n, t.p, g.m, false, false));
+    }
+    const int n2 = (int)xs.size();
+    const int64_t mq = (int64_t)g.m * g.q;
+    ReduceGroup r{};
+    r.e0 = e0;
+    r.soff = soff;
+    r.d = g.d;
+    r.drs = g.drs;
+    r.dcs = g.dcs;
+    r.m = g.m;
+    r.q = g.q;
+    int nsplit = 0;
+    for (int part = 0; part < 2; ++part) {
+      const int lo = part == 0 ? n0 : n1, hi = part == 0 ? n1 : n2;
+      int i = lo;
+      while (i < hi) {
+        double acc = 0.0;
+        int j = i;
+        while (j < hi && (j == i || acc + w[j] <= chunk_work)) acc += w[j++];
+        ChainGroup t = g;
+        t.first = i;
+        t.count = j - i;
+        t.d = (uint64_t)(soff + (int64_t)nsplit * mq);  // slot: m x q row-major
+        if (part == 0) {
+          t.drs = g.q;
+          t.dcs = 1;
+        } else {  // transposed chunk: q x m output written into the m x q slot
+          t.m = g.q;
+          t.q = g.m;
+          t.drs = 1;
+          t.dcs = g.q;
+        }
+        place(t);
+        ++nsplit;
+        i = j;
+      }
+    }
+    r.nsplit = nsplit;
+    vr.push_back(r);
+    soff += (int64_t)nsplit * mq;
+    e0 += mq;
+  }
+  // optionally heaviest groups first: CTAs are dispatched in grid order, so the
+  // light groups fill the last wave; the natural order keeps the chunks of one
+  // output block (which read the same operators) adjacent.  Results do not
+  // depend on the order.
+  auto by_work = [&](std::vector<ChainGroup> &v) {
+    std::vector<std::pair<double, int>> key(v.size());
+    for (size_t i = 0; i < v.size(); ++i) {
+      double wsum = 0.0;
+      for (int e = v[i].first; e < v[i].first + v[i].count; ++e) wsum += w[e];
+      key[i] = {-wsum, (int)i};
+    }
+    std::stable_sort(key.begin(), key.end());
+    std::vector<ChainGroup> out(v.size());
+    for (size_t i = 0; i < v.size(); ++i) out[i] = v[key[i].second];
+    v.swap(out);
+  };
+  if (tune.by_work) {
+    by_work(vf);
+    by_work(vt);
+  }
+}
 
 // A task list on the device.  When the tensor cores are enabled, output blocks
 // with both sides <= 128, one side >= tc_min and every entry's n, p <= 128 go
@@ -324,156 +543,15 @@ struct DevChain {
 
   void upload(const ChainList &CL, cudaStream_t s, bool tensor_cores = false, bool split_tasks = false,
               const ChainTune &tune = ChainTune()) {
-    std::vector<ChainGroup> vb, vf, vt;
-    std::vector<ReduceGroup> vr;
+    ExecPlan X;
+    plan_exec(CL, tensor_cores, split_tasks, tune, X);
     split = split_tasks;
     flat_wide = tune.flat_wide;
-    int tiles = 0;
-    int64_t soff = 0, e0 = 0;
-    // Execution list: with split chunks, the entries of an output block whose
-    // other association is cheaper (n p q + m n q < m n p + m p q) run as the
-    // transposed product D^T += f Z^T Y^T X^T (same operands, swapped strides)
-    // in chunks of their own; their slot is written through transposed strides,
-    // so the ordered reduction is unchanged.
-    std::vector<ChainEntry> xs;
-    std::vector<double> w;
-    xs.reserve(CL.flat.size());
-    w.reserve(CL.flat.size());
-    auto tc_entry_ok = [&](const ChainEntry &e, int m, int q) {
-      // Y must be a whole row-major psi block; identity sides are square
-      return !(e.n < 1 || e.p < 1 || e.n > 128 || e.p > 128 || e.y == ~0ull || e.ycs != 1 || e.yrs != e.p ||
-               (e.x == ~0ull && e.n != m) || (e.z == ~0ull && e.p != q));
-    };
-    auto tc_shape_ok = [&](int m, int q) {
-      return tensor_cores && m <= 128 && q <= 128 && (m >= tune.tc_min || q >= tune.tc_min);
-    };
-    double total = 0.0;
-    for (const auto &g : CL.grp)
-      for (int i = g.first; i < g.first + g.count; ++i) {
-        const ChainEntry &e = CL.flat[i];
-        total += 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
-      }
-    const double chunk_work = std::max(total / tune.target_chunks, tune.min_chunk);
-    auto place = [&](ChainGroup t) {
-      bool tc_ok = t.count > 0 && tc_shape_ok(t.m, t.q);
-      for (int i = t.first; tc_ok && i < t.first + t.count; ++i) tc_ok = tc_entry_ok(xs[i], t.m, t.q);
-      if (tc_ok) {
-        vt.push_back(t);
-      } else if (t.m <= 32 && t.q <= 32) {
-        vf.push_back(t);
-      } else {
-        t.tile0 = tiles;
-        tiles += ((t.m + 31) / 32) * ((t.q + 31) / 32);
-        vb.push_back(t);
-      }
-    };
-    for (const auto &g : CL.grp) {
-      if (!split) {
-        ChainGroup t = g;
-        t.first = (int)xs.size();
-        for (int i = g.first; i < g.first + g.count; ++i) {
-          const ChainEntry &e = CL.flat[i];
-          xs.push_back(e);
-          w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull));
-        }
-        place(t);
-        continue;
-      }
-      // orientation of each entry (tensor-core blocks keep the stored one)
-      bool tc_group = tc_shape_ok(g.m, g.q);
-      for (int i = g.first; tc_group && i < g.first + g.count; ++i) tc_group = tc_entry_ok(CL.flat[i], g.m, g.q);
-      const int n0 = (int)xs.size();
-      std::vector<int> tr;
-      for (int i = g.first; i < g.first + g.count; ++i) {
-        const ChainEntry &e = CL.flat[i];
-        const bool xid = e.x == ~0ull, zid = e.z == ~0ull;
-        if (tune.orient && !tc_group && !xid && !zid && prefer_transposed(g.m, e.n, e.p, g.q)) {
-          tr.push_back(i);
-          continue;
-        }
-        xs.push_back(e);
-        w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, xid, zid));
-      }
-      const int n1 = (int)xs.size();
-      for (int i : tr) {
-        const ChainEntry &e = CL.flat[i];
-        ChainEntry t{};
-        t.x = e.z;  // X' = Z^T
-        t.xrs = e.zcs;
-        t.xcs = e.zrs;
-        t.y = e.y;  // Y' = Y^T
-        t.yrs = e.ycs;
-        t.ycs = e.yrs;
-        t.z = e.x;  // Z' = X^T
-        t.zrs = e.xcs;
-        t.zcs = e.xrs;
-        t.n = e.p;
-        t.p = e.n;
-        t.f = e.f;
-        xs.push_back(t);
-        w.push_back(1.0 + entry_flops(g.q, t.n, t.p, g.m, false, false));
-      }
-      const int n2 = (int)xs.size();
-      const int64_t mq = (int64_t)g.m * g.q;
-      ReduceGroup r{};
-      r.e0 = e0;
-      r.soff = soff;
-      r.d = g.d;
-      r.drs = g.drs;
-      r.dcs = g.dcs;
-      r.m = g.m;
-      r.q = g.q;
-      int nsplit = 0;
-      for (int part = 0; part < 2; ++part) {
-        const int lo = part == 0 ? n0 : n1, hi = part == 0 ? n1 : n2;
-        int i = lo;
-        while (i < hi) {
-          double acc = 0.0;
-          int j = i;
-          while (j < hi && (j == i || acc + w[j] <= chunk_work)) acc += w[j++];
-          ChainGroup t = g;
-          t.first = i;
-          t.count = j - i;
-          t.d = (uint64_t)(soff + (int64_t)nsplit * mq);  // slot: m x q row-major
-          if (part == 0) {
-            t.drs = g.q;
-            t.dcs = 1;
-          } else {  // transposed chunk: q x m output written into the m x q slot
-            t.m = g.q;
-            t.q = g.m;
-            t.drs = 1;
-            t.dcs = g.q;
-          }
-          place(t);
-          ++nsplit;
-          i = j;
-        }
-      }
-      r.nsplit = nsplit;
-      vr.push_back(r);
-      soff += (int64_t)nsplit * mq;
-      e0 += mq;
-    }
-    // optionally heaviest groups first: CTAs are dispatched in grid order, so the
-    // light groups fill the last wave; the natural order keeps the chunks of one
-    // output block (which read the same operators) adjacent.  Results do not
-    // depend on the order.
-    auto by_work = [&](std::vector<ChainGroup> &v) {
-      std::vector<std::pair<double, int>> key(v.size());
-      for (size_t i = 0; i < v.size(); ++i) {
-        double wsum = 0.0;
-        for (int e = v[i].first; e < v[i].first + v[i].count; ++e) wsum += w[e];
-        key[i] = {-wsum, (int)i};
-      }
-      std::stable_sort(key.begin(), key.end());
-      std::vector<ChainGroup> out(v.size());
-      for (size_t i = 0; i < v.size(); ++i) out[i] = v[key[i].second];
-      v.swap(out);
-    };
-    if (tune.by_work) {
-      by_work(vf);
-      by_work(vt);
-    }
+    const std::vector<ChainEntry> &xs = X.xs;
+    const std::vector<ChainGroup> &vb = X.vb, &vf = X.vf, &vt = X.vt;
+    const std::vector<ReduceGroup> &vr = X.vr;
+    const int tiles = X.tiles;
+    const int64_t soff = X.soff, e0 = X.e0;
     ent.upload(CL.flat, s);  // the task list as built (diagonal, batching)
     xent.upload(xs, s);      // the execution list of the chunk kernels
     nent = (int64_t)CL.flat.size();
@@ -901,34 +979,14 @@ static void expand_hpsi_range(const std::vector<RPiece> &rps, size_t r0, size_t 
 static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const Psi &Y,
                         const BlockLayout &lb, ChainList &CL, double &flops) {
   const size_t nr = std::min<size_t>(rps.size(), 64);
-  std::vector<std::vector<std::pair<int, ChainEntry>>> part(nr);
+  std::vector<ChainList::Keyed> part(nr);
   std::vector<double> fl(nr, 0.0);
-  std::atomic<size_t> next{0};
-  std::mutex err_mu;
-  std::exception_ptr err;  // the first failure of a worker (e.g. host allocation), rethrown here
-  auto worker = [&]() {
-    try {
-      for (size_t c = next.fetch_add(1); c < nr; c = next.fetch_add(1))
-        expand_hpsi_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb, part[c], fl[c]);
-    } catch (...) {
-      std::lock_guard<std::mutex> lk(err_mu);
-      if (!err) err = std::current_exception();
-      next.store(nr);
-    }
-  };
-  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  std::vector<std::thread> pool;
-  for (unsigned t = 1; t < hw && t < nr; ++t) pool.emplace_back(worker);
-  worker();
-  for (auto &th : pool) th.join();
-  if (err) std::rethrow_exception(err);
-  size_t total = CL.ent.size();
-  for (const auto &v : part) total += v.size();
-  CL.ent.reserve(total);
+  parallel_for(nr, [&](size_t c) {
+    expand_hpsi_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb, part[c], fl[c]);
+  });
   flops = 0.0;
   for (size_t c = 0; c < nr; ++c) {
-    CL.ent.insert(CL.ent.end(), part[c].begin(), part[c].end());
-    std::vector<std::pair<int, ChainEntry>>().swap(part[c]);
+    CL.parts.push_back(std::move(part[c]));  // grouped by finish() without a serial concatenation
     flops += fl[c];
   }
 }
@@ -2228,7 +2286,7 @@ extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, c
   double f = 0.0;
   expand_hpsi(rps, A, Y, lb, CL, f);
   if (flops) *flops = f;
-  if (tasks) *tasks = (long long)CL.ent.size();
+  if (tasks) *tasks = (long long)CL.size();
   API_END
 }
 
@@ -2263,14 +2321,15 @@ extern "C" int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const
   ChainList CL;
   double f = 0.0;
   expand_hpsi(rps, A, Y, lb, CL, f);
-  *ntasks = (long long)CL.ent.size();
-  std::vector<std::pair<int, ChainEntry>> tasks;
+  *ntasks = (long long)CL.size();
+  ChainList::Keyed tasks;
   if (grouped) {  // the order the GPU task list uses: grouped by output block
     CL.finish(psi_protos(Y));
     for (const auto &g : CL.grp)
       for (int i = g.first; i < g.first + g.count; ++i) tasks.push_back({Y.find_block(g.d), CL.flat[i]});
   } else {
     tasks.swap(CL.ent);
+    for (const auto &p : CL.parts) tasks.insert(tasks.end(), p.begin(), p.end());
   }
   if (out) {
     if (cap < *ntasks) throw Fail{DMRG_EINVAL, "dmrg_debug_tasks: buffer too small"};
@@ -2287,6 +2346,103 @@ extern "C" int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const
       o[6] = (int)e.y;     // input block offset in psi
     }
   }
+  API_END
+}
+
+extern "C" int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                               const int *sec_l, int nr, const int *sec_r, int tensor_cores,
+                               const double *tune, long long *counts, long long *xs_out, long long *grp_out,
+                               long long *red_out) {
+  API_BEGIN
+  if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r || !counts)
+    throw Fail{DMRG_EINVAL, "dmrg_debug_exec: bad arguments"};
+  if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
+  ChainTune T;
+  if (tune) {
+    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1))
+      throw Fail{DMRG_EINVAL, "dmrg_debug_exec: bad launch-shape parameters"};
+    T.target_chunks = tune[0];
+    T.min_chunk = tune[1];
+    T.tc_min = (int)tune[2];
+    T.by_work = (int)tune[3];
+  }
+  Integrals I;
+  I.L = L;
+  I.h.assign(h, h + (size_t)L * L);
+  I.v.assign(v, v + (size_t)L * L * L * L);
+  auto sectors = [](int n, const int *t) {
+    std::vector<Sector> out;
+    for (int i = 0; i < n; ++i) out.push_back({t[3 * i], t[3 * i + 1], t[3 * i + 2]});
+    return out;
+  };
+  std::vector<int> ls, rs;
+  for (int s = 0; s < k; ++s) ls.push_back(s);
+  for (int s = k + 2; s < L; ++s) rs.push_back(s);
+  BlockLayout lb, rb;
+  build_layout(lb, 0, L, ls, sectors(nl, sec_l));
+  build_layout(rb, 1, L, rs, sectors(nr, sec_r));
+  Psi Y = psi_layout(lb, rb, (N + two_sz) / 2, (N - two_sz) / 2);
+  TempSet temps;
+  auto rps = resolve_pieces(I, k, lb, rb, temps);
+  const BlockLayout *lay[2] = {&lb, &rb};
+  temps.layout(lay);
+  Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 8};
+  ChainList CL;
+  double f = 0.0;
+  expand_hpsi(rps, A, Y, lb, CL, f);
+  CL.finish(psi_protos(Y));
+  ExecPlan X;
+  plan_exec(CL, tensor_cores != 0, true, T, X);
+  counts[0] = (long long)X.xs.size();
+  counts[1] = (long long)X.vb.size();
+  counts[2] = (long long)X.vf.size();
+  counts[3] = (long long)X.vt.size();
+  counts[4] = (long long)X.vr.size();
+  counts[5] = X.tiles;
+  counts[6] = X.soff;
+  counts[7] = X.e0;
+  if (xs_out)
+    for (size_t i = 0; i < X.xs.size(); ++i) {
+      const ChainEntry &e = X.xs[i];
+      long long *o = xs_out + 8 * i;
+      o[0] = (long long)e.y;
+      o[1] = e.n;
+      o[2] = e.p;
+      o[3] = e.yrs;
+      o[4] = e.ycs;
+      o[5] = (e.x == ~0ull ? 1 : 0) | (e.z == ~0ull ? 2 : 0);
+      o[6] = (long long)e.x;  // -1: identity
+      o[7] = (long long)e.z;
+    }
+  if (grp_out) {
+    size_t j = 0;
+    const std::vector<ChainGroup> *kinds[3] = {&X.vb, &X.vf, &X.vt};
+    for (int kd = 0; kd < 3; ++kd)
+      for (const ChainGroup &g : *kinds[kd]) {
+        long long *o = grp_out + 8 * j++;
+        o[0] = kd;
+        o[1] = (long long)g.d;
+        o[2] = g.drs;
+        o[3] = g.dcs;
+        o[4] = g.m;
+        o[5] = g.q;
+        o[6] = g.first;
+        o[7] = g.count;
+      }
+  }
+  if (red_out)
+    for (size_t i = 0; i < X.vr.size(); ++i) {
+      const ReduceGroup &r = X.vr[i];
+      long long *o = red_out + 8 * i;
+      o[0] = r.e0;
+      o[1] = r.soff;
+      o[2] = (long long)r.d;
+      o[3] = r.drs;
+      o[4] = r.dcs;
+      o[5] = r.m;
+      o[6] = r.q;
+      o[7] = r.nsplit;
+    }
   API_END
 }
 
