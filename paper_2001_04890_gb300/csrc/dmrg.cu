@@ -16,6 +16,7 @@
 #include <cstring>
 #include <exception>
 #include <memory>
+#include <utility>
 #include <mutex>
 #include <numeric>
 #include <stdexcept>
@@ -52,6 +53,28 @@ struct Fail {
 
 // ---------------------------------------------------------------- device buffers
 
+// Allocator whose resize() leaves trivially constructible elements
+// uninitialized: large host task lists are written once, by several threads,
+// right after they are sized (no serial zero fill of fresh pages).
+template <class T>
+struct NoInitAlloc : std::allocator<T> {
+  template <class U>
+  struct rebind {
+    using other = NoInitAlloc<U>;
+  };
+  NoInitAlloc() = default;
+  template <class U>
+  NoInitAlloc(const NoInitAlloc<U> &) noexcept {}
+  template <class U, class... Args>
+  void construct(U *p, Args &&...args) {
+    ::new ((void *)p) U(std::forward<Args>(args)...);
+  }
+  template <class U>
+  void construct(U *p) noexcept {
+    ::new ((void *)p) U;
+  }
+};
+
 template <class T>
 struct DBuf {
   T *p = nullptr;
@@ -72,7 +95,8 @@ struct DBuf {
     CK(cudaMalloc(&p, count * sizeof(T)));
     n = count;
   }
-  void upload(const std::vector<T> &h, cudaStream_t s) {
+  template <class A>
+  void upload(const std::vector<T, A> &h, cudaStream_t s) {
     alloc(h.size());
     if (!h.empty()) CK(cudaMemcpyAsync(p, h.data(), h.size() * sizeof(T), cudaMemcpyHostToDevice, s));
   }
@@ -275,7 +299,7 @@ struct ChainList {
   Keyed ent;                    // entries in build order
   std::vector<Keyed> parts;     // further entries, built after ent, in part order
   std::vector<ChainGroup> grp;  // one per key, filled by finish()
-  std::vector<ChainEntry> flat;
+  std::vector<ChainEntry, NoInitAlloc<ChainEntry>> flat;
   int ntiles = 0;
   double flops = 0.0;
   size_t size() const {
@@ -307,7 +331,8 @@ struct ChainList {
       }
     }
     start[ng] = run;
-    flat.assign((size_t)run, ChainEntry{});
+    flat.clear();
+    flat.resize((size_t)run);  // every element is written by the scatter below
     parallel_for(ns, [&](size_t s) {
       int64_t *o = off.data() + s * ng;
       for (const auto &pe : *src[s]) flat[(size_t)o[(size_t)pe.first]++] = pe.second;
@@ -344,38 +369,47 @@ struct ChainTune {
   int flat_wide = 1;   // flat kernel CTAs: 1 = one wide CTA per SM (6 FP64 / 12 FP32 warps),
                        // 0 = two narrower CTAs per SM (4 / 8 warps each)
 };
-
 // Host half of a task list's upload: the execution list (entries in their
 // cheaper association, cut into equal-work chunks when split_tasks), the launch
 // groups of the three chunk kernels (32 x 32 tiles, flattened lanes, tensor
 // cores) and the ordered reduction of the chunk slots.
 struct ExecPlan {
-  std::vector<ChainEntry> xs;
-  std::vector<double> w;
+  std::vector<ChainEntry, NoInitAlloc<ChainEntry>> xs;
+  std::vector<double, NoInitAlloc<double>> w;
   std::vector<ChainGroup> vb, vf, vt;
   std::vector<ReduceGroup> vr;
   int tiles = 0;
   int64_t soff = 0, e0 = 0;
 };
 
+// The entry D^T += f Z^T Y^T X^T of D += f X Y Z: same operands, swapped strides.
+static ChainEntry transposed_entry(const ChainEntry &e) {
+  ChainEntry t{};
+  t.x = e.z;  // X' = Z^T
+  t.xrs = e.zcs;
+  t.xcs = e.zrs;
+  t.y = e.y;  // Y' = Y^T
+  t.yrs = e.ycs;
+  t.ycs = e.yrs;
+  t.z = e.x;  // Z' = X^T
+  t.zrs = e.xcs;
+  t.zcs = e.xrs;
+  t.n = e.p;
+  t.p = e.n;
+  t.f = e.f;
+  return t;
+}
+
 static void plan_exec(const ChainList &CL, bool tensor_cores, bool split_tasks, const ChainTune &tune,
                       ExecPlan &X) {
   std::vector<ChainGroup> &vb = X.vb, &vf = X.vf, &vt = X.vt;
   std::vector<ReduceGroup> &vr = X.vr;
-  const bool split = split_tasks;
   int &tiles = X.tiles;
   int64_t &soff = X.soff, &e0 = X.e0;
   tiles = 0;
   soff = e0 = 0;
-  // Execution list: with split chunks, the entries of an output block whose
-  // other association is cheaper (n p q + m n q < m n p + m p q) run as the
-  // transposed product D^T += f Z^T Y^T X^T (same operands, swapped strides)
-  // in chunks of their own; their slot is written through transposed strides,
-  // so the ordered reduction is unchanged.
-  std::vector<ChainEntry> &xs = X.xs;
-  std::vector<double> &w = X.w;
-  xs.reserve(CL.flat.size());
-  w.reserve(CL.flat.size());
+  auto &xs = X.xs;
+  auto &w = X.w;
   auto tc_entry_ok = [&](const ChainEntry &e, int m, int q) {
     // Y must be a whole row-major psi block; identity sides are square
     return !(e.n < 1 || e.p < 1 || e.n > 128 || e.p > 128 || e.y == ~0ull || e.ycs != 1 || e.yrs != e.p ||
@@ -384,17 +418,12 @@ static void plan_exec(const ChainList &CL, bool tensor_cores, bool split_tasks, 
   auto tc_shape_ok = [&](int m, int q) {
     return tensor_cores && m <= 128 && q <= 128 && (m >= tune.tc_min || q >= tune.tc_min);
   };
-  double total = 0.0;
-  for (const auto &g : CL.grp)
-    for (int i = g.first; i < g.first + g.count; ++i) {
-      const ChainEntry &e = CL.flat[i];
-      total += 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
-    }
-  const double chunk_work = std::max(total / tune.target_chunks, tune.min_chunk);
-  auto place = [&](ChainGroup t) {
-    bool tc_ok = t.count > 0 && tc_shape_ok(t.m, t.q);
-    for (int i = t.first; tc_ok && i < t.first + t.count; ++i) tc_ok = tc_entry_ok(xs[i], t.m, t.q);
-    if (tc_ok) {
+  auto weight = [](const ChainGroup &g, const ChainEntry &e) {
+    return 1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull);
+  };
+  // chunk kind: tensor-core chunks need every entry in the tensor-core form
+  auto place = [&](ChainGroup t, bool entries_tc_ok) {
+    if (t.count > 0 && tc_shape_ok(t.m, t.q) && entries_tc_ok) {
       vt.push_back(t);
     } else if (t.m <= 32 && t.q <= 32) {
       vf.push_back(t);
@@ -404,92 +433,153 @@ static void plan_exec(const ChainList &CL, bool tensor_cores, bool split_tasks, 
       vb.push_back(t);
     }
   };
-  for (const auto &g : CL.grp) {
-    if (!split) {
+  auto chunk_tc_ok = [&](const ChainGroup &t) {
+    bool ok = t.count > 0 && tc_shape_ok(t.m, t.q);
+    for (int i = t.first; ok && i < t.first + t.count; ++i) ok = tc_entry_ok(xs[i], t.m, t.q);
+    return ok;
+  };
+  const size_t ng = CL.grp.size();
+  if (!split_tasks) {
+    xs.reserve(CL.flat.size());
+    w.reserve(CL.flat.size());
+    for (const auto &g : CL.grp) {
       ChainGroup t = g;
       t.first = (int)xs.size();
       for (int i = g.first; i < g.first + g.count; ++i) {
-        const ChainEntry &e = CL.flat[i];
-        xs.push_back(e);
-        w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, e.x == ~0ull, e.z == ~0ull));
+        xs.push_back(CL.flat[i]);
+        w.push_back(weight(g, CL.flat[i]));
       }
-      place(t);
-      continue;
+      place(t, chunk_tc_ok(t));
     }
-    // orientation of each entry (tensor-core blocks keep the stored one)
-    bool tc_group = tc_shape_ok(g.m, g.q);
-    for (int i = g.first; tc_group && i < g.first + g.count; ++i) tc_group = tc_entry_ok(CL.flat[i], g.m, g.q);
-    const int n0 = (int)xs.size();
-    std::vector<int> tr;
-    for (int i = g.first; i < g.first + g.count; ++i) {
-      const ChainEntry &e = CL.flat[i];
-      const bool xid = e.x == ~0ull, zid = e.z == ~0ull;
-      if (tune.orient && !tc_group && !xid && !zid && prefer_transposed(g.m, e.n, e.p, g.q)) {
-        tr.push_back(i);
-        continue;
-      }
-      xs.push_back(e);
-      w.push_back(1.0 + entry_flops(g.m, e.n, e.p, g.q, xid, zid));
-    }
-    const int n1 = (int)xs.size();
-    for (int i : tr) {
-      const ChainEntry &e = CL.flat[i];
-      ChainEntry t{};
-      t.x = e.z;  // X' = Z^T
-      t.xrs = e.zcs;
-      t.xcs = e.zrs;
-      t.y = e.y;  // Y' = Y^T
-      t.yrs = e.ycs;
-      t.ycs = e.yrs;
-      t.z = e.x;  // Z' = X^T
-      t.zrs = e.xcs;
-      t.zcs = e.xrs;
-      t.n = e.p;
-      t.p = e.n;
-      t.f = e.f;
-      xs.push_back(t);
-      w.push_back(1.0 + entry_flops(g.q, t.n, t.p, g.m, false, false));
-    }
-    const int n2 = (int)xs.size();
-    const int64_t mq = (int64_t)g.m * g.q;
-    ReduceGroup r{};
-    r.e0 = e0;
-    r.soff = soff;
-    r.d = g.d;
-    r.drs = g.drs;
-    r.dcs = g.dcs;
-    r.m = g.m;
-    r.q = g.q;
-    int nsplit = 0;
-    for (int part = 0; part < 2; ++part) {
-      const int lo = part == 0 ? n0 : n1, hi = part == 0 ? n1 : n2;
-      int i = lo;
-      while (i < hi) {
+  } else {
+    // Execution list: the entries of an output block whose other association
+    // is cheaper (n p q + m n q < m n p + m p q) run as the transposed product
+    // in chunks of their own, after the block's other chunks; their slot is
+    // written through transposed strides, so the ordered reduction is
+    // unchanged.  Tensor-core blocks keep the stored association.  Output
+    // blocks are planned in parallel; every weight is an integer, so the sums
+    // (and with them the chunk boundaries) do not depend on the order.
+    std::vector<double> gwork(ng, 0.0);
+    parallel_for(ng, [&](size_t gi) {
+      const ChainGroup &g = CL.grp[gi];
+      double a = 0.0;
+      for (int i = g.first; i < g.first + g.count; ++i) a += weight(g, CL.flat[i]);
+      gwork[gi] = a;
+    });
+    double total = 0.0;
+    for (double a : gwork) total += a;
+    const double chunk_work = std::max(total / tune.target_chunks, tune.min_chunk);
+    struct GroupExec {
+      bool tc = false;                 // tensor-core shape with every entry in tensor-core form
+      int nn = 0;                      // entries kept in the stored association
+      std::vector<int> csize[2];       // chunk sizes: stored association, transposed
+      std::vector<char> ctc[2];        // chunk routable to the tensor cores (filled with the entries)
+      int64_t xbase = 0, soff = 0;
+    };
+    std::vector<GroupExec> ge(ng);
+    auto transposed_here = [&](const ChainGroup &g, bool tcg, const ChainEntry &e) {
+      return tune.orient && !tcg && e.x != ~0ull && e.z != ~0ull && prefer_transposed(g.m, e.n, e.p, g.q);
+    };
+    parallel_for(ng, [&](size_t gi) {
+      const ChainGroup &g = CL.grp[gi];
+      GroupExec &G = ge[gi];
+      bool tcg = tc_shape_ok(g.m, g.q);
+      for (int i = g.first; tcg && i < g.first + g.count; ++i) tcg = tc_entry_ok(CL.flat[i], g.m, g.q);
+      G.tc = tcg;
+      for (int part = 0; part < 2; ++part) {
+        // greedy equal-work chunks over this part's entries, in build order
         double acc = 0.0;
-        int j = i;
-        while (j < hi && (j == i || acc + w[j] <= chunk_work)) acc += w[j++];
-        ChainGroup t = g;
-        t.first = i;
-        t.count = j - i;
-        t.d = (uint64_t)(soff + (int64_t)nsplit * mq);  // slot: m x q row-major
-        if (part == 0) {
-          t.drs = g.q;
-          t.dcs = 1;
-        } else {  // transposed chunk: q x m output written into the m x q slot
-          t.m = g.q;
-          t.q = g.m;
-          t.drs = 1;
-          t.dcs = g.q;
+        int cnt = 0;
+        for (int i = g.first; i < g.first + g.count; ++i) {
+          const ChainEntry &e = CL.flat[i];
+          if (transposed_here(g, tcg, e) != (part == 1)) continue;
+          if (part == 0) ++G.nn;
+          const double we = part == 0 ? weight(g, e) : 1.0 + entry_flops(g.q, e.p, e.n, g.m, false, false);
+          if (cnt > 0 && acc + we > chunk_work) {
+            G.csize[part].push_back(cnt);
+            acc = 0.0;
+            cnt = 0;
+          }
+          acc += we;
+          ++cnt;
         }
-        place(t);
-        ++nsplit;
-        i = j;
+        if (cnt > 0) G.csize[part].push_back(cnt);
       }
+    });
+    int64_t nx = 0;
+    for (size_t gi = 0; gi < ng; ++gi) {
+      const ChainGroup &g = CL.grp[gi];
+      ge[gi].xbase = nx;
+      ge[gi].soff = soff;
+      nx += g.count;
+      soff += (int64_t)(ge[gi].csize[0].size() + ge[gi].csize[1].size()) * g.m * g.q;
     }
-    r.nsplit = nsplit;
-    vr.push_back(r);
-    soff += (int64_t)nsplit * mq;
-    e0 += mq;
+    xs.resize((size_t)nx);  // every element is written below
+    w.resize((size_t)nx);
+    parallel_for(ng, [&](size_t gi) {
+      const ChainGroup &g = CL.grp[gi];
+      GroupExec &G = ge[gi];
+      int64_t a = G.xbase, b = G.xbase + G.nn;
+      for (int i = g.first; i < g.first + g.count; ++i) {
+        const ChainEntry &e = CL.flat[i];
+        if (!transposed_here(g, G.tc, e)) {
+          xs[(size_t)a] = e;
+          w[(size_t)a++] = weight(g, e);
+        } else {
+          const ChainEntry t = transposed_entry(e);
+          xs[(size_t)b] = t;
+          w[(size_t)b++] = 1.0 + entry_flops(g.q, t.n, t.p, g.m, false, false);
+        }
+      }
+      int64_t first = G.xbase;
+      for (int part = 0; part < 2; ++part)
+        for (int c : G.csize[part]) {
+          ChainGroup t{};
+          t.first = (int)first;
+          t.count = c;
+          t.m = part == 0 ? g.m : g.q;
+          t.q = part == 0 ? g.q : g.m;
+          G.ctc[part].push_back(chunk_tc_ok(t) ? 1 : 0);
+          first += c;
+        }
+    });
+    for (size_t gi = 0; gi < ng; ++gi) {
+      const ChainGroup &g = CL.grp[gi];
+      const GroupExec &G = ge[gi];
+      const int64_t mq = (int64_t)g.m * g.q;
+      ReduceGroup r{};
+      r.e0 = e0;
+      r.soff = G.soff;
+      r.d = g.d;
+      r.drs = g.drs;
+      r.dcs = g.dcs;
+      r.m = g.m;
+      r.q = g.q;
+      int nsplit = 0;
+      int64_t first = G.xbase;
+      for (int part = 0; part < 2; ++part)
+        for (size_t c = 0; c < G.csize[part].size(); ++c) {
+          ChainGroup t = g;
+          t.first = (int)first;
+          t.count = G.csize[part][c];
+          t.d = (uint64_t)(G.soff + (int64_t)nsplit * mq);  // slot: m x q row-major
+          if (part == 0) {
+            t.drs = g.q;
+            t.dcs = 1;
+          } else {  // transposed chunk: q x m output written into the m x q slot
+            t.m = g.q;
+            t.q = g.m;
+            t.drs = 1;
+            t.dcs = g.q;
+          }
+          place(t, G.ctc[part][c] != 0);
+          ++nsplit;
+          first += t.count;
+        }
+      r.nsplit = nsplit;
+      vr.push_back(r);
+      e0 += mq;
+    }
   }
   // optionally heaviest groups first: CTAs are dispatched in grid order, so the
   // light groups fill the last wave; the natural order keeps the chunks of one
@@ -547,7 +637,7 @@ struct DevChain {
     plan_exec(CL, tensor_cores, split_tasks, tune, X);
     split = split_tasks;
     flat_wide = tune.flat_wide;
-    const std::vector<ChainEntry> &xs = X.xs;
+    const auto &xs = X.xs;
     const std::vector<ChainGroup> &vb = X.vb, &vf = X.vf, &vt = X.vt;
     const std::vector<ReduceGroup> &vr = X.vr;
     const int tiles = X.tiles;
@@ -573,7 +663,7 @@ struct DevChain {
   // Tensor-core entries: tile images of every X, Z^T operator view (deduplicated,
   // exact identity tiles for identity sides) and of every psi block read as Y^T.
   // Operator addresses are absolute (the task list is launched with x/z bases 0).
-  void build_tc(const std::vector<ChainEntry> &xs, const std::vector<ChainGroup> &vt, cudaStream_t s) {
+  void build_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt, cudaStream_t s) {
     std::vector<TcEntry> te;
     std::vector<TcGroup> tg;
     std::vector<TileSpec> ts;
@@ -908,86 +998,165 @@ static std::vector<RPiece> resolve_pieces(const Integrals &I, int k, const Block
 
 // Expand pieces over the psi blocks of Eq. wf_sec into the H.psi task list
 // (Sec. 2.2.1): one entry per (piece, s -> s'), plus the transposed entry of
-// Hermitian-conjugate pieces.  Also counts the algorithmic FLOPs.  This part:
-// the pieces [r0, r1).
-static void expand_hpsi_range(const std::vector<RPiece> &rps, size_t r0, size_t r1, const Arenas &A,
-                              const Psi &Y, const BlockLayout &lb,
-                              std::vector<std::pair<int, ChainEntry>> &out, double &flops) {
-  flops = 0.0;
+// Hermitian-conjugate pieces.  Returns the algorithmic FLOPs.  This part: the
+// pieces [r0, r1); emit(output block, entry) receives the entries in build
+// order.  Per piece, the site images of the four site states and the effective
+// block of every block sector are tabulated once for all psi blocks.
+template <class Emit>
+static double expand_range(const std::vector<RPiece> &rps, size_t r0, size_t r1, const Arenas &A, const Psi &Y,
+                           const BlockLayout &lb, Emit &&emit) {
+  struct Eff {
+    bool ok;
+    int a2, rs, cs;
+    uint64_t addr;
+  };
+  std::vector<Eff> effl((size_t)Y.nl), effr((size_t)Y.nr);
+  double flops = 0.0;
   for (size_t ri = r0; ri < r1; ++ri) {
     const RPiece &rp = rps[ri];
     const Piece &p = rp.p;
     const int psl = mat_parity(p.sl), psr = mat_parity(p.sr);
+    int b2[4], c2[4];
+    double vb[4], vc[4];
+    bool any_b = false, any_c = false;
+    for (int x = 0; x < 4; ++x) {
+      b2[x] = site_image(p.sl, x, vb[x]);
+      c2[x] = site_image(p.sr, x, vc[x]);
+      any_b |= b2[x] >= 0;
+      any_c |= c2[x] >= 0;
+    }
+    if (!any_b || !any_c) continue;
+    for (int x = 0; x < Y.nl; ++x) {
+      Eff &E = effl[(size_t)x];
+      E.ok = eff_block(rp.l, A, 0, x, E.a2, E.addr, E.rs, E.cs);
+    }
+    for (int x = 0; x < Y.nr; ++x) {
+      Eff &E = effr[(size_t)x];
+      E.ok = eff_block(rp.r, A, 1, x, E.a2, E.addr, E.rs, E.cs);
+    }
+    const bool xid = rp.l.arena < 0, zid = rp.r.arena < 0;
     for (size_t si = 0; si < Y.blk.size(); ++si) {
       const PsiBlock &s = Y.blk[si];
-      double vb, vc;
-      const int b2 = site_image(p.sl, s.b, vb);
-      if (b2 < 0) continue;
-      const int c2 = site_image(p.sr, s.c, vc);
-      if (c2 < 0) continue;
-      int a2, d2, lrs, lcs, rrs, rcs;
-      uint64_t la, ra;
-      if (!eff_block(rp.l, A, 0, s.a, a2, la, lrs, lcs)) continue;
-      if (!eff_block(rp.r, A, 1, s.d, d2, ra, rrs, rcs)) continue;
-      const int so = Y.find(a2, b2, c2, d2);
+      const int sb = b2[s.b], sc = c2[s.c];
+      if (sb < 0 || sc < 0) continue;
+      const Eff &El = effl[(size_t)s.a];
+      if (!El.ok) continue;
+      const Eff &Er = effr[(size_t)s.d];
+      if (!Er.ok) continue;
+      const int so = Y.find(El.a2, sb, sc, Er.a2);
       if (so < 0) continue;
       const PsiBlock &t = Y.blk[so];
       const int na = npart(lb.sec[s.a]), nb = nsite(s.b), nc = nsite(s.c);
       const int sgn_exp = rp.r.par * (na + nb + nc) + psr * (na + nb) + psl * na;
-      const double f = p.coef * vb * vc * ((sgn_exp & 1) ? -1.0 : 1.0);
-      const bool xid = rp.l.arena < 0, zid = rp.r.arena < 0;
+      const double f = p.coef * vb[s.b] * vc[s.c] * ((sgn_exp & 1) ? -1.0 : 1.0);
       ChainEntry e{};
-      e.x = la;
-      e.xrs = lrs;
-      e.xcs = lcs;
+      e.x = El.addr;
+      e.xrs = El.rs;
+      e.xcs = El.cs;
       e.y = (uint64_t)s.off;
       e.yrs = s.md;
       e.ycs = 1;
-      e.z = ra;
-      e.zrs = rcs;  // Z = R^T
-      e.zcs = rrs;
+      e.z = Er.addr;
+      e.zrs = Er.cs;  // Z = R^T
+      e.zcs = Er.rs;
       e.n = s.ma;
       e.p = s.md;
       e.f = f;
-      out.push_back({(int)so, e});
+      emit(so, e);
       flops += entry_flops(t.ma, s.ma, s.md, t.md, xid, zid);
       if (p.hc) {
         ChainEntry h{};
-        h.x = la;
-        h.xrs = lcs;  // X = L^T
-        h.xcs = lrs;
+        h.x = El.addr;
+        h.xrs = El.cs;  // X = L^T
+        h.xcs = El.rs;
         h.y = (uint64_t)t.off;
         h.yrs = t.md;
         h.ycs = 1;
-        h.z = ra;  // Z = R
-        h.zrs = rrs;
-        h.zcs = rcs;
+        h.z = Er.addr;  // Z = R
+        h.zrs = Er.rs;
+        h.zcs = Er.cs;
         h.n = t.ma;
         h.p = t.md;
         h.f = f;
-        out.push_back({(int)si, h});
+        emit((int)si, h);
         flops += entry_flops(s.ma, t.ma, t.md, s.md, xid, zid);
       }
     }
   }
+  return flops;
 }
 
-// The whole expansion, in piece order: a fixed cut of the pieces into ranges
-// (independent of the host's core count) expanded by worker threads, then
-// concatenated in range order, so the task list is the same as a sequential
-// expansion and the FLOP sum (exact integers) is identical.
+// The pieces are cut into a fixed number of ranges (independent of the host's
+// core count) that worker threads expand; ranges keep piece order, so the
+// result is that of a sequential expansion and the FLOP sum (exact integers)
+// is identical.
+static size_t expand_ranges(const std::vector<RPiece> &rps) { return std::min<size_t>(rps.size(), 64); }
+
+// The task list in build order (per-range parts, grouped later by finish()).
 static void expand_hpsi(const std::vector<RPiece> &rps, const Arenas &A, const Psi &Y,
                         const BlockLayout &lb, ChainList &CL, double &flops) {
-  const size_t nr = std::min<size_t>(rps.size(), 64);
+  const size_t nr = expand_ranges(rps);
   std::vector<ChainList::Keyed> part(nr);
   std::vector<double> fl(nr, 0.0);
   parallel_for(nr, [&](size_t c) {
-    expand_hpsi_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb, part[c], fl[c]);
+    ChainList::Keyed &out = part[c];
+    fl[c] = expand_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb,
+                         [&](int key, const ChainEntry &e) { out.push_back({key, e}); });
   });
   flops = 0.0;
   for (size_t c = 0; c < nr; ++c) {
-    CL.parts.push_back(std::move(part[c]));  // grouped by finish() without a serial concatenation
+    CL.parts.push_back(std::move(part[c]));
     flops += fl[c];
+  }
+}
+
+static std::vector<ChainGroup> psi_protos(const Psi &Y);
+
+// The task list grouped by output block, as finish() would leave it, built in
+// two passes over the pieces: count the entries of every (range, output block),
+// then write each entry straight to its place (no intermediate list).
+static void expand_hpsi_grouped(const std::vector<RPiece> &rps, const Arenas &A, const Psi &Y,
+                                const BlockLayout &lb, ChainList &CL, double &flops) {
+  const size_t nr = expand_ranges(rps), ng = Y.blk.size();
+  std::vector<int64_t> cnt(nr * ng, 0);
+  std::vector<double> fl(nr, 0.0);
+  parallel_for(nr, [&](size_t c) {
+    int64_t *k = cnt.data() + c * ng;
+    fl[c] = expand_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb,
+                         [&](int key, const ChainEntry &) { ++k[(size_t)key]; });
+  });
+  std::vector<int64_t> start(ng + 1, 0), off(nr * ng);
+  int64_t run = 0;
+  for (size_t g = 0; g < ng; ++g) {
+    start[g] = run;
+    for (size_t c = 0; c < nr; ++c) {
+      off[c * ng + g] = run;
+      run += cnt[c * ng + g];
+    }
+  }
+  start[ng] = run;
+  CL.flat.clear();
+  CL.flat.resize((size_t)run);  // every element is written by the second pass
+  parallel_for(nr, [&](size_t c) {
+    int64_t *o = off.data() + c * ng;
+    ChainEntry *dst = CL.flat.data();
+    expand_range(rps, c * rps.size() / nr, (c + 1) * rps.size() / nr, A, Y, lb,
+                 [&](int key, const ChainEntry &e) { dst[o[(size_t)key]++] = e; });
+  });
+  flops = 0.0;
+  for (size_t c = 0; c < nr; ++c) flops += fl[c];
+  const std::vector<ChainGroup> protos = psi_protos(Y);
+  CL.grp.clear();
+  CL.ntiles = 0;
+  for (size_t g = 0; g < ng; ++g) {
+    const int64_t n = start[g + 1] - start[g];
+    if (n == 0) continue;
+    ChainGroup G = protos[g];
+    G.first = (int)start[g];
+    G.count = (int)n;
+    G.tile0 = CL.ntiles;
+    CL.ntiles += ((G.m + 31) / 32) * ((G.q + 31) / 32);
+    CL.grp.push_back(G);
   }
 }
 
@@ -1012,13 +1181,12 @@ static void hpsi_chainlist(dmrg_ctx *c, bool f32, ChainList &CL, double &flops) 
   DevBlock *lb = lblock(c), *rb = rblock(c);
   if (f32) {
     Arenas A32{{&lb->lay, &rb->lay}, {P.f32[0].p, P.f32[1].p}, &P.temps.set, {P.f32[2].p, P.f32[3].p}, 4};
-    expand_hpsi(P.rps, A32, P.psi, lb->lay, CL, flops);
+    expand_hpsi_grouped(P.rps, A32, P.psi, lb->lay, CL, flops);
   } else {
     Arenas A{{&lb->lay, &rb->lay}, {lb->arena(), rb->arena()}, &P.temps.set,
              {P.temps.arena[0].p, P.temps.arena[1].p}, 8};
-    expand_hpsi(P.rps, A, P.psi, lb->lay, CL, flops);
+    expand_hpsi_grouped(P.rps, A, P.psi, lb->lay, CL, flops);
   }
-  CL.finish(psi_protos(P.psi));
 }
 
 static void build_hplan(dmrg_ctx *c) {
@@ -2284,9 +2452,9 @@ extern "C" int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, c
   Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 8};
   ChainList CL;
   double f = 0.0;
-  expand_hpsi(rps, A, Y, lb, CL, f);
+  expand_hpsi_grouped(rps, A, Y, lb, CL, f);
   if (flops) *flops = f;
-  if (tasks) *tasks = (long long)CL.size();
+  if (tasks) *tasks = (long long)CL.flat.size();
   API_END
 }
 
@@ -2320,15 +2488,15 @@ extern "C" int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const
   Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 8};
   ChainList CL;
   double f = 0.0;
-  expand_hpsi(rps, A, Y, lb, CL, f);
-  *ntasks = (long long)CL.size();
   ChainList::Keyed tasks;
-  if (grouped) {  // the order the GPU task list uses: grouped by output block
-    CL.finish(psi_protos(Y));
+  if (grouped) {  // the task list the GPU runs: grouped by output block
+    expand_hpsi_grouped(rps, A, Y, lb, CL, f);
+    *ntasks = (long long)CL.flat.size();
     for (const auto &g : CL.grp)
       for (int i = g.first; i < g.first + g.count; ++i) tasks.push_back({Y.find_block(g.d), CL.flat[i]});
-  } else {
-    tasks.swap(CL.ent);
+  } else {  // build order
+    expand_hpsi(rps, A, Y, lb, CL, f);
+    *ntasks = (long long)CL.size();
     for (const auto &p : CL.parts) tasks.insert(tasks.end(), p.begin(), p.end());
   }
   if (out) {
@@ -2389,8 +2557,7 @@ extern "C" int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const 
   Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 8};
   ChainList CL;
   double f = 0.0;
-  expand_hpsi(rps, A, Y, lb, CL, f);
-  CL.finish(psi_protos(Y));
+  expand_hpsi_grouped(rps, A, Y, lb, CL, f);
   ExecPlan X;
   plan_exec(CL, tensor_cores != 0, true, T, X);
   counts[0] = (long long)X.xs.size();

@@ -10,6 +10,7 @@
 #include <limits>
 #include <sstream>
 #include <stdexcept>
+#include <unordered_map>
 
 namespace dmrg {
 
@@ -610,59 +611,95 @@ std::vector<Piece> hamiltonian_pieces(const Integrals &I, int k, bool l_empty, b
 
 // ---------------------------------------------------------------- compression
 
-static std::string opkey(const OpRef &o) {
-  std::ostringstream s;
-  s << o.type << ':' << o.kind << ':' << o.i << ':' << o.j << ':' << o.tr;
-  if (o.type == 2) {
-    s << '[';
-    for (auto &t : o.lc) {
-      double c = std::get<2>(t);
-      uint64_t bits;
-      std::memcpy(&bits, &c, 8);
-      s << std::get<0>(t) << ',' << std::get<1>(t) << ',' << bits << ';';
-    }
-    s << ']';
-  }
-  return s.str();
-}
-
-static std::string famkey(const OpRef &o) {
-  if (o.type == 0) return "I";
-  int i = o.i, j = o.j;
-  if (o.type == 2) { i = std::get<0>(o.lc[0]); j = std::get<1>(o.lc[0]); }
-  int du, dd;
-  dq_of(o.kind, i, j, du, dd);
-  std::ostringstream s;
-  s << o.kind << ':' << o.tr << ':' << du << ':' << dd;
-  return s.str();
-}
-
 static void add_sources(std::map<std::pair<int, int>, double> &acc, const OpRef &o, double c) {
   if (o.type == 1) acc[{o.i, o.j}] += c;
   else for (auto &t : o.lc) acc[{std::get<0>(t), std::get<1>(t)}] += c * std::get<2>(t);
 }
 
+// Exact identity of an operator reference (coefficients compared bit for bit).
+static bool same_op(const OpRef &a, const OpRef &b) {
+  if (a.type != b.type || a.kind != b.kind || a.i != b.i || a.j != b.j || a.tr != b.tr) return false;
+  if (a.type != 2) return true;
+  if (a.lc.size() != b.lc.size()) return false;
+  for (size_t t = 0; t < a.lc.size(); ++t) {
+    if (std::get<0>(a.lc[t]) != std::get<0>(b.lc[t]) || std::get<1>(a.lc[t]) != std::get<1>(b.lc[t])) return false;
+    uint64_t x, y;
+    const double cx = std::get<2>(a.lc[t]), cy = std::get<2>(b.lc[t]);
+    std::memcpy(&x, &cx, 8);
+    std::memcpy(&y, &cy, 8);
+    if (x != y) return false;
+  }
+  return true;
+}
+
+static uint64_t mix(uint64_t h, uint64_t x) {
+  h ^= x + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  return h;
+}
+
+static uint64_t op_hash(const OpRef &o) {
+  uint64_t h = mix(mix(mix(mix(mix(0, (uint64_t)o.type), (uint64_t)(o.kind + 1)), (uint64_t)(o.i + 1)),
+                       (uint64_t)(o.j + 1)), (uint64_t)o.tr);
+  if (o.type == 2)
+    for (const auto &t : o.lc) {
+      uint64_t bits;
+      const double c = std::get<2>(t);
+      std::memcpy(&bits, &c, 8);
+      h = mix(mix(mix(h, (uint64_t)std::get<0>(t)), (uint64_t)std::get<1>(t)), bits);
+    }
+  return h;
+}
+
+// The pieces that can be merged: same exact operator on the fixed side, same
+// family (kind, transpose, quantum-number change) on the varying side, same
+// Hermitian-conjugate flag.
+struct MergeKey {
+  const OpRef *fixed;
+  int kind, du, dd;
+  bool tr, hc;
+  uint64_t hash;
+};
+struct MergeKeyHash {
+  size_t operator()(const MergeKey &k) const { return (size_t)k.hash; }
+};
+struct MergeKeyEq {
+  bool operator()(const MergeKey &a, const MergeKey &b) const {
+    return a.hash == b.hash && a.kind == b.kind && a.du == b.du && a.dd == b.dd && a.tr == b.tr &&
+           a.hc == b.hc && same_op(*a.fixed, *b.fixed);
+  }
+};
+
 // side 0: merge the left operators of pieces sharing the exact right operator.
 static std::vector<Piece> compress_side(const std::vector<Piece> &in, int side) {
-  std::map<std::string, std::vector<int>> groups;
-  std::vector<std::string> order;
+  std::unordered_map<MergeKey, int, MergeKeyHash, MergeKeyEq> index;
+  std::vector<std::vector<int>> groups;  // in order of first appearance
   for (int i = 0; i < (int)in.size(); ++i) {
     const Piece &p = in[i];
     const OpRef &fixed = side == 0 ? p.r : p.l;
     const OpRef &var = side == 0 ? p.l : p.r;
     if (var.type == 0) {  // identity on the varying side: nothing to merge
-      std::string k = "single:" + std::to_string(i);
-      groups[k].push_back(i);
-      order.push_back(k);
+      groups.push_back({i});
       continue;
     }
-    std::string k = opkey(fixed) + "|" + famkey(var) + "|" + (p.hc ? "h" : "n");
-    if (!groups.count(k)) order.push_back(k);
-    groups[k].push_back(i);
+    int vi = var.i, vj = var.j;
+    if (var.type == 2) {
+      vi = std::get<0>(var.lc[0]);
+      vj = std::get<1>(var.lc[0]);
+    }
+    MergeKey k{&fixed, var.kind, 0, 0, var.tr, p.hc, 0};
+    dq_of(var.kind, vi, vj, k.du, k.dd);
+    k.hash = mix(mix(mix(mix(mix(op_hash(fixed), (uint64_t)(var.kind + 1)), (uint64_t)var.tr),
+                         (uint64_t)(k.du + 64)), (uint64_t)(k.dd + 64)), (uint64_t)p.hc);
+    auto it = index.find(k);
+    if (it == index.end()) {
+      index.emplace(k, (int)groups.size());
+      groups.push_back({i});
+    } else {
+      groups[it->second].push_back(i);
+    }
   }
   std::vector<Piece> out;
-  for (auto &k : order) {
-    auto &g = groups[k];
+  for (auto &g : groups) {
     if (g.size() == 1) { out.push_back(in[g[0]]); continue; }
     // elementary site pairs -> merged sources
     std::map<std::pair<int, int>, std::map<std::pair<int, int>, double>> acc;

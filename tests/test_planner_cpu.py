@@ -165,17 +165,26 @@ def test_task_dump_reproduces_the_flop_count():
     assert np.all(T[:, 1:5] >= 1)
 
 
-def test_grouped_task_list_is_a_stable_sort_by_output_block():
-    """The GPU task list is the build-order list grouped by output psi block, tasks
-    of one block in build order (the ordered sigma accumulation relies on it)."""
+@pytest.mark.parametrize("layout", ["mixed", "profile_sz1", "profile_large"])
+def test_grouped_task_list_is_a_stable_sort_by_output_block(layout):
+    """The GPU task list (built in two counting passes straight into grouped order)
+    is the build-order list grouped by output psi block, tasks of one block in
+    build order (the ordered sigma accumulation relies on it)."""
     import numpy as np
     from paper_2001_04890_gb300 import binding, workloads
-    L, N, k = 10, 10, 4
+    if layout == "mixed":
+        L, N, tsz, k = 10, 10, 0, 4
+        sec = [(a, b, 1 + (3 * a + b) % 5) for a in range(0, 5) for b in range(0, 5)]
+        sec_r = [(a, b, 1 + (a + 2 * b) % 4) for a in range(0, 5) for b in range(0, 5)]
+    else:
+        L, N, tsz, M, k = (13, 13, 1, 90, 5) if layout == "profile_sz1" else (16, 16, 0, 300, 7)
+        nu, nd = (N + tsz) // 2, (N - tsz) // 2
+        left, right = workloads.middle_bond_sectors(L, nu, nd, M, k)
+        sec = [(a, b, d) for (a, b), d in sorted(left.items())]
+        sec_r = [(a, b, d) for (a, b), d in sorted(right.items())]
     h, v = workloads.integrals(L, seed=3)
-    sec = [(a, b, 1 + (3 * a + b) % 5) for a in range(0, 5) for b in range(0, 5)]
-    sec_r = [(a, b, 1 + (a + 2 * b) % 4) for a in range(0, 5) for b in range(0, 5)]
-    T0 = binding.debug_tasks(h, v, N, 0, k, sec, sec_r)
-    T1 = binding.debug_tasks(h, v, N, 0, k, sec, sec_r, grouped=True)
+    T0 = binding.debug_tasks(h, v, N, tsz, k, sec, sec_r)
+    T1 = binding.debug_tasks(h, v, N, tsz, k, sec, sec_r, grouped=True)
     assert T1.shape == T0.shape
     order = np.argsort(T0[:, 0], kind="stable")
     assert np.array_equal(T1, T0[order])
