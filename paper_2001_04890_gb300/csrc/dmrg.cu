@@ -1335,14 +1335,23 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
   Arenas A{{lay[0], lay[1]}, {stored[0], stored[1]}, &temps.set,
            {temps.arena[0].p, temps.arena[1].p}, 8};
 
-  // sub-block lookup: enlarged sector index + row offset of (x, y)
-  std::map<std::pair<int, int>, std::pair<int, int>> where;
+  // sub-block lookup: enlarged sector index + row offset of (block sector, site
+  // state), a dense table over the old block's sectors and the four site states
+  const int nob = (int)old->lay.sec.size();
+  std::vector<std::pair<int, int>> where((size_t)nob * 4, {-1, 0});
   for (size_t e = 0; e < enl.size(); ++e)
-    for (auto &sb : enl[e].sub) where[{sb.x, sb.y}] = {(int)e, sb.roff};
+    for (auto &sb : enl[e].sub) {
+      const int bs = side == 0 ? sb.x : sb.y, st = side == 0 ? sb.y : sb.x;
+      where[(size_t)bs * 4 + st] = {(int)e, sb.roff};
+    }
 
-  // output groups: (family, k, new ket sector)
+  // output groups: (family, k, new ket sector), numbered in order of first use
+  const int nns = (int)nb->lay.sec.size();
+  std::vector<int64_t> fam_gbase(nb->lay.fam.size() + 1, 0);
+  for (size_t f = 0; f < nb->lay.fam.size(); ++f)
+    fam_gbase[f + 1] = fam_gbase[f] + (int64_t)nb->lay.fam[f].K() * nns;
+  std::vector<int> gid((size_t)fam_gbase.back(), -1);
   std::vector<ChainGroup> protos;
-  std::map<std::tuple<int, int, int>, int> gid;
   ChainList CL;
   const double *Op = Odev.p;
   for (auto &rd : rds) {
@@ -1363,20 +1372,17 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
         int b2, rs, cs;
         uint64_t addr;
         if (!eff_block(rd.blk, A, side, blk_sec, b2, addr, rs, cs)) continue;
-        const std::pair<int, int> key2 = side == 0 ? std::make_pair(b2, site2) : std::make_pair(site2, b2);
-        auto it = where.find(key2);
-        if (it == where.end()) continue;
-        const int e2 = it->second.first, roff2 = it->second.second;
+        const std::pair<int, int> &w2 = where[(size_t)b2 * 4 + site2];
+        if (w2.first < 0) continue;
+        const int e2 = w2.first, roff2 = w2.second;
         if (new_of_enl[e2] != Bn) continue;
         const int sgn_exp = side == 0 ? psite * npart(old->lay.sec[blk_sec])
                                       : pblk * nsite(site_st);
         const double f = rd.coef * sv * ((sgn_exp & 1) ? -1.0 : 1.0);
         const int mk = kept[e], mk2 = kept[e2];
         const int mb = old->lay.sec[blk_sec].dim, mb2 = old->lay.sec[b2].dim;
-        auto g = std::make_tuple(rd.fam, rd.k, An);
-        int gi;
-        auto git = gid.find(g);
-        if (git == gid.end()) {
+        int &gi = gid[(size_t)(fam_gbase[rd.fam] + (int64_t)rd.k * nns + An)];
+        if (gi < 0) {
           ChainGroup cg{};
           cg.d = eaddr(nb->ops.p) + F.base + F.off[An] + (int64_t)rd.k * mk2 * mk;
           cg.drs = mk;
@@ -1385,9 +1391,6 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
           cg.q = mk;
           gi = (int)protos.size();
           protos.push_back(cg);
-          gid[g] = gi;
-        } else {
-          gi = git->second;
         }
         ChainEntry ce{};
         // X = O_{e2}[rows of (b2, site2)]^T : mk2 x mb2
