@@ -603,6 +603,195 @@ static void plan_exec(const ChainList &CL, bool tensor_cores, bool split_tasks, 
   }
 }
 
+// First-use numbering of keys: occurrence i (0 <= i < n) has key key_of(i);
+// uid[i] receives the number of its key, keys numbered in order of first
+// occurrence, and first[u] the first occurrence of key u.  Parallel: the keys
+// are split into hash shards, each numbered by one thread scanning all
+// occurrences in order, so the numbering is that of a serial pass.
+template <class Key, class Hash, class KeyOf>
+static void first_use_numbering(size_t n, KeyOf key_of, Hash hash, std::vector<uint32_t> &uid,
+                                std::vector<size_t> &first) {
+  const size_t S = 16, B = 1 << 16;
+  std::vector<uint8_t> shard(n);
+  parallel_for((n + B - 1) / B, [&](size_t c) {
+    for (size_t i = c * B; i < std::min(n, (c + 1) * B); ++i)
+      shard[i] = (uint8_t)((hash(key_of(i)) >> 40) % S);
+  });
+  std::vector<uint32_t> lid(n);
+  std::vector<std::vector<size_t>> lfirst(S);
+  parallel_for(S, [&](size_t sh) {
+    std::unordered_map<Key, uint32_t, Hash> m;
+    for (size_t i = 0; i < n; ++i) {
+      if (shard[i] != sh) continue;
+      auto r = m.try_emplace(key_of(i), (uint32_t)lfirst[sh].size());
+      if (r.second) lfirst[sh].push_back(i);
+      lid[i] = r.first->second;
+    }
+  });
+  // global numbers in order of first occurrence
+  std::vector<std::vector<uint32_t>> gnum(S);
+  std::vector<size_t> pos(S, 0);
+  for (size_t sh = 0; sh < S; ++sh) gnum[sh].resize(lfirst[sh].size());
+  first.clear();
+  for (size_t i = 0; i < n; ++i) {
+    const size_t sh = shard[i];
+    if (pos[sh] < lfirst[sh].size() && lfirst[sh][pos[sh]] == i) {
+      gnum[sh][pos[sh]++] = (uint32_t)first.size();
+      first.push_back(i);
+    }
+  }
+  uid.resize(n);
+  parallel_for((n + B - 1) / B, [&](size_t c) {
+    for (size_t i = c * B; i < std::min(n, (c + 1) * B); ++i) uid[i] = gnum[shard[i]][lid[i]];
+  });
+}
+
+// An operator view read as a tensor-core tile: source address, strides, shape.
+struct ViewKey {
+  uint64_t src;
+  int rs, cs, R, K;
+  bool operator==(const ViewKey &o) const {
+    return src == o.src && rs == o.rs && cs == o.cs && R == o.R && K == o.K;
+  }
+};
+struct ViewHash {
+  size_t operator()(const ViewKey &k) const {
+    uint64_t h = k.src * 0x9E3779B97F4A7C15ull;
+    h ^= ((uint64_t)(uint32_t)k.rs << 32 | (uint32_t)k.cs) + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
+    h ^= ((uint64_t)(uint32_t)k.R << 32 | (uint32_t)k.K) + 0x8CB92BA72F3D8DD7ull + (h << 6) + (h >> 2);
+    return (size_t)h;
+  }
+};
+struct OffsetHash {
+  size_t operator()(uint64_t y) const {
+    uint64_t h = y * 0x9E3779B97F4A7C15ull;
+    return (size_t)(h ^ (h >> 29));
+  }
+};
+
+// Host plan of the tensor-core launch: entries with tile offsets, blocks
+// ordered by kernel shape, and the operator-view and psi tiles to build.
+// Tiles are laid out in order of first use in launch order; identical views
+// are stored once (deduplicated by address, strides and shape); identity
+// operators are exact identity tiles.
+struct TcPlan {
+  std::vector<TcEntry> te;
+  std::vector<TcGroup> tg;
+  std::vector<TileSpec> ts;
+  std::vector<PsiTileSpec> ps;
+  int ntc_shape[3] = {0, 0, 0};
+  uint64_t opbytes = 0, psibytes = 0;
+};
+
+static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
+                    TcPlan &P) {
+  auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
+  const size_t nv = vt.size();
+  // kernel shape per block: 2 (m <= 64, q, p <= 32), 1 (m, q, p <= 64), 0 (the rest);
+  // blocks ordered by shape.  Shape 2 is used only when every block fits it: each
+  // shape is its own launch with its own last-wave tail, and a third launch costs
+  // more than the extra resident CTAs gain when larger blocks are present.
+  std::vector<int> pmax(nv, 0);
+  parallel_for(nv, [&](size_t i) {
+    const ChainGroup &g = vt[i];
+    int m = 0;
+    for (int j = g.first; j < g.first + g.count; ++j) m = std::max(m, xs[j].p);
+    pmax[i] = m;
+  });
+  auto fits = [&](size_t i, int lim_q) { return vt[i].m <= 64 && vt[i].q <= lim_q && pmax[i] <= lim_q; };
+  bool all_tiny = true;
+  for (size_t i = 0; i < nv; ++i) all_tiny = all_tiny && fits(i, 32);
+  auto shape_of = [&](size_t i) {
+    if (all_tiny) return 2;
+    return fits(i, 64) ? 1 : 0;
+  };
+  std::vector<size_t> order;
+  for (int sh : {2, 1, 0}) {
+    int cnt = 0;
+    for (size_t i = 0; i < nv; ++i)
+      if (shape_of(i) == sh) {
+        order.push_back(i);
+        ++cnt;
+      }
+    P.ntc_shape[sh] = cnt;
+  }
+  const size_t nb = order.size();
+  std::vector<int64_t> base(nb + 1, 0);
+  for (size_t k = 0; k < nb; ++k) base[k + 1] = base[k] + vt[order[k]].count;
+  const size_t T = (size_t)base[nb];
+  P.tg.resize(nb);
+  P.te.assign(T, TcEntry{});
+  std::vector<int> src(T), blk(T);  // per launch position: entry index, block
+  parallel_for(nb, [&](size_t k) {
+    const ChainGroup &g = vt[order[k]];
+    P.tg[k] = TcGroup{g.d, g.drs, g.dcs, g.m, g.q, (int)base[k], g.count};
+    // tasks of this output block that read the same psi block run as stacks: their X
+    // along the MMA's M in one stage 1 (at most MR / m16 of them, MR the shape's M)
+    const int mr = shape_of(order[k]) == 0 ? 128 : 64;
+    const int cap = std::max(1, std::min(8, mr / (int)c16(g.m)));
+    std::vector<int> idx(g.count);
+    std::iota(idx.begin(), idx.end(), g.first);
+    std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return xs[a].y < xs[b].y; });
+    std::vector<uint64_t> keys(idx.size());
+    for (size_t j = 0; j < idx.size(); ++j) keys[j] = xs[idx[j]].y;
+    const std::vector<int> runs = stack_runs(keys, cap);
+    size_t run_i = 0;
+    int remaining = 0;
+    for (size_t j = 0; j < idx.size(); ++j) {
+      const ChainEntry &e = xs[idx[j]];
+      TcEntry &t = P.te[(size_t)base[k] + j];
+      if (remaining == 0) {  // first member of a stack: the run of tasks on this psi block
+        t.stack = runs[run_i++];
+        remaining = t.stack;
+      }
+      --remaining;
+      t.n = e.n;
+      t.p = e.p;
+      t.f = (float)e.f;
+      src[(size_t)base[k] + j] = idx[j];
+      blk[(size_t)base[k] + j] = (int)k;
+    }
+  });
+  // operator views: occurrence 2 i is entry i's X, 2 i + 1 its Z^T
+  auto view_of = [&](size_t o) {
+    const size_t i = o >> 1;
+    const ChainEntry &e = xs[(size_t)src[i]];
+    const TcGroup &g = P.tg[(size_t)blk[i]];
+    if ((o & 1) == 0)
+      return e.x == ~0ull ? ViewKey{~0ull, 0, 0, e.n, e.n} : ViewKey{e.x * 4ull, e.xrs, e.xcs, g.m, e.n};
+    return e.z == ~0ull ? ViewKey{~0ull, 0, 0, e.p, e.p} : ViewKey{e.z * 4ull, e.zcs, e.zrs, g.q, e.p};
+  };
+  std::vector<uint32_t> vid;
+  std::vector<size_t> vfirst;
+  first_use_numbering<ViewKey>(2 * T, view_of, ViewHash(), vid, vfirst);
+  std::vector<uint64_t> voff(vfirst.size());
+  for (size_t u = 0; u < vfirst.size(); ++u) {
+    const ViewKey v = view_of(vfirst[u]);
+    voff[u] = P.opbytes;
+    P.ts.push_back(TileSpec{v.src, P.opbytes, v.rs, v.cs, v.R, v.K});
+    P.opbytes += c16(v.R) * c16(v.K) * 4;
+  }
+  // psi blocks read as Y^T
+  auto y_of = [&](size_t i) { return xs[(size_t)src[i]].y; };
+  std::vector<uint32_t> yid;
+  std::vector<size_t> yfirst;
+  first_use_numbering<uint64_t>(T, y_of, OffsetHash(), yid, yfirst);
+  std::vector<uint64_t> yoff(yfirst.size());
+  for (size_t u = 0; u < yfirst.size(); ++u) {
+    const ChainEntry &e = xs[(size_t)src[yfirst[u]]];
+    yoff[u] = P.psibytes;
+    P.ps.push_back(PsiTileSpec{(int64_t)e.y, P.psibytes, e.n, e.p});
+    P.psibytes += c16(e.p) * c16(e.n) * 4;
+  }
+  parallel_for((T + 65535) / 65536, [&](size_t c) {
+    for (size_t i = c * 65536; i < std::min(T, (c + 1) * 65536); ++i) {
+      P.te[i].xt = voff[vid[2 * i]];
+      P.te[i].zt = voff[vid[2 * i + 1]];
+      P.te[i].yt = yoff[yid[i]];
+    }
+  });
+}
+
 // A task list on the device.  When the tensor cores are enabled, output blocks
 // with both sides <= 128, one side >= tc_min and every entry's n, p <= 128 go
 // to the tensor-core kernel; of the rest, blocks of at most 32 x 32 go to the
@@ -663,103 +852,16 @@ struct DevChain {
   // Tensor-core entries: tile images of every X, Z^T operator view (deduplicated,
   // exact identity tiles for identity sides) and of every psi block read as Y^T.
   // Operator addresses are absolute (the task list is launched with x/z bases 0).
-  void build_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt, cudaStream_t s) {
-    std::vector<TcEntry> te;
-    std::vector<TcGroup> tg;
-    std::vector<TileSpec> ts;
-    std::vector<PsiTileSpec> ps;
-    struct ViewKey {
-      uint64_t src;
-      int rs, cs, R, K;
-      bool operator==(const ViewKey &o) const {
-        return src == o.src && rs == o.rs && cs == o.cs && R == o.R && K == o.K;
-      }
-    };
-    struct ViewHash {
-      size_t operator()(const ViewKey &k) const {
-        uint64_t h = k.src * 0x9E3779B97F4A7C15ull;
-        h ^= ((uint64_t)(uint32_t)k.rs << 32 | (uint32_t)k.cs) + 0x632BE59BD9B4E019ull + (h << 6) + (h >> 2);
-        h ^= ((uint64_t)(uint32_t)k.R << 32 | (uint32_t)k.K) + 0x8CB92BA72F3D8DD7ull + (h << 6) + (h >> 2);
-        return (size_t)h;
-      }
-    };
-    std::unordered_map<ViewKey, uint64_t, ViewHash> opmap;  // operator view -> tile offset
-    std::unordered_map<uint64_t, uint64_t> psimap;
-    uint64_t opbytes = 0, psibytes = 0;
-    auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
-    auto op_tile = [&](uint64_t src, int rs, int cs, int R, int K) -> uint64_t {
-      const ViewKey key{src, rs, cs, R, K};
-      auto it = opmap.find(key);
-      if (it != opmap.end()) return it->second;
-      ts.push_back(TileSpec{src, opbytes, rs, cs, R, K});
-      opmap.emplace(key, opbytes);
-      const uint64_t at = opbytes;
-      opbytes += c16(R) * c16(K) * 4;
-      return at;
-    };
-    // kernel shape per block: 2 (m <= 64, q, p <= 32), 1 (m, q, p <= 64), 0 (the rest);
-    // groups ordered by shape.  Shape 2 is used only when every block fits it: each
-    // shape is its own launch with its own last-wave tail, and a third launch costs
-    // more than the extra resident CTAs gain when larger blocks are present.
-    auto fits = [&](const ChainGroup &g, int lim_q) {
-      int pmax = 0;
-      for (int i = g.first; i < g.first + g.count; ++i) pmax = std::max(pmax, xs[i].p);
-      return g.m <= 64 && g.q <= lim_q && pmax <= lim_q;
-    };
-    bool all_tiny = true;
-    for (const auto &g : vt) all_tiny = all_tiny && fits(g, 32);
-    auto shape_of = [&](const ChainGroup &g) {
-      if (all_tiny) return 2;
-      return fits(g, 64) ? 1 : 0;
-    };
-    std::vector<ChainGroup> order;
-    for (int sh : {2, 1, 0}) {
-      int cnt = 0;
-      for (const auto &g : vt)
-        if (shape_of(g) == sh) {
-          order.push_back(g);
-          ++cnt;
-        }
-      ntc_shape[sh] = cnt;
-    }
-    for (const auto &g : order) {
-      tg.push_back(TcGroup{g.d, g.drs, g.dcs, g.m, g.q, (int)te.size(), g.count});
-      // tasks of this output block that read the same psi block run as stacks: their X
-      // along the MMA's M in one stage 1 (at most MR / m16 of them, MR the shape's M)
-      const int mr = shape_of(g) == 0 ? 128 : 64;
-      const int cap = std::max(1, std::min(8, mr / (int)c16(g.m)));
-      std::vector<int> idx(g.count);
-      std::iota(idx.begin(), idx.end(), g.first);
-      std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return xs[a].y < xs[b].y; });
-      std::vector<uint64_t> keys(idx.size());
-      for (size_t k = 0; k < idx.size(); ++k) keys[k] = xs[idx[k]].y;
-      const std::vector<int> runs = stack_runs(keys, cap);
-      size_t run_i = 0;
-      int remaining = 0;
-      for (size_t k = 0; k < idx.size(); ++k) {
-        const int i = idx[k];
-        const ChainEntry &e = xs[i];
-        TcEntry t{};
-        if (remaining == 0) {  // first member of a stack: the run of tasks on this psi block
-          t.stack = runs[run_i++];
-          remaining = t.stack;
-        }
-        --remaining;
-        t.n = e.n;
-        t.p = e.p;
-        t.f = (float)e.f;
-        t.xt = e.x == ~0ull ? op_tile(~0ull, 0, 0, e.n, e.n) : op_tile(e.x * 4ull, e.xrs, e.xcs, g.m, e.n);
-        t.zt = e.z == ~0ull ? op_tile(~0ull, 0, 0, e.p, e.p) : op_tile(e.z * 4ull, e.zcs, e.zrs, g.q, e.p);
-        auto it = psimap.find(e.y);
-        if (it == psimap.end()) {
-          it = psimap.emplace(e.y, psibytes).first;
-          ps.push_back(PsiTileSpec{(int64_t)e.y, psibytes, e.n, e.p});
-          psibytes += c16(e.p) * c16(e.n) * 4;
-        }
-        t.yt = it->second;
-        te.push_back(t);
-      }
-    }
+  void build_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
+                cudaStream_t s) {
+    TcPlan P;
+    plan_tc(xs, vt, P);
+    std::vector<TcEntry> &te = P.te;
+    std::vector<TcGroup> &tg = P.tg;
+    std::vector<TileSpec> &ts = P.ts;
+    std::vector<PsiTileSpec> &ps = P.ps;
+    const uint64_t opbytes = P.opbytes, psibytes = P.psibytes;
+    for (int sh = 0; sh < 3; ++sh) ntc_shape[sh] = P.ntc_shape[sh];
     ntc = (int)tg.size();
     npts = (int)ps.size();
     if (ntc == 0) return;
