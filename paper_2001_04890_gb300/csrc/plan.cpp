@@ -834,23 +834,25 @@ std::string dump_halfop(const HalfOp &h) {
 
 Ref TempSet::make(int side, const BlockLayout &b, const OpRef &op, bool &zero) {
   zero = false;
-  std::vector<std::pair<int, double>> src;
+  std::vector<std::pair<int, double>> m;
+  m.reserve(op.lc.size());
   int fam = -1;
   for (auto &t : op.lc) {
     int f, kk;
     if (!b.get(op.kind, std::get<0>(t), std::get<1>(t), f, kk)) continue;
     if (fam < 0) fam = f;
     if (f != fam) throw std::runtime_error("linear combination spans operator families");
-    src.emplace_back(kk, std::get<2>(t));
+    m.emplace_back(kk, std::get<2>(t));
   }
-  if (src.empty()) { zero = true; return Ref(); }
-  std::sort(src.begin(), src.end());
-  // merge duplicates
-  std::vector<std::pair<int, double>> m;
-  for (auto &x : src) {
-    if (!m.empty() && m.back().first == x.first) m.back().second += x.second;
-    else m.push_back(x);
+  if (m.empty()) { zero = true; return Ref(); }
+  // sources in (operator, coefficient) order, duplicates summed in that order
+  if (!std::is_sorted(m.begin(), m.end())) std::sort(m.begin(), m.end());
+  size_t w = 0;
+  for (size_t r = 0; r < m.size(); ++r) {
+    if (w > 0 && m[w - 1].first == m[r].first) m[w - 1].second += m[r].second;
+    else m[w++] = m[r];
   }
+  m.resize(w);
   auto fk = std::make_tuple(side, fam, op.tr);
   int tf;
   auto it = fam_of[side].find(fk);
@@ -868,29 +870,52 @@ Ref TempSet::make(int side, const BlockLayout &b, const OpRef &op, bool &zero) {
   } else {
     tf = it->second;
   }
-  std::vector<std::pair<int, int64_t>> key;
+  // an identical temporary (same family, same sources, coefficients bit for bit)
+  // is stored once
+  auto same_bits = [](double x, double y) {
+    uint64_t a, c;
+    std::memcpy(&a, &x, 8);
+    std::memcpy(&c, &y, 8);
+    return a == c;
+  };
+  uint64_t h = 0x243f6a8885a308d3ull ^ ((uint64_t)tf << 1) ^ (uint64_t)op.tr;
   for (auto &x : m) {
-    int64_t bits;
+    uint64_t bits;
     std::memcpy(&bits, &x.second, 8);
-    key.emplace_back(x.first, bits);
+    h ^= (uint64_t)x.first + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h ^= bits + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
   }
-  auto dk = std::make_tuple(side, tf, op.tr, key);
-  int kk;
-  auto d = dedup[side].find(dk);
-  if (d == dedup[side].end()) {
-    kk = this->fam[side][tf].K();
-    this->fam[side][tf].coefs.push_back(m);
-    dedup[side][dk] = kk;
-  } else {
-    kk = d->second;
+  TempFamily &T = this->fam[side][tf];
+  auto &cands = dedup[side][h];
+  for (const auto &cand : cands) {
+    if (cand.first != tf) continue;
+    const int kk = cand.second;
+    const auto &c = T.coefs[(size_t)kk];
+    if (c.size() != m.size()) continue;
+    bool eq = true;
+    for (size_t i = 0; eq && i < m.size(); ++i) eq = c[i].first == m[i].first && same_bits(c[i].second, m[i].second);
+    if (eq) {
+      Ref r;
+      r.arena = 2 + side;
+      r.fam = tf;
+      r.k = kk;
+      r.tr = false;
+      r.dnu = T.dnu;
+      r.dnd = T.dnd;
+      r.par = (r.dnu + r.dnd) & 1;
+      return r;
+    }
   }
+  const int kk = T.K();
+  T.coefs.push_back(std::move(m));
+  cands.push_back({tf, kk});
   Ref r;
   r.arena = 2 + side;
   r.fam = tf;
   r.k = kk;
   r.tr = false;
-  r.dnu = this->fam[side][tf].dnu;
-  r.dnd = this->fam[side][tf].dnd;
+  r.dnu = T.dnu;
+  r.dnd = T.dnd;
   r.par = (r.dnu + r.dnd) & 1;
   return r;
 }

@@ -226,7 +226,7 @@ struct Ref {
 struct TempSet {
   std::vector<TempFamily> fam[2];
   std::map<std::tuple<int, int, bool>, int> fam_of[2];
-  std::map<std::tuple<int, int, bool, std::vector<std::pair<int, int64_t>>>, int> dedup[2];
+  std::unordered_map<uint64_t, std::vector<std::pair<int, int>>> dedup[2];  // hash -> (family, temp)
   int64_t total[2] = {0, 0};
   Ref make(int side, const BlockLayout &b, const OpRef &op, bool &zero);
   void layout(const BlockLayout *blocks[2]);
