@@ -611,11 +611,6 @@ std::vector<Piece> hamiltonian_pieces(const Integrals &I, int k, bool l_empty, b
 
 // ---------------------------------------------------------------- compression
 
-static void add_sources(std::map<std::pair<int, int>, double> &acc, const OpRef &o, double c) {
-  if (o.type == 1) acc[{o.i, o.j}] += c;
-  else for (auto &t : o.lc) acc[{std::get<0>(t), std::get<1>(t)}] += c * std::get<2>(t);
-}
-
 // Exact identity of an operator reference (coefficients compared bit for bit).
 static bool same_op(const OpRef &a, const OpRef &b) {
   if (a.type != b.type || a.kind != b.kind || a.i != b.i || a.j != b.j || a.tr != b.tr) return false;
@@ -699,34 +694,82 @@ static std::vector<Piece> compress_side(const std::vector<Piece> &in, int side) 
     }
   }
   std::vector<Piece> out;
+  // Merged sources per elementary site pair, accumulated in dense arrays over
+  // the source index (i + 1, j + 1): every source receives its contributions
+  // in the order of the pieces, and both the site pairs and the sources come
+  // out in ascending order.  Buffers are reused across groups.
+  int D = 2;
+  for (const auto &p : in)
+    for (const OpRef *o : {&p.l, &p.r}) {
+      D = std::max(D, std::max(o->i, o->j) + 2);
+      for (const auto &t : o->lc) D = std::max(D, std::max(std::get<0>(t), std::get<1>(t)) + 2);
+    }
+  struct Acc {
+    std::vector<double> val;
+    std::vector<char> used;
+    std::vector<int> touched;
+  };
+  std::vector<Acc> pool;
+  std::vector<int> slot_of(256, -1), pairs;
   for (auto &g : groups) {
     if (g.size() == 1) { out.push_back(in[g[0]]); continue; }
-    // elementary site pairs -> merged sources
-    std::map<std::pair<int, int>, std::map<std::pair<int, int>, double>> acc;
+    pairs.clear();
     for (int i : g) {
       const Piece &p = in[i];
+      const OpRef &var = side == 0 ? p.l : p.r;
       for (int e1 = 0; e1 < 16; ++e1) {
         if (p.sl[e1] == 0.0) continue;
         for (int e2 = 0; e2 < 16; ++e2) {
           if (p.sr[e2] == 0.0) continue;
-          add_sources(acc[{e1, e2}], side == 0 ? p.l : p.r, p.coef * p.sl[e1] * p.sr[e2]);
+          const int pe = e1 * 16 + e2;
+          if (slot_of[pe] < 0) {
+            slot_of[pe] = (int)pairs.size();
+            pairs.push_back(pe);
+            if (pool.size() < pairs.size()) pool.emplace_back();
+            Acc &a = pool[(size_t)slot_of[pe]];
+            if (a.val.size() < (size_t)D * D) {
+              a.val.assign((size_t)D * D, 0.0);
+              a.used.assign((size_t)D * D, 0);
+            }
+          }
+          Acc &a = pool[(size_t)slot_of[pe]];
+          const double c = p.coef * p.sl[e1] * p.sr[e2];
+          auto add = [&](int si, int sj, double x) {
+            const size_t idx = (size_t)(si + 1) * D + (sj + 1);
+            if (!a.used[idx]) {
+              a.used[idx] = 1;
+              a.val[idx] = 0.0;
+              a.touched.push_back((int)idx);
+            }
+            a.val[idx] += x;
+          };
+          if (var.type == 1) add(var.i, var.j, c);
+          else for (const auto &t : var.lc) add(std::get<0>(t), std::get<1>(t), c * std::get<2>(t));
         }
       }
     }
     const Piece &p0 = in[g[0]];
     const OpRef &var0 = side == 0 ? p0.l : p0.r;
-    for (auto &e : acc) {
+    std::sort(pairs.begin(), pairs.end());
+    for (int pe : pairs) {
+      Acc &a = pool[(size_t)slot_of[pe]];
+      slot_of[pe] = -1;
+      std::sort(a.touched.begin(), a.touched.end());
       std::vector<std::tuple<int, int, double>> lc;
-      for (auto &s : e.second)
-        if (s.second != 0.0) lc.emplace_back(s.first.first, s.first.second, s.second);
+      for (int idx : a.touched) {
+        a.used[(size_t)idx] = 0;
+        const double x = a.val[(size_t)idx];
+        if (x != 0.0) lc.emplace_back(idx / D - 1, idx % D - 1, x);
+      }
+      a.touched.clear();
       if (lc.empty()) continue;
       Piece q;
       q.coef = 1.0;
       q.hc = p0.hc;
       q.sl = mat_zero();
-      q.sl[e.first.first] = 1.0;
+      q.sl[pe / 16] = 1.0;
       q.sr = mat_zero();
-      q.sr[e.first.second] = 1.0;
+      q.sr[pe % 16] = 1.0;
       OpRef m = lincomb(var0.kind, var0.tr, lc);
       if (side == 0) { q.l = m; q.r = p0.r; } else { q.l = p0.l; q.r = m; }
       out.push_back(q);
