@@ -620,12 +620,40 @@ static void first_use_numbering(size_t n, KeyOf key_of, Hash hash, std::vector<u
   std::vector<uint32_t> lid(n);
   std::vector<std::vector<size_t>> lfirst(S);
   parallel_for(S, [&](size_t sh) {
-    std::unordered_map<Key, uint32_t, Hash> m;
+    // open-addressing table (linear probing, at most half full)
+    struct Slot {
+      Key key;
+      uint64_t h;
+      uint32_t id;
+    };
+    const uint32_t EMPTY = 0xffffffffu;
+    std::vector<Slot> tab(1024, Slot{Key{}, 0, EMPTY});
+    size_t used = 0;
+    auto place = [&](std::vector<Slot> &t, const Slot &x) {
+      size_t at = (size_t)x.h & (t.size() - 1);
+      while (t[at].id != EMPTY) at = (at + 1) & (t.size() - 1);
+      t[at] = x;
+    };
     for (size_t i = 0; i < n; ++i) {
       if (shard[i] != sh) continue;
-      auto r = m.try_emplace(key_of(i), (uint32_t)lfirst[sh].size());
-      if (r.second) lfirst[sh].push_back(i);
-      lid[i] = r.first->second;
+      const Key k = key_of(i);
+      const uint64_t h = (uint64_t)hash(k);
+      size_t at = (size_t)h & (tab.size() - 1);
+      while (tab[at].id != EMPTY && !(tab[at].h == h && tab[at].key == k)) at = (at + 1) & (tab.size() - 1);
+      if (tab[at].id != EMPTY) {
+        lid[i] = tab[at].id;
+        continue;
+      }
+      const uint32_t id = (uint32_t)lfirst[sh].size();
+      lfirst[sh].push_back(i);
+      lid[i] = id;
+      tab[at] = Slot{k, h, id};
+      if (2 * ++used > tab.size()) {
+        std::vector<Slot> bigger(2 * tab.size(), Slot{Key{}, 0, EMPTY});
+        for (const Slot &x : tab)
+          if (x.id != EMPTY) place(bigger, x);
+        tab.swap(bigger);
+      }
     }
   });
   // global numbers in order of first occurrence
