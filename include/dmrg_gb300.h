@@ -377,6 +377,27 @@ int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, 
                     const int *sec_l, int nr, const int *sec_r, int tensor_cores, const double *tune,
                     long long *counts, long long *xs_out, long long *grp_out, long long *red_out);
 
+/*
+ * dmrg_debug_tc -- host-only dump of the tensor-core launch plan for the same
+ * task list as dmrg_debug_exec with tensor_cores = 1 (FP32 operand addresses):
+ * the blocks routed to the tensor cores, ordered by kernel shape, their tasks
+ * grouped into stacks that share a psi block, and the operator and psi tiles
+ * in order of first use.  tune: NULL or 4 doubles as in dmrg_debug_exec.
+ * counts (9): tasks, blocks, operator tiles, psi tiles, operator tile bytes,
+ * psi tile bytes, blocks of the 64 x 32, 64 x 64 and 128 x 128 shapes.
+ * Optional arrays (NULL to skip): te_out 14 per task (X tile, Y^T tile, Z^T
+ * tile byte offsets, stack length or 0, execution-list entry, X offset, X row
+ * and column strides, Z offset, Z row and column strides, psi offset of Y, n,
+ * p), tg_out 7 per block (output offset, row stride, column stride, m, q,
+ * first task, task count), ts_out 6 per operator tile (source element offset
+ * times 4 or -1 for identity, tile byte offset, source row and column strides,
+ * rows, columns), ps_out 4 per psi tile (psi offset, tile byte offset, n, p).
+ * No GPU is used.
+ */
+int dmrg_debug_tc(int L, int N, int two_sz, const double *h, const double *v, int k, int nl, const int *sec_l,
+                  int nr, const int *sec_r, const double *tune, long long *counts, long long *te_out,
+                  long long *tg_out, long long *ts_out, long long *ps_out);
+
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */
 int dmrg_debug_pieces(int L, const double *h, const double *v, int k, int l_empty, int r_empty,

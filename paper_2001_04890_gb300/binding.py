@@ -81,6 +81,8 @@ def lib():
                                        C.c_int, ip, C.c_longlong, llp]),
         "dmrg_debug_exec": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
                                       C.c_int, dp, llp, llp, llp, llp]),
+        "dmrg_debug_tc": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip, dp,
+                                    llp, llp, llp, llp, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
                                         C.c_char_p, C.c_longlong, llp]),
     }
@@ -155,6 +157,30 @@ def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
                                  red.ctypes.data_as(llp)))
     keys = ("entries", "tile_chunks", "flat_chunks", "tc_chunks", "reduce_groups", "tiles", "scratch", "reduced")
     return dict(zip(keys, (int(x) for x in cnt))), xs, ch, red
+
+
+def debug_tc(h, v, N, two_sz, k, sec_l, sec_r, tune=None):
+    """Host-only tensor-core launch plan: dict of counts and the arrays tasks (n, 14),
+    blocks (n, 7), op_tiles (n, 6), psi_tiles (n, 4) described in the header."""
+    h, v = _f64(h), _f64(v)
+    L = h.shape[0]
+    tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
+    tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
+    tune_arr = None if tune is None else np.ascontiguousarray(tune, dtype=np.float64)
+    tp = None if tune_arr is None else _dptr(tune_arr)
+    llp = C.POINTER(C.c_longlong)
+    cnt = np.zeros(9, dtype=np.int64)
+    args = (L, N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr), _iptr(tr), tp)
+    _check(lib().dmrg_debug_tc(*args, cnt.ctypes.data_as(llp), None, None, None, None))
+    te = np.zeros((cnt[0], 14), dtype=np.int64)
+    tg = np.zeros((cnt[1], 7), dtype=np.int64)
+    ts = np.zeros((cnt[2], 6), dtype=np.int64)
+    ps = np.zeros((cnt[3], 4), dtype=np.int64)
+    _check(lib().dmrg_debug_tc(*args, cnt.ctypes.data_as(llp), te.ctypes.data_as(llp), tg.ctypes.data_as(llp),
+                               ts.ctypes.data_as(llp), ps.ctypes.data_as(llp)))
+    keys = ("tasks", "blocks", "op_tiles", "psi_tiles", "op_bytes", "psi_bytes", "shape64x32", "shape64x64",
+            "shape128")
+    return dict(zip(keys, (int(x) for x in cnt))), te, tg, ts, ps
 
 
 def plan_hpsi_flops(h, v, N, two_sz, k, sec_l, sec_r):

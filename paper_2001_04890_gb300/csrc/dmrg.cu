@@ -712,7 +712,7 @@ struct TcPlan {
 };
 
 static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
-                    TcPlan &P) {
+                    TcPlan &P, std::vector<int> *entry_of = nullptr) {
   auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
   const size_t nv = vt.size();
   // kernel shape per block: 2 (m <= 64, q, p <= 32), 1 (m, q, p <= 64), 0 (the rest);
@@ -818,6 +818,7 @@ static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, 
       P.te[i].yt = yoff[yid[i]];
     }
   });
+  if (entry_of) entry_of->swap(src);
 }
 
 // A task list on the device.  When the tensor cores are enabled, output blocks
@@ -2742,6 +2743,91 @@ extern "C" int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const 
       o[5] = r.m;
       o[6] = r.q;
       o[7] = r.nsplit;
+    }
+  API_END
+}
+
+extern "C" int dmrg_debug_tc(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                             const int *sec_l, int nr, const int *sec_r, const double *tune, long long *counts,
+                             long long *te_out, long long *tg_out, long long *ts_out, long long *ps_out) {
+  API_BEGIN
+  if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r || !counts)
+    throw Fail{DMRG_EINVAL, "dmrg_debug_tc: bad arguments"};
+  if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
+  ChainTune T;
+  if (tune) {
+    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1))
+      throw Fail{DMRG_EINVAL, "dmrg_debug_tc: bad launch-shape parameters"};
+    T.target_chunks = tune[0];
+    T.min_chunk = tune[1];
+    T.tc_min = (int)tune[2];
+    T.by_work = (int)tune[3];
+  }
+  Integrals I;
+  I.L = L;
+  I.h.assign(h, h + (size_t)L * L);
+  I.v.assign(v, v + (size_t)L * L * L * L);
+  auto sectors = [](int n, const int *t) {
+    std::vector<Sector> out;
+    for (int i = 0; i < n; ++i) out.push_back({t[3 * i], t[3 * i + 1], t[3 * i + 2]});
+    return out;
+  };
+  std::vector<int> ls, rs;
+  for (int s = 0; s < k; ++s) ls.push_back(s);
+  for (int s = k + 2; s < L; ++s) rs.push_back(s);
+  BlockLayout lb, rb;
+  build_layout(lb, 0, L, ls, sectors(nl, sec_l));
+  build_layout(rb, 1, L, rs, sectors(nr, sec_r));
+  Psi Y = psi_layout(lb, rb, (N + two_sz) / 2, (N - two_sz) / 2);
+  TempSet temps;
+  auto rps = resolve_pieces(I, k, lb, rb, temps);
+  const BlockLayout *lay[2] = {&lb, &rb};
+  temps.layout(lay);
+  Arenas A{{&lb, &rb}, {nullptr, nullptr}, &temps, {nullptr, nullptr}, 4};  // FP32 operand addresses
+  ChainList CL;
+  double f = 0.0;
+  expand_hpsi_grouped(rps, A, Y, lb, CL, f);
+  ExecPlan X;
+  plan_exec(CL, true, true, T, X);
+  TcPlan P;
+  std::vector<int> src;
+  plan_tc(X.xs, X.vt, P, &src);
+  counts[0] = (long long)P.te.size();
+  counts[1] = (long long)P.tg.size();
+  counts[2] = (long long)P.ts.size();
+  counts[3] = (long long)P.ps.size();
+  counts[4] = (long long)P.opbytes;
+  counts[5] = (long long)P.psibytes;
+  counts[6] = P.ntc_shape[2];
+  counts[7] = P.ntc_shape[1];
+  counts[8] = P.ntc_shape[0];
+  if (te_out)
+    for (size_t i = 0; i < P.te.size(); ++i) {
+      const TcEntry &t = P.te[i];
+      const ChainEntry &e = X.xs[(size_t)src[i]];
+      long long *o = te_out + 14 * i;
+      const long long v14[14] = {(long long)t.xt, (long long)t.yt, (long long)t.zt, t.stack, src[i],
+                                 (long long)e.x, e.xrs, e.xcs, (long long)e.z, e.zrs, e.zcs,
+                                 (long long)e.y, t.n, t.p};
+      for (int j = 0; j < 14; ++j) o[j] = v14[j];
+    }
+  if (tg_out)
+    for (size_t i = 0; i < P.tg.size(); ++i) {
+      const TcGroup &g = P.tg[i];
+      const long long v7[7] = {(long long)g.d, g.drs, g.dcs, g.m, g.q, g.first, g.count};
+      for (int j = 0; j < 7; ++j) tg_out[7 * i + j] = v7[j];
+    }
+  if (ts_out)
+    for (size_t i = 0; i < P.ts.size(); ++i) {
+      const TileSpec &t = P.ts[i];
+      const long long v6[6] = {(long long)t.src, (long long)t.dst, t.rs, t.cs, t.R, t.K};
+      for (int j = 0; j < 6; ++j) ts_out[6 * i + j] = v6[j];
+    }
+  if (ps_out)
+    for (size_t i = 0; i < P.ps.size(); ++i) {
+      const PsiTileSpec &t = P.ps[i];
+      const long long v4[4] = {(long long)t.src, (long long)t.dst, t.n, t.p};
+      for (int j = 0; j < 4; ++j) ps_out[4 * i + j] = v4[j];
     }
   API_END
 }
