@@ -211,6 +211,24 @@ int dmrg_truncation_stats(dmrg_ctx *ctx, double *last_gap, double *min_gap, long
                           long long *straddled);
 
 /*
+ * dmrg_orbital_entropies -- one- and two-orbital entropies of the current
+ * two-site wave function (Eq. wf_sec) at its two sites k and k+1.  The
+ * two-orbital reduced density matrix over the site-state pairs (b, c) of the
+ * two sites, rho[(b c), (b' c')] = sum_{a,d} <psi_{a b c d}, psi_{a b' c' d}>
+ * (trace = |psi|^2), is built on the host from a copy of psi; the one-orbital
+ * matrices are its partial traces (diagonal in {0, up, dn, updn}).  s3 (may
+ * be NULL) receives the von Neumann entropies -tr(r ln r) of the
+ * trace-normalised matrices {s_k, s_{k+1}, s_{k,k+1}}; the mutual information
+ * of the pair is s_k + s_{k+1} - s_{k,k+1}.  rho2 (may be NULL): the 16 x 16
+ * matrix, row-major over 4 b + c, site states in the order 0, up, dn, updn.
+ * The paper uses these entropies for orbital ordering (single-site entropies
+ * and mutual information, Sec. 3) without defining them; these are the
+ * standard definitions.  Errors: DMRG_EINVAL (NULL context or both outputs
+ * NULL), DMRG_ESTATE (no wave function at this position), DMRG_ECUDA.
+ */
+int dmrg_orbital_entropies(dmrg_ctx *ctx, double *s3, double *rho2);
+
+/*
  * dmrg_sweep -- nsweeps two-site sweeps (Sec. 2.1, Fig. dmrg_blocks): forward
  * over positions 0..L-3 (Davidson then dmrg_renormalize(+1)), backward over
  * L-2..1 (Davidson then dmrg_renormalize(-1)).  Starts from position 0 in the
@@ -397,6 +415,19 @@ int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, 
 int dmrg_debug_tc(int L, int N, int two_sz, const double *h, const double *v, int k, int nl, const int *sec_l,
                   int nr, const int *sec_r, const double *tune, long long *counts, long long *te_out,
                   long long *tg_out, long long *ts_out, long long *ps_out);
+
+/*
+ * dmrg_debug_pair_rdm -- host-only form of dmrg_orbital_entropies for a
+ * caller's two-site wave function: nblocks blocks, abcd 4 ints per block
+ * (left block sector, left site state 0..3, right site state 0..3, right block
+ * sector; sectors are any integer labels), off_size 2 per block (element
+ * offset in psi, element count m_a m_d), psi the values.  rho2 (256, may be
+ * NULL) and s3 (3, may be NULL) as in dmrg_orbital_entropies.  DMRG_EINVAL on
+ * bad arguments or blocks of one (a, d) pair with different sizes.  No GPU is
+ * used.
+ */
+int dmrg_debug_pair_rdm(int nblocks, const int *abcd, const long long *off_size, const double *psi,
+                        double *rho2, double *s3);
 
 /* Planner introspection (host only, no GPU): text dumps of the H pieces at
  * position k and of the blocking definitions of a new block's operators. */

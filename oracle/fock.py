@@ -270,3 +270,49 @@ def fci_ground(h: np.ndarray, v: np.ndarray, n_up: int, n_dn: int, dense_max: in
         return float(ev[0]), evec[:, 0], D
     e, x = lanczos_ground(lambda y: H @ y, dim)
     return e, x, D
+
+
+# --------------------------------------------------------------------------
+# orbital reduced density matrices and entropies (post-processing of a state)
+# --------------------------------------------------------------------------
+
+def pair_rdm_dets(x: np.ndarray, D: np.ndarray, i: int) -> np.ndarray:
+    """Two-orbital reduced density matrix of sites i and i+1 of the state sum_D x_D |D>.
+
+    Indexed by 4 b + c with b, c the site states (0, up, dn, updn) of sites i
+    and i+1.  The four modes of the pair are consecutive in the Jordan-Wigner
+    order, and elements only connect pair states of equal particle number, so
+    the pair factors out of every determinant with a sign that cancels:
+    rho[(b c), (b' c')] = sum over the other modes' occupations of
+    x(b c, rest) x(b' c', rest).
+    """
+    local = (D >> (2 * i)) & 0xF
+    b = (local & 1) + 2 * ((local >> 1) & 1)
+    c = ((local >> 2) & 1) + 2 * ((local >> 3) & 1)
+    pair = (4 * b + c).astype(np.int64)
+    rest = D & ~(np.int64(0xF) << (2 * i))
+    rho = np.zeros((16, 16))
+    order = np.argsort(rest, kind="stable")
+    rs, ps, xs = rest[order], pair[order], x[order]
+    start = 0
+    while start < len(rs):
+        end = start
+        while end < len(rs) and rs[end] == rs[start]:
+            end += 1
+        v = np.zeros(16)
+        v[ps[start:end]] = xs[start:end]
+        rho += np.outer(v, v)
+        start = end
+    return rho
+
+
+def orbital_entropies(rho: np.ndarray):
+    """(s_i, s_{i+1}, s_{i,i+1}): von Neumann entropies -tr(r ln r) of the
+    trace-normalised one-orbital matrices (partial traces of the pair matrix)
+    and of the pair matrix itself."""
+    r = rho / np.trace(rho)
+    h = lambda p: float(-sum(q * np.log(q) for q in p if q > 0.0))
+    R = r.reshape(4, 4, 4, 4)
+    wl = np.einsum("bcbc->b", R)
+    wr = np.einsum("bcbc->c", R)
+    return h(wl), h(wr), h(np.linalg.eigvalsh(r))

@@ -73,6 +73,8 @@ def lib():
         "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
         "dmrg_get_tune": (C.c_int, [vp, dp]),
         "dmrg_truncation_stats": (C.c_int, [vp, dp, dp, llp, llp]),
+        "dmrg_orbital_entropies": (C.c_int, [vp, dp, dp]),
+        "dmrg_debug_pair_rdm": (C.c_int, [C.c_int, ip, llp, dp, dp, dp]),
         "dmrg_debug_truncation": (C.c_int, [C.c_int, ip, dp, C.c_int, ip, ip, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
         "dmrg_debug_pieces": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int, C.c_int,
@@ -212,6 +214,20 @@ def debug_truncation(spectra, mkeep):
         per.append(cols[pos:pos + n].copy())
         pos += n
     return kept, per, out3[0], out3[1], out3[2]
+
+
+def debug_pair_rdm(layout, psi):
+    """Host-only two-orbital matrix and entropies of a two-site wave function given as
+    blocks (a, b, c, d, m_a, m_d, offset) and values: (rho2 16 x 16, (s_left, s_right, s_pair))."""
+    lay = np.asarray(layout, dtype=np.int64).reshape(-1, 7)
+    abcd = np.ascontiguousarray(lay[:, :4], dtype=np.int32)
+    offsz = np.ascontiguousarray(np.stack([lay[:, 6], lay[:, 4] * lay[:, 5]], axis=1), dtype=np.int64)
+    psi = _f64(psi)
+    rho = np.zeros(256)
+    s3 = np.zeros(3)
+    _check(lib().dmrg_debug_pair_rdm(len(lay), _iptr(abcd), offsz.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                     _dptr(psi), _dptr(rho), _dptr(s3)))
+    return rho.reshape(16, 16), tuple(s3)
 
 
 def selftest_tcgen05(A, B):
@@ -383,6 +399,15 @@ class DMRG:
         par = np.zeros(5)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
+
+    def orbital_entropies(self):
+        """Entropies of the two sites of the current wave function (k and k+1): dict with
+        s_left, s_right, s_pair, mutual_information and the 16 x 16 two-orbital matrix rho2."""
+        s3 = np.zeros(3)
+        rho = np.zeros(256)
+        _check(lib().dmrg_orbital_entropies(self.ctx, _dptr(s3), _dptr(rho)))
+        return dict(s_left=s3[0], s_right=s3[1], s_pair=s3[2], mutual_information=s3[0] + s3[1] - s3[2],
+                    rho2=rho.reshape(16, 16))
 
     def truncation_stats(self):
         """Record of the density-matrix truncations since init: gap at the cut of the

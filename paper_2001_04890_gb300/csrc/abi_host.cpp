@@ -116,3 +116,31 @@ extern "C" int dmrg_debug_truncation(int nsectors, const int *dims, const double
     return DMRG_EINVAL;
   }
 }
+
+extern "C" int dmrg_debug_pair_rdm(int nblocks, const int *abcd, const long long *off_size, const double *psi,
+                                   double *rho2, double *s3) {
+  try {
+    if (nblocks < 1 || !abcd || !off_size || !psi) {
+      dmrg::set_error("dmrg_debug_pair_rdm: bad arguments");
+      return DMRG_EINVAL;
+    }
+    std::vector<dmrg::PsiBlockRef> blocks((size_t)nblocks);
+    for (int i = 0; i < nblocks; ++i) {
+      const int *q = abcd + 4 * i;
+      if (q[1] < 0 || q[1] > 3 || q[2] < 0 || q[2] > 3 || off_size[2 * i] < 0 || off_size[2 * i + 1] < 0) {
+        dmrg::set_error("dmrg_debug_pair_rdm: site state outside 0..3 or negative offset/size");
+        return DMRG_EINVAL;
+      }
+      blocks[(size_t)i] = {q[0], q[1], q[2], q[3], (int64_t)off_size[2 * i], (int64_t)off_size[2 * i + 1]};
+    }
+    double rho[256];
+    dmrg::pair_rdm(blocks, psi, rho);
+    if (rho2)
+      for (int i = 0; i < 256; ++i) rho2[i] = rho[i];
+    if (s3) dmrg::orbital_entropies(rho, s3);
+    return DMRG_OK;
+  } catch (const std::exception &e) {
+    dmrg::set_error(e.what());
+    return DMRG_EINVAL;
+  }
+}

@@ -3212,6 +3212,26 @@ extern "C" int dmrg_truncation_stats(dmrg_ctx *c, double *last_gap, double *min_
   API_END
 }
 
+extern "C" int dmrg_orbital_entropies(dmrg_ctx *c, double *s3, double *rho2) {
+  API_BEGIN
+  if (!c || (!s3 && !rho2)) throw Fail{DMRG_EINVAL, "NULL argument"};
+  if (!c->psi_valid) throw Fail{DMRG_ESTATE, "no wave function at this position"};
+  require_blocks(c);
+  const Psi Y = psi_layout(lblock(c)->lay, rblock(c)->lay, c->nu, c->nd);
+  if ((size_t)Y.dim > c->psi.n) throw Fail{DMRG_ESTATE, "wave function does not match the position's layout"};
+  std::vector<double> h((size_t)std::max<int64_t>(Y.dim, 1));
+  CK(cudaMemcpyAsync(h.data(), c->psi.p, Y.dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  std::vector<PsiBlockRef> blocks;
+  for (const PsiBlock &b : Y.blk) blocks.push_back({b.a, b.b, b.c, b.d, b.off, (int64_t)b.ma * b.md});
+  double rho[256];
+  pair_rdm(blocks, h.data(), rho);
+  if (rho2)
+    for (int i = 0; i < 256; ++i) rho2[i] = rho[i];
+  if (s3) orbital_entropies(rho, s3);
+  API_END
+}
+
 extern "C" int dmrg_get_tune(dmrg_ctx *c, double *params) {
   API_BEGIN
   if (!c || !params) throw Fail{DMRG_EINVAL, "NULL argument"};

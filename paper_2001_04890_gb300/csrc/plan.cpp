@@ -1062,4 +1062,88 @@ KeptSet choose_kept(const std::vector<std::vector<double>> &ev_ascending, int mk
   return r;
 }
 
+void pair_rdm(const std::vector<PsiBlockRef> &blocks, const double *psi, double rho[256]) {
+  for (int i = 0; i < 256; ++i) rho[i] = 0.0;
+  // blocks sharing the block sectors (a, d) couple; sum in block order
+  std::map<std::pair<int, int>, std::vector<size_t>> by_ad;
+  for (size_t i = 0; i < blocks.size(); ++i) by_ad[{blocks[i].a, blocks[i].d}].push_back(i);
+  for (const auto &kv : by_ad)
+    for (size_t u : kv.second)
+      for (size_t w : kv.second) {
+        const PsiBlockRef &s = blocks[u], &t = blocks[w];
+        if (s.size != t.size) throw std::runtime_error("pair_rdm: blocks of one (a, d) differ in size");
+        double acc = 0.0;
+        for (int64_t e = 0; e < s.size; ++e) acc += psi[s.off + e] * psi[t.off + e];
+        rho[(4 * s.b + s.c) * 16 + 4 * t.b + t.c] += acc;
+      }
+}
+
+void small_symmetric_eigenvalues(int n, const double *a_in, double *ev) {
+  if (n < 1 || n > 16) throw std::runtime_error("small_symmetric_eigenvalues: n out of range");
+  double a[256];
+  for (int i = 0; i < n * n; ++i) a[i] = a_in[i];
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0, diag = 0.0;
+    for (int i = 0; i < n; ++i)
+      for (int j = 0; j < n; ++j) (i == j ? diag : off) += a[i * n + j] * a[i * n + j];
+    if (off <= 1e-30 * std::max(diag, 1e-300)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const double apq = a[p * n + q];
+        if (apq == 0.0) continue;
+        // rotation angle that zeroes a_pq: tan(2 theta) = 2 a_pq / (a_qq - a_pp)
+        const double tau = (a[q * n + q] - a[p * n + p]) / (2.0 * apq);
+        const double t = (tau >= 0.0 ? 1.0 : -1.0) / (std::fabs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = t * c;
+        for (int k = 0; k < n; ++k) {  // columns p, q
+          const double akp = a[k * n + p], akq = a[k * n + q];
+          a[k * n + p] = c * akp - sn * akq;
+          a[k * n + q] = sn * akp + c * akq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows p, q
+          const double apk = a[p * n + k], aqk = a[q * n + k];
+          a[p * n + k] = c * apk - sn * aqk;
+          a[q * n + k] = sn * apk + c * aqk;
+        }
+      }
+  }
+  for (int i = 0; i < n; ++i) ev[i] = a[i * n + i];
+  std::sort(ev, ev + n);
+}
+
+void orbital_entropies(const double rho[256], double out[3]) {
+  double tr = 0.0;
+  for (int i = 0; i < 16; ++i) tr += rho[i * 16 + i];
+  if (!(tr > 0.0)) throw std::runtime_error("orbital_entropies: zero wave function");
+  auto h = [](double x) { return x > 0.0 ? -x * std::log(x) : 0.0; };
+  double sl = 0.0, sr = 0.0;
+  for (int x = 0; x < 4; ++x) {
+    double wl = 0.0, wr = 0.0;
+    for (int y = 0; y < 4; ++y) {
+      wl += rho[(4 * x + y) * 17];
+      wr += rho[(4 * y + x) * 17];
+    }
+    sl += h(wl / tr);
+    sr += h(wr / tr);
+  }
+  // the pair matrix is block diagonal in (n_up, n_dn) of the pair: diagonalise each block
+  static const int NU[4] = {0, 1, 0, 1}, ND[4] = {0, 0, 1, 1};
+  double spair = 0.0;
+  for (int u = 0; u <= 2; ++u)
+    for (int d = 0; d <= 2; ++d) {
+      int idx[16], n = 0;
+      for (int x = 0; x < 16; ++x)
+        if (NU[x / 4] + NU[x % 4] == u && ND[x / 4] + ND[x % 4] == d) idx[n++] = x;
+      if (n == 0) continue;
+      double blk[256], ev[16];
+      for (int i = 0; i < n; ++i)
+        for (int j = 0; j < n; ++j) blk[i * n + j] = rho[idx[i] * 16 + idx[j]] / tr;
+      small_symmetric_eigenvalues(n, blk, ev);
+      for (int i = 0; i < n; ++i) spair += h(ev[i]);
+    }
+  out[0] = sl;
+  out[1] = sr;
+  out[2] = spair;
+}
+
 }  // namespace dmrg

@@ -278,4 +278,22 @@ struct KeptSet {
 };
 KeptSet choose_kept(const std::vector<std::vector<double>> &ev_ascending, int mkeep, double drop);
 
+// Orbital reduced density matrices of the two sites of a two-site wave function
+// (Eq. wf_sec): block s = (a, b, c, d) holds psi_{a b c d} (m_a x m_d at psi +
+// off, size = m_a m_d).  The two-orbital matrix over the site-state pairs
+// 4 b + c is rho[(b c), (b' c')] = sum_{a,d} <psi_{a b c d}, psi_{a b' c' d}>
+// (the local transition operators are parity-even, so no Jordan-Wigner sign
+// enters); it is block diagonal in the pair's (n_up, n_dn).
+struct PsiBlockRef {
+  int a, b, c, d;
+  int64_t off, size;
+};
+void pair_rdm(const std::vector<PsiBlockRef> &blocks, const double *psi, double rho[256]);
+// Von Neumann entropies -sum x ln x of the trace-normalised one-orbital
+// matrices of the left and right site (diagonal: the four site states differ
+// in (n_up, n_dn)) and of the two-orbital matrix: out = {s_left, s_right, s_pair}.
+void orbital_entropies(const double rho[256], double out[3]);
+// Eigenvalues of a small symmetric matrix (n <= 16, row-major) by cyclic Jacobi rotations.
+void small_symmetric_eigenvalues(int n, const double *a, double *ev);
+
 }  // namespace dmrg

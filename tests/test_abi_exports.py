@@ -56,6 +56,7 @@ def test_tune_calls_reject_bad_arguments_without_a_gpu():
     assert lib.dmrg_set_bond_dims(None, 10, 10) == binding.DMRG_EINVAL
     assert b"dmrg_set_bond_dims" in lib.dmrg_last_error()
     assert lib.dmrg_truncation_stats(None, None, None, None, None) == binding.DMRG_EINVAL
+    assert lib.dmrg_orbital_entropies(None, None, None) == binding.DMRG_EINVAL
 
 
 def test_init_rejects_bad_problems_without_a_gpu():
