@@ -211,6 +211,23 @@ int dmrg_truncation_stats(dmrg_ctx *ctx, double *last_gap, double *min_gap, long
                           long long *straddled);
 
 /*
+ * dmrg_block_basis -- export the renormalization matrix O of a stored block
+ * (Eq. renorm): the MPS tensor of the block's outermost site (Sec. 2.1, the
+ * MPS matrices are the reshaped renormalization matrices).  side 0: the left
+ * block of `sites` sites (0..sites-1), made from the left block of sites-1
+ * sites and site sites-1; side 1: the right block of `sites` sites
+ * (L-sites..L-1), made from site L-sites and the right block of sites-1 sites.
+ * Same format as the input of dmrg_renormalize: per enlarged sector (in the
+ * enlarged-layout order of the header comment) the kept count, and O as the
+ * concatenated row-major dim_E x kept_E matrices.  Outputs (host, each may be
+ * NULL): *nsec enlarged sectors, kept (nsec ints), O (*nO doubles), *nO.
+ * Chaining the exported O of blocks 1..n rebuilds the block's basis states
+ * in the product basis of its sites.  Errors: DMRG_EINVAL (bad arguments),
+ * DMRG_ESTATE (no stored basis for that block, e.g. never built or released).
+ */
+int dmrg_block_basis(dmrg_ctx *ctx, int side, int sites, int *nsec, int *kept, double *O, long long *nO);
+
+/*
  * dmrg_orbital_entropies -- one- and two-orbital entropies of the current
  * two-site wave function (Eq. wf_sec) at its two sites k and k+1.  The
  * two-orbital reduced density matrix over the site-state pairs (b, c) of the

@@ -74,6 +74,7 @@ def lib():
         "dmrg_get_tune": (C.c_int, [vp, dp]),
         "dmrg_truncation_stats": (C.c_int, [vp, dp, dp, llp, llp]),
         "dmrg_orbital_entropies": (C.c_int, [vp, dp, dp]),
+        "dmrg_block_basis": (C.c_int, [vp, C.c_int, C.c_int, ip, ip, dp, llp]),
         "dmrg_debug_pair_rdm": (C.c_int, [C.c_int, ip, llp, dp, dp, dp]),
         "dmrg_debug_truncation": (C.c_int, [C.c_int, ip, dp, C.c_int, ip, ip, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
@@ -399,6 +400,17 @@ class DMRG:
         par = np.zeros(5)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
+
+    def block_basis(self, side, sites):
+        """(kept per enlarged sector, flat O) of the stored left (0) / right (1) block of `sites`
+        sites, in the format dmrg_renormalize takes."""
+        n, tot = C.c_int(), C.c_longlong()
+        _check(lib().dmrg_block_basis(self.ctx, int(side), int(sites), C.byref(n), None, None, C.byref(tot)))
+        kept = np.zeros(max(n.value, 1), dtype=np.int32)
+        O = np.zeros(max(tot.value, 1))
+        _check(lib().dmrg_block_basis(self.ctx, int(side), int(sites), C.byref(n), _iptr(kept), _dptr(O),
+                                      C.byref(tot)))
+        return kept[:n.value], O[:tot.value]
 
     def orbital_entropies(self):
         """Entropies of the two sites of the current wave function (k and k+1): dict with

@@ -3212,6 +3212,28 @@ extern "C" int dmrg_truncation_stats(dmrg_ctx *c, double *last_gap, double *min_
   API_END
 }
 
+extern "C" int dmrg_block_basis(dmrg_ctx *c, int side, int sites, int *nsec, int *kept, double *O,
+                                long long *nO) {
+  API_BEGIN
+  if (!c || (side != 0 && side != 1) || sites < 1) throw Fail{DMRG_EINVAL, "dmrg_block_basis: bad arguments"};
+  const auto &store = side == 0 ? c->left : c->right;
+  const DevBlock *b = sites < (int)store.size() ? store[(size_t)sites].get() : nullptr;
+  if (!b || b->parent.empty() || b->kept.size() != b->parent.size())
+    throw Fail{DMRG_ESTATE, "dmrg_block_basis: no stored basis for that block"};
+  int64_t total = 0;
+  for (size_t e = 0; e < b->parent.size(); ++e) total += (int64_t)b->parent[e].dim * b->kept[e];
+  if (nsec) *nsec = (int)b->parent.size();
+  if (nO) *nO = (long long)total;
+  if (kept)
+    for (size_t e = 0; e < b->kept.size(); ++e) kept[e] = b->kept[e];
+  if (O && total > 0) {
+    if (!b->O.p || b->O.n < (size_t)total) throw Fail{DMRG_ESTATE, "dmrg_block_basis: basis not resident"};
+    CK(cudaMemcpyAsync(O, b->O.p, (size_t)total * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CK(cudaStreamSynchronize(c->stream));
+  }
+  API_END
+}
+
 extern "C" int dmrg_orbital_entropies(dmrg_ctx *c, double *s3, double *rho2) {
   API_BEGIN
   if (!c || (!s3 && !rho2)) throw Fail{DMRG_EINVAL, "NULL argument"};

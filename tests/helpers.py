@@ -65,3 +65,22 @@ def build_random_position(ctx, h, v, k, M, seed=0, left_M=None, right_M=None):
         rb = ob.grow_right(rb, s, {E: b for E, b in zip(lay, blocks)})
     ctx.set_position(k, 1)
     return lb, rb
+
+
+def rebuild_blocks(exports, L, side, n_sites):
+    """Explicit-basis block (oracle/blocks.py) of n_sites sites rebuilt from exported
+    renormalization matrices: exports[j] = (kept per enlarged sector, flat O) of the
+    block of j sites, in the format dmrg_renormalize takes (dmrg_block_basis)."""
+    blk = ob.empty_block()
+    for j in range(1, n_sites + 1):
+        kept, O = exports[j]
+        lay = ob.enlarged_left(blk) if side == 0 else ob.enlarged_right(blk)
+        dims = [ob.enlarged_dims(lay)[E] for E in lay]
+        assert len(kept) == len(lay)
+        blocks, pos = {}, 0
+        for E, d, m in zip(lay, dims, kept):
+            blocks[E] = np.asarray(O[pos:pos + d * m]).reshape(d, m)
+            pos += d * m
+        assert pos == len(O)
+        blk = ob.grow_left(blk, j - 1, blocks) if side == 0 else ob.grow_right(blk, L - j, blocks)
+    return blk

@@ -97,3 +97,30 @@ def test_library_pair_rdm_rejects_inconsistent_blocks():
         binding.debug_pair_rdm(layout, np.ones(6))
     with pytest.raises(binding.DMRGError):
         binding.debug_pair_rdm(np.array([[0, 4, 0, 0, 1, 1, 0]]), np.ones(1))
+
+
+def test_basis_export_format_rebuilds_the_blocks():
+    """Chained renormalization matrices in the dmrg_renormalize / dmrg_block_basis format
+    rebuild the explicit block bases (the MPS tensors of the sites, Sec. 2.1)."""
+    from tests.helpers import rebuild_blocks
+    L, k, M = 7, 3, 10
+    rng = np.random.default_rng(4)
+    exports = {0: {}, 1: {}}
+    lb = ob.empty_block()
+    for s in range(k):
+        lay = ob.enlarged_left(lb)
+        kept, blocks, flat = random_O([ob.enlarged_dims(lay)[E] for E in lay], M, rng)
+        exports[0][s + 1] = (kept, flat)
+        lb = ob.grow_left(lb, s, {E: b for E, b in zip(lay, blocks)})
+    rb = ob.empty_block()
+    for j, s in enumerate(range(L - 1, k + 1, -1), start=1):
+        lay = ob.enlarged_right(rb)
+        kept, blocks, flat = random_O([ob.enlarged_dims(lay)[E] for E in lay], M, rng)
+        exports[1][j] = (kept, flat)
+        rb = ob.grow_right(rb, s, {E: b for E, b in zip(lay, blocks)})
+    lb2 = rebuild_blocks(exports[0], L, 0, k)
+    rb2 = rebuild_blocks(exports[1], L, 1, L - k - 2)
+    for a, b in ((lb, lb2), (rb, rb2)):
+        assert a.sectors == b.sectors and a.dims == b.dims
+        for E in a.sectors:
+            assert np.array_equal(a.V[E], b.V[E])
