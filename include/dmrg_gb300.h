@@ -255,6 +255,17 @@ int dmrg_orbital_entropies(dmrg_ctx *ctx, double *s3, double *rho2);
 int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
 
 /*
+ * dmrg_sweep_record -- dmrg_sweep with per-step records (each output host,
+ * may be NULL, one slot per Davidson step in sweep order): energies, the
+ * discarded weight of the step's truncation (dmrg_renormalize), and entropies
+ * (3 per step: one-orbital entropies of the step's two sites k, k+1 and
+ * their two-orbital entropy, as dmrg_orbital_entropies after the step's
+ * Davidson).  Over one sweep every site and every adjacent pair appears.
+ */
+int dmrg_sweep_record(dmrg_ctx *ctx, int nsweeps, double tol, double *energies, double *discarded,
+                      double *entropies);
+
+/*
  * dmrg_set_bond_dims -- asymmetric bond dimensions: later RDM truncations of
  * dmrg_renormalize keep at most m_forward states in new left blocks
  * (direction +1) and m_backward in new right blocks (direction -1), e.g. the

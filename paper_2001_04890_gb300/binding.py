@@ -75,6 +75,7 @@ def lib():
         "dmrg_truncation_stats": (C.c_int, [vp, dp, dp, llp, llp]),
         "dmrg_orbital_entropies": (C.c_int, [vp, dp, dp]),
         "dmrg_block_basis": (C.c_int, [vp, C.c_int, C.c_int, ip, ip, dp, llp]),
+        "dmrg_sweep_record": (C.c_int, [vp, C.c_int, C.c_double, dp, dp, dp]),
         "dmrg_debug_pair_rdm": (C.c_int, [C.c_int, ip, llp, dp, dp, dp]),
         "dmrg_debug_truncation": (C.c_int, [C.c_int, ip, dp, C.c_int, ip, ip, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
@@ -372,6 +373,14 @@ class DMRG:
         e = np.zeros(nsweeps * 2 * (self.L - 2))
         _check(lib().dmrg_sweep(self.ctx, nsweeps, tol, _dptr(e)))
         return e
+
+    def sweep_record(self, nsweeps, tol=1e-9):
+        """Sweeps with per-step records: dict of energies, discarded weights and entropies
+        (steps x 3: s_k, s_k+1, s_pair of the step's two sites)."""
+        n = nsweeps * 2 * (self.L - 2)
+        e, dw, ent = np.zeros(n), np.zeros(n), np.zeros(3 * n)
+        _check(lib().dmrg_sweep_record(self.ctx, nsweeps, tol, _dptr(e), _dptr(dw), _dptr(ent)))
+        return dict(energies=e, discarded=dw, entropies=ent.reshape(n, 3))
 
     def stats(self, reset=False):
         ms, calls, fl, launches, dav = C.c_double(), C.c_longlong(), C.c_double(), C.c_longlong(), C.c_longlong()

@@ -2474,34 +2474,50 @@ extern "C" int dmrg_renormalize(dmrg_ctx *c, int direction, const int *kept, con
   API_END
 }
 
-extern "C" int dmrg_sweep(dmrg_ctx *c, int nsweeps, double tol, double *energies) {
-  API_BEGIN
-  if (!c || nsweeps < 0 || !(tol > 0.0)) throw Fail{DMRG_EINVAL, "bad arguments"};
-  if (c->L < 3) throw Fail{DMRG_EINVAL, "sweeps need L >= 3"};
+// The two-site entropies of the current wave function (host copy of psi).
+static void current_entropies(dmrg_ctx *c, double s3[3], double *rho2);
+
+// Sweeps (Sec. 2.1): forward over positions 0..L-3, backward over L-2..1, a
+// Davidson step then a truncation + renormalization at each.  Per step j
+// (optional records): energies[j], the discarded weight of its truncation,
+// and the entropies of the step's two sites {s_k, s_k+1, s_pair}.
+static void sweep_impl(dmrg_ctx *c, int nsweeps, double tol, double *energies, double *discarded,
+                       double *entropies) {
   c->k = 0;
   c->dir = 1;
   c->plan.valid = false;
   int idx = 0;
+  auto step = [&](int direction) {
+    double e, dw = 0.0;
+    int it;
+    bool conv;
+    davidson(c, tol, 200, &e, &it, conv);
+    if (energies) energies[idx] = e;
+    if (entropies) current_entropies(c, entropies + 3 * idx, nullptr);
+    do_renormalize(c, direction, nullptr, nullptr, &dw, nullptr);
+    if (discarded) discarded[idx] = dw;
+    ++idx;
+  };
   for (int sw = 0; sw < nsweeps; ++sw) {
-    for (int k = 0; k <= c->L - 3; ++k) {
-      double e;
-      int it;
-      bool conv;
-      davidson(c, tol, 200, &e, &it, conv);
-      if (energies) energies[idx] = e;
-      ++idx;
-      do_renormalize(c, +1, nullptr, nullptr, nullptr, nullptr);
-    }
-    for (int k = c->L - 2; k >= 1; --k) {
-      double e;
-      int it;
-      bool conv;
-      davidson(c, tol, 200, &e, &it, conv);
-      if (energies) energies[idx] = e;
-      ++idx;
-      do_renormalize(c, -1, nullptr, nullptr, nullptr, nullptr);
-    }
+    for (int k = 0; k <= c->L - 3; ++k) step(+1);
+    for (int k = c->L - 2; k >= 1; --k) step(-1);
   }
+}
+
+extern "C" int dmrg_sweep(dmrg_ctx *c, int nsweeps, double tol, double *energies) {
+  API_BEGIN
+  if (!c || nsweeps < 0 || !(tol > 0.0)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  if (c->L < 3) throw Fail{DMRG_EINVAL, "sweeps need L >= 3"};
+  sweep_impl(c, nsweeps, tol, energies, nullptr, nullptr);
+  API_END
+}
+
+extern "C" int dmrg_sweep_record(dmrg_ctx *c, int nsweeps, double tol, double *energies, double *discarded,
+                                 double *entropies) {
+  API_BEGIN
+  if (!c || nsweeps < 0 || !(tol > 0.0)) throw Fail{DMRG_EINVAL, "bad arguments"};
+  if (c->L < 3) throw Fail{DMRG_EINVAL, "sweeps need L >= 3"};
+  sweep_impl(c, nsweeps, tol, energies, discarded, entropies);
   API_END
 }
 
@@ -3234,9 +3250,7 @@ extern "C" int dmrg_block_basis(dmrg_ctx *c, int side, int sites, int *nsec, int
   API_END
 }
 
-extern "C" int dmrg_orbital_entropies(dmrg_ctx *c, double *s3, double *rho2) {
-  API_BEGIN
-  if (!c || (!s3 && !rho2)) throw Fail{DMRG_EINVAL, "NULL argument"};
+static void current_entropies(dmrg_ctx *c, double s3[3], double *rho2) {
   if (!c->psi_valid) throw Fail{DMRG_ESTATE, "no wave function at this position"};
   require_blocks(c);
   const Psi Y = psi_layout(lblock(c)->lay, rblock(c)->lay, c->nu, c->nd);
@@ -3251,6 +3265,12 @@ extern "C" int dmrg_orbital_entropies(dmrg_ctx *c, double *s3, double *rho2) {
   if (rho2)
     for (int i = 0; i < 256; ++i) rho2[i] = rho[i];
   if (s3) orbital_entropies(rho, s3);
+}
+
+extern "C" int dmrg_orbital_entropies(dmrg_ctx *c, double *s3, double *rho2) {
+  API_BEGIN
+  if (!c || (!s3 && !rho2)) throw Fail{DMRG_EINVAL, "NULL argument"};
+  current_entropies(c, s3, rho2);
   API_END
 }
 
