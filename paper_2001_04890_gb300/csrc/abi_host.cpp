@@ -2,6 +2,7 @@
 // introspection (no CUDA calls; usable on a machine without a GPU).
 #include <cstring>
 #include <string>
+#include <utility>
 
 #include "../../include/dmrg_gb300.h"
 #include "plan.hpp"
@@ -41,7 +42,7 @@ extern "C" int dmrg_debug_pieces(int L, const double *h, const double *v, int k,
     }
     auto I = make_integrals(L, h, v);
     auto ps = dmrg::hamiltonian_pieces(I, k, l_empty != 0, r_empty != 0);
-    if (compress) ps = dmrg::compress_pieces(ps);
+    if (compress) ps = dmrg::compress_pieces(std::move(ps));
     return copy_out(dmrg::dump_pieces(ps), buf, buflen, needed);
   } catch (const std::exception &e) {
     dmrg::set_error(e.what());

@@ -270,30 +270,6 @@ static inline int npart(const Sector &s) { return s.nu + s.nd; }
 static inline int nsite(int b) { return SITE_NU[b] + SITE_ND[b]; }
 
 // task list grouped by output block
-// Run fn(i) for i in [0, n) on up to 16 host threads (work handed out one index
-// at a time); the first exception of any worker is rethrown here.
-template <class F>
-static void parallel_for(size_t n, F fn) {
-  std::atomic<size_t> next{0};
-  std::mutex err_mu;
-  std::exception_ptr err;
-  auto worker = [&]() {
-    try {
-      for (size_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
-    } catch (...) {
-      std::lock_guard<std::mutex> lk(err_mu);
-      if (!err) err = std::current_exception();
-      next.store(n);
-    }
-  };
-  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
-  std::vector<std::thread> pool;
-  for (unsigned t = 1; t < hw && t < n; ++t) pool.emplace_back(worker);
-  worker();
-  for (auto &th : pool) th.join();
-  if (err) std::rethrow_exception(err);
-}
-
 struct ChainList {
   using Keyed = std::vector<std::pair<int, ChainEntry>>;  // (group key, entry)
   Keyed ent;                    // entries in build order

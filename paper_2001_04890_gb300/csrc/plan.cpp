@@ -7,10 +7,12 @@
 #include <cstdio>
 #include <cstring>
 #include <functional>
+#include <iterator>
 #include <limits>
 #include <sstream>
 #include <stdexcept>
 #include <unordered_map>
+#include <utility>
 
 namespace dmrg {
 
@@ -588,23 +590,33 @@ std::vector<Piece> hamiltonian_pieces(const Integrals &I, int k, bool l_empty, b
   for (int j = lp_end; j < 2 * L; ++j) product(ps, O.L_T(j), O.R_c(j), 1.0, true);
   for (int i = 0; i < lp_end; ++i) product(ps, O.L_C(i), O.R_V(i), 1.0, true);
   const bool normal_on_left = (k + 1) <= (L - k - 1);
+  // the pair terms, one row of pair indices per task, appended in row order
+  auto rows = [&](int lo, int hi, auto &&row) {
+    std::vector<std::vector<Piece>> part((size_t)(hi - lo));
+    parallel_for(part.size(), [&](size_t i) { row((int)i + lo, part[i]); });
+    for (auto &v : part) ps.insert(ps.end(), std::make_move_iterator(v.begin()), std::make_move_iterator(v.end()));
+  };
   if (normal_on_left) {
-    for (int p = 0; p < lp_end; ++p)
-      for (int q = p + 1; q < lp_end; ++q) product(ps, O.L_A(p, q), O.R_Pa(p, q), 1.0, true);
-    for (int p = 0; p < lp_end; ++p)
-      for (int s = 0; s < lp_end; ++s) product(ps, O.L_B(p, s), O.R_Q(p, s), 1.0, false);
+    rows(0, lp_end, [&](int p, std::vector<Piece> &out) {
+      for (int q = p + 1; q < lp_end; ++q) product(out, O.L_A(p, q), O.R_Pa(p, q), 1.0, true);
+    });
+    rows(0, lp_end, [&](int p, std::vector<Piece> &out) {
+      for (int s = 0; s < lp_end; ++s) product(out, O.L_B(p, s), O.R_Q(p, s), 1.0, false);
+    });
   } else {
-    for (int r = lp_end; r < 2 * L; ++r)
-      for (int s = r + 1; s < 2 * L; ++s) product(ps, O.L_Pc(r, s), O.R_AT(r, s), 1.0, true);
-    for (int q = lp_end; q < 2 * L; ++q)
-      for (int r = lp_end; r < 2 * L; ++r) product(ps, O.L_Q(q, r), O.R_B(q, r), 1.0, false);
+    rows(lp_end, 2 * L, [&](int r, std::vector<Piece> &out) {
+      for (int s = r + 1; s < 2 * L; ++s) product(out, O.L_Pc(r, s), O.R_AT(r, s), 1.0, true);
+    });
+    rows(lp_end, 2 * L, [&](int q, std::vector<Piece> &out) {
+      for (int r = lp_end; r < 2 * L; ++r) product(out, O.L_Q(q, r), O.R_B(q, r), 1.0, false);
+    });
   }
   // drop pieces on operators of empty blocks (all zero there)
   std::vector<Piece> out;
   for (auto &p : ps) {
     if (l_empty && p.l.type != 0) continue;
     if (r_empty && p.r.type != 0) continue;
-    out.push_back(p);
+    out.push_back(std::move(p));
   }
   return out;
 }
@@ -665,7 +677,7 @@ struct MergeKeyEq {
 };
 
 // side 0: merge the left operators of pieces sharing the exact right operator.
-static std::vector<Piece> compress_side(const std::vector<Piece> &in, int side) {
+static std::vector<Piece> compress_side(std::vector<Piece> in, int side) {
   std::unordered_map<MergeKey, int, MergeKeyHash, MergeKeyEq> index;
   std::vector<std::vector<int>> groups;  // in order of first appearance
   for (int i = 0; i < (int)in.size(); ++i) {
@@ -693,93 +705,112 @@ static std::vector<Piece> compress_side(const std::vector<Piece> &in, int side) 
       groups[it->second].push_back(i);
     }
   }
-  std::vector<Piece> out;
   // Merged sources per elementary site pair, accumulated in dense arrays over
   // the source index (i + 1, j + 1): every source receives its contributions
   // in the order of the pieces, and both the site pairs and the sources come
-  // out in ascending order.  Buffers are reused across groups.
+  // out in ascending order.  Groups are independent: chunks of them run in
+  // parallel, each thread reusing its own buffers, and the outputs are joined
+  // in group order.
+  const size_t CD = 256;
+  std::vector<int> dmax((in.size() + CD - 1) / CD, 2);
+  parallel_for(dmax.size(), [&](size_t ch) {
+    int m = 2;
+    for (size_t i = ch * CD; i < std::min(in.size(), (ch + 1) * CD); ++i)
+      for (const OpRef *o : {&in[i].l, &in[i].r}) {
+        m = std::max(m, std::max(o->i, o->j) + 2);
+        for (const auto &t : o->lc) m = std::max(m, std::max(std::get<0>(t), std::get<1>(t)) + 2);
+      }
+    dmax[ch] = m;
+  });
   int D = 2;
-  for (const auto &p : in)
-    for (const OpRef *o : {&p.l, &p.r}) {
-      D = std::max(D, std::max(o->i, o->j) + 2);
-      for (const auto &t : o->lc) D = std::max(D, std::max(std::get<0>(t), std::get<1>(t)) + 2);
-    }
+  for (int m : dmax) D = std::max(D, m);
   struct Acc {
     std::vector<double> val;
     std::vector<char> used;
     std::vector<int> touched;
   };
-  std::vector<Acc> pool;
-  std::vector<int> slot_of(256, -1), pairs;
-  for (auto &g : groups) {
-    if (g.size() == 1) { out.push_back(in[g[0]]); continue; }
-    pairs.clear();
-    for (int i : g) {
-      const Piece &p = in[i];
-      const OpRef &var = side == 0 ? p.l : p.r;
-      for (int e1 = 0; e1 < 16; ++e1) {
-        if (p.sl[e1] == 0.0) continue;
-        for (int e2 = 0; e2 < 16; ++e2) {
-          if (p.sr[e2] == 0.0) continue;
-          const int pe = e1 * 16 + e2;
-          if (slot_of[pe] < 0) {
-            slot_of[pe] = (int)pairs.size();
-            pairs.push_back(pe);
-            if (pool.size() < pairs.size()) pool.emplace_back();
+  std::vector<std::vector<Piece>> gout(groups.size());
+  const size_t CH = 64;
+  parallel_for((groups.size() + CH - 1) / CH, [&](size_t ch) {
+    thread_local std::vector<Acc> pool;
+    thread_local std::vector<int> slot_of, pairs;
+    if (slot_of.size() != 256) slot_of.assign(256, -1);
+    for (size_t gi = ch * CH; gi < std::min(groups.size(), (ch + 1) * CH); ++gi) {
+      const std::vector<int> &g = groups[gi];
+      if (g.size() == 1) {
+        gout[gi].push_back(std::move(in[(size_t)g[0]]));
+        continue;
+      }
+      pairs.clear();
+      for (int i : g) {
+        const Piece &p = in[(size_t)i];
+        const OpRef &var = side == 0 ? p.l : p.r;
+        for (int e1 = 0; e1 < 16; ++e1) {
+          if (p.sl[e1] == 0.0) continue;
+          for (int e2 = 0; e2 < 16; ++e2) {
+            if (p.sr[e2] == 0.0) continue;
+            const int pe = e1 * 16 + e2;
+            if (slot_of[pe] < 0) {
+              slot_of[pe] = (int)pairs.size();
+              pairs.push_back(pe);
+              if (pool.size() < pairs.size()) pool.emplace_back();
+              Acc &a = pool[(size_t)slot_of[pe]];
+              if (a.val.size() < (size_t)D * D) {
+                a.val.assign((size_t)D * D, 0.0);
+                a.used.assign((size_t)D * D, 0);
+              }
+            }
             Acc &a = pool[(size_t)slot_of[pe]];
-            if (a.val.size() < (size_t)D * D) {
-              a.val.assign((size_t)D * D, 0.0);
-              a.used.assign((size_t)D * D, 0);
-            }
+            const double c = p.coef * p.sl[e1] * p.sr[e2];
+            auto add = [&](int si, int sj, double x) {
+              const size_t idx = (size_t)(si + 1) * D + (sj + 1);
+              if (!a.used[idx]) {
+                a.used[idx] = 1;
+                a.val[idx] = 0.0;
+                a.touched.push_back((int)idx);
+              }
+              a.val[idx] += x;
+            };
+            if (var.type == 1) add(var.i, var.j, c);
+            else for (const auto &t : var.lc) add(std::get<0>(t), std::get<1>(t), c * std::get<2>(t));
           }
-          Acc &a = pool[(size_t)slot_of[pe]];
-          const double c = p.coef * p.sl[e1] * p.sr[e2];
-          auto add = [&](int si, int sj, double x) {
-            const size_t idx = (size_t)(si + 1) * D + (sj + 1);
-            if (!a.used[idx]) {
-              a.used[idx] = 1;
-              a.val[idx] = 0.0;
-              a.touched.push_back((int)idx);
-            }
-            a.val[idx] += x;
-          };
-          if (var.type == 1) add(var.i, var.j, c);
-          else for (const auto &t : var.lc) add(std::get<0>(t), std::get<1>(t), c * std::get<2>(t));
         }
       }
-    }
-    const Piece &p0 = in[g[0]];
-    const OpRef &var0 = side == 0 ? p0.l : p0.r;
-    std::sort(pairs.begin(), pairs.end());
-    for (int pe : pairs) {
-      Acc &a = pool[(size_t)slot_of[pe]];
-      slot_of[pe] = -1;
-      std::sort(a.touched.begin(), a.touched.end());
-      std::vector<std::tuple<int, int, double>> lc;
-      for (int idx : a.touched) {
-        a.used[(size_t)idx] = 0;
-        const double x = a.val[(size_t)idx];
-        if (x != 0.0) lc.emplace_back(idx / D - 1, idx % D - 1, x);
+      const Piece &p0 = in[(size_t)g[0]];
+      const OpRef &var0 = side == 0 ? p0.l : p0.r;
+      std::sort(pairs.begin(), pairs.end());
+      for (int pe : pairs) {
+        Acc &a = pool[(size_t)slot_of[pe]];
+        slot_of[pe] = -1;
+        std::sort(a.touched.begin(), a.touched.end());
+        std::vector<std::tuple<int, int, double>> lc;
+        for (int idx : a.touched) {
+          a.used[(size_t)idx] = 0;
+          const double x = a.val[(size_t)idx];
+          if (x != 0.0) lc.emplace_back(idx / D - 1, idx % D - 1, x);
+        }
+        a.touched.clear();
+        if (lc.empty()) continue;
+        Piece q;
+        q.coef = 1.0;
+        q.hc = p0.hc;
+        q.sl = mat_zero();
+        q.sl[pe / 16] = 1.0;
+        q.sr = mat_zero();
+        q.sr[pe % 16] = 1.0;
+        OpRef m = lincomb(var0.kind, var0.tr, lc);
+        if (side == 0) { q.l = m; q.r = p0.r; } else { q.l = p0.l; q.r = m; }
+        gout[gi].push_back(std::move(q));
       }
-      a.touched.clear();
-      if (lc.empty()) continue;
-      Piece q;
-      q.coef = 1.0;
-      q.hc = p0.hc;
-      q.sl = mat_zero();
-      q.sl[pe / 16] = 1.0;
-      q.sr = mat_zero();
-      q.sr[pe % 16] = 1.0;
-      OpRef m = lincomb(var0.kind, var0.tr, lc);
-      if (side == 0) { q.l = m; q.r = p0.r; } else { q.l = p0.l; q.r = m; }
-      out.push_back(q);
     }
-  }
+  });
+  std::vector<Piece> out;
+  for (auto &v : gout) out.insert(out.end(), std::make_move_iterator(v.begin()), std::make_move_iterator(v.end()));
   return out;
 }
 
-std::vector<Piece> compress_pieces(const std::vector<Piece> &in) {
-  return compress_side(compress_side(in, 0), 1);
+std::vector<Piece> compress_pieces(std::vector<Piece> in) {
+  return compress_side(compress_side(std::move(in), 0), 1);
 }
 
 // ---------------------------------------------------------------- new block ops

@@ -18,15 +18,45 @@
 // of Sec. 2.2.1 (one entry per (operator combination, s -> s')).
 #pragma once
 
+#include <algorithm>
 #include <array>
+#include <atomic>
 #include <cstdint>
+#include <exception>
 #include <map>
+#include <mutex>
 #include <string>
+#include <thread>
 #include <tuple>
 #include <unordered_map>
 #include <vector>
 
 namespace dmrg {
+
+// Run fn(i) for i in [0, n) on up to 16 host threads (work handed out one index
+// at a time); the first exception of any worker is rethrown here.
+template <class F>
+inline void parallel_for(size_t n, F fn) {
+  std::atomic<size_t> next{0};
+  std::mutex err_mu;
+  std::exception_ptr err;
+  auto worker = [&]() {
+    try {
+      for (size_t i = next.fetch_add(1); i < n; i = next.fetch_add(1)) fn(i);
+    } catch (...) {
+      std::lock_guard<std::mutex> lk(err_mu);
+      if (!err) err = std::current_exception();
+      next.store(n);
+    }
+  };
+  const unsigned hw = std::max(1u, std::min(16u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> pool;
+  for (unsigned t = 1; t < hw && t < n; ++t) pool.emplace_back(worker);
+  worker();
+  for (auto &th : pool) th.join();
+  if (err) std::rethrow_exception(err);
+}
+
 
 using Mat4 = std::array<double, 16>;  // site matrix, row-major [b'][b]
 
@@ -182,7 +212,7 @@ std::vector<Piece> hamiltonian_pieces(const Integrals &I, int k, bool l_empty, b
 
 // Merge pieces that share one side exactly: sum_u X_u (x) S_u (x) Y = sum_E
 // (sum_u S_u[E] X_u) (x) E (x) Y (a pre-summation, Sec. 2.2.3).
-std::vector<Piece> compress_pieces(const std::vector<Piece> &in);
+std::vector<Piece> compress_pieces(std::vector<Piece> in);
 
 // For the renormalization of the new block (Sec. 2.2.2): the half operator
 // defining each stored operator of the new block, in family order.
