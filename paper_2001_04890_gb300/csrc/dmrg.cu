@@ -1091,14 +1091,24 @@ static std::unique_ptr<DevBlock> empty_block(int side, int L) {
 static std::vector<RPiece> resolve_pieces(const Integrals &I, int k, const BlockLayout &L,
                                           const BlockLayout &R, TempSet &temps) {
   auto pieces = compress_pieces(hamiltonian_pieces(I, k, L.empty(), R.empty()));
+  // linear-combination operators prepared in parallel, then numbered in piece order
+  std::vector<PreparedTemp> pl(pieces.size()), pr(pieces.size());
+  const size_t CH = 64;
+  parallel_for((pieces.size() + CH - 1) / CH, [&](size_t c) {
+    for (size_t i = c * CH; i < std::min(pieces.size(), (c + 1) * CH); ++i) {
+      if (pieces[i].l.type == 2) pl[i] = prepare_temp(L, pieces[i].l);
+      if (pieces[i].r.type == 2) pr[i] = prepare_temp(R, pieces[i].r);
+    }
+  });
   std::vector<RPiece> out;
-  for (auto &p : pieces) {
+  for (size_t i = 0; i < pieces.size(); ++i) {
+    Piece &p = pieces[i];
     bool zl, zr;
-    Ref l = resolve(p.l, 0, L, temps, zl);
+    Ref l = p.l.type == 2 ? temps.make_prepared(0, L, p.l, std::move(pl[i]), zl) : resolve(p.l, 0, L, temps, zl);
     if (zl) continue;
-    Ref r = resolve(p.r, 1, R, temps, zr);
+    Ref r = p.r.type == 2 ? temps.make_prepared(1, R, p.r, std::move(pr[i]), zr) : resolve(p.r, 1, R, temps, zr);
     if (zr) continue;
-    out.push_back({l, r, p});
+    out.push_back({l, r, std::move(p)});
   }
   return out;
 }

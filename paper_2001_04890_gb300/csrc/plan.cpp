@@ -906,19 +906,19 @@ std::string dump_halfop(const HalfOp &h) {
 
 // ---------------------------------------------------------------- resolution
 
-Ref TempSet::make(int side, const BlockLayout &b, const OpRef &op, bool &zero) {
-  zero = false;
-  std::vector<std::pair<int, double>> m;
+PreparedTemp prepare_temp(const BlockLayout &b, const OpRef &op) {
+  PreparedTemp pt;
+  std::vector<std::pair<int, double>> &m = pt.m;
   m.reserve(op.lc.size());
-  int fam = -1;
   for (auto &t : op.lc) {
     int f, kk;
     if (!b.get(op.kind, std::get<0>(t), std::get<1>(t), f, kk)) continue;
-    if (fam < 0) fam = f;
-    if (f != fam) throw std::runtime_error("linear combination spans operator families");
+    if (pt.fam < 0) pt.fam = f;
+    if (f != pt.fam) throw std::runtime_error("linear combination spans operator families");
     m.emplace_back(kk, std::get<2>(t));
   }
-  if (m.empty()) { zero = true; return Ref(); }
+  if (m.empty()) return pt;
+  pt.zero = false;
   // sources in (operator, coefficient) order, duplicates summed in that order
   if (!std::is_sorted(m.begin(), m.end())) std::sort(m.begin(), m.end());
   size_t w = 0;
@@ -927,6 +927,25 @@ Ref TempSet::make(int side, const BlockLayout &b, const OpRef &op, bool &zero) {
     else m[w++] = m[r];
   }
   m.resize(w);
+  uint64_t h = 0x243f6a8885a308d3ull;
+  for (auto &x : m) {
+    uint64_t bits;
+    std::memcpy(&bits, &x.second, 8);
+    h ^= (uint64_t)x.first + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+    h ^= bits + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
+  }
+  pt.hash = h;
+  return pt;
+}
+
+Ref TempSet::make(int side, const BlockLayout &b, const OpRef &op, bool &zero) {
+  return make_prepared(side, b, op, prepare_temp(b, op), zero);
+}
+
+Ref TempSet::make_prepared(int side, const BlockLayout &b, const OpRef &op, PreparedTemp &&pt, bool &zero) {
+  zero = pt.zero;
+  if (pt.zero) return Ref();
+  const int fam = pt.fam;
   auto fk = std::make_tuple(side, fam, op.tr);
   int tf;
   auto it = fam_of[side].find(fk);
@@ -952,46 +971,33 @@ Ref TempSet::make(int side, const BlockLayout &b, const OpRef &op, bool &zero) {
     std::memcpy(&c, &y, 8);
     return a == c;
   };
-  uint64_t h = 0x243f6a8885a308d3ull ^ ((uint64_t)tf << 1) ^ (uint64_t)op.tr;
-  for (auto &x : m) {
-    uint64_t bits;
-    std::memcpy(&bits, &x.second, 8);
-    h ^= (uint64_t)x.first + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
-    h ^= bits + 0x9e3779b97f4a7c15ull + (h << 6) + (h >> 2);
-  }
+  const std::vector<std::pair<int, double>> &m = pt.m;
+  const uint64_t h = pt.hash ^ (((uint64_t)tf << 1) | (uint64_t)op.tr) * 0x9e3779b97f4a7c15ull;
   TempFamily &T = this->fam[side][tf];
   auto &cands = dedup[side][h];
+  auto ref = [&](int kk) {
+    Ref r;
+    r.arena = 2 + side;
+    r.fam = tf;
+    r.k = kk;
+    r.tr = false;
+    r.dnu = T.dnu;
+    r.dnd = T.dnd;
+    r.par = (r.dnu + r.dnd) & 1;
+    return r;
+  };
   for (const auto &cand : cands) {
     if (cand.first != tf) continue;
-    const int kk = cand.second;
-    const auto &c = T.coefs[(size_t)kk];
+    const auto &c = T.coefs[(size_t)cand.second];
     if (c.size() != m.size()) continue;
     bool eq = true;
     for (size_t i = 0; eq && i < m.size(); ++i) eq = c[i].first == m[i].first && same_bits(c[i].second, m[i].second);
-    if (eq) {
-      Ref r;
-      r.arena = 2 + side;
-      r.fam = tf;
-      r.k = kk;
-      r.tr = false;
-      r.dnu = T.dnu;
-      r.dnd = T.dnd;
-      r.par = (r.dnu + r.dnd) & 1;
-      return r;
-    }
+    if (eq) return ref(cand.second);
   }
   const int kk = T.K();
-  T.coefs.push_back(std::move(m));
+  T.coefs.push_back(std::move(pt.m));
   cands.push_back({tf, kk});
-  Ref r;
-  r.arena = 2 + side;
-  r.fam = tf;
-  r.k = kk;
-  r.tr = false;
-  r.dnu = T.dnu;
-  r.dnd = T.dnd;
-  r.par = (r.dnu + r.dnd) & 1;
-  return r;
+  return ref(kk);
 }
 
 void TempSet::layout(const BlockLayout *blocks[2]) {

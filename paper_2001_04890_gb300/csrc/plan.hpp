@@ -253,12 +253,24 @@ struct Ref {
   int dnu = 0, dnd = 0, par = 0;
 };
 
+// The sources of a linear-combination operator on a block, resolved to stored
+// operators of one family, sorted, duplicates merged (prepare_temp: pure, so
+// many can be prepared in parallel before TempSet numbers them in order).
+struct PreparedTemp {
+  bool zero = true;
+  int fam = -1;
+  std::vector<std::pair<int, double>> m;
+  uint64_t hash = 0;
+};
+PreparedTemp prepare_temp(const BlockLayout &b, const OpRef &op);
+
 struct TempSet {
   std::vector<TempFamily> fam[2];
   std::map<std::tuple<int, int, bool>, int> fam_of[2];
   std::unordered_map<uint64_t, std::vector<std::pair<int, int>>> dedup[2];  // hash -> (family, temp)
   int64_t total[2] = {0, 0};
   Ref make(int side, const BlockLayout &b, const OpRef &op, bool &zero);
+  Ref make_prepared(int side, const BlockLayout &b, const OpRef &op, PreparedTemp &&pt, bool &zero);
   void layout(const BlockLayout *blocks[2]);
 };
 
