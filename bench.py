@@ -155,7 +155,11 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
     elif getattr(args, "autotune", False):
         tune_ms, tune = ctx.autotune(reps=2)  # plan-time choice of the launch shape (untimed)
     blocks, dim = ctx.psi_layout()
-    flops_per_hpsi, ntasks = ctx.hpsi_flops()
+    if tune is not None:
+        ctx.set_tune(**tune)  # same shape; drops the plan so that one build of it is timed here
+    t_plan = time.perf_counter()
+    flops_per_hpsi, ntasks = ctx.hpsi_flops()  # builds the position's H.psi plan (host lists + upload)
+    plan_s = time.perf_counter() - t_plan
     psi0_host = workloads.gaussian(dim, seed=1)
     psi0_host /= np.linalg.norm(psi0_host)
     with torch.cuda.stream(stream):
@@ -223,7 +227,7 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
     psi_mid = ctx.get_psi()
     step_ms_max = max_over_ranks(step_ms, f"cuda:{dev}")
     ctx.close()
-    return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st,
+    return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st, plan_s=plan_s,
                 step_ms=step_ms_max, iters=iters, energy=energy, e2e_ms=e2e_ms, tune=tune,
                 h2d=psi0_host.nbytes, d2h=d2h_bytes, clocks=clocks, k=k, e_mid=e_mid, psi_mid=psi_mid)
 
@@ -606,6 +610,7 @@ def main():
         "davidson_iters_per_step": dav_iters / K,
         "hpsi_kernel_tflops": kernel_tflops,
         "hpsi_gflop_per_call": r["flops_per_hpsi"] / 1e9,
+        "hpsi_plan_s": r["plan_s"],
         "energy": r["energy"],
         "roofline": {
             "bound": "alu",
@@ -638,6 +643,7 @@ def main():
                 "davidson_iters_per_step": ms["davidson_iters"] / K,
                 "lowp_matvec_iters_per_step": ms["davidson_iters_lowp"] / K,
                 "launch_shape": m["tune"],
+                "hpsi_plan_s": m["plan_s"],
                 "abs_dE_vs_fp64": abs(m["e_mid"] - r["e_mid"]),
                 "overlap_vs_fp64": float(abs(np.dot(m["psi_mid"], r["psi_mid"]))),
                 "energy": m["e_mid"],
