@@ -90,7 +90,8 @@ int dmrg_free(dmrg_ctx *ctx);
  */
 int dmrg_set_position(dmrg_ctx *ctx, int k, int direction);
 
-/* Current position (k) and the left/right block sizes (host ints; any may be NULL). */
+/* Current position k and the recorded sweep direction (+1 / -1); host ints, each may be
+ * NULL.  DMRG_EINVAL for a NULL context. */
 int dmrg_get_position(dmrg_ctx *ctx, int *k, int *direction);
 
 /*
@@ -184,7 +185,8 @@ int dmrg_davidson(dmrg_ctx *ctx, double tol, int max_iter, double *energy, int *
  * direction -1: new right block r' = s_r (x) r, position k -> k-1.
  * If O is NULL the basis is the kept eigenvectors of rho^L = psi psi^T
  * (rho^R = psi^T psi) of the current psi: the M largest eigenvalues over all
- * sectors, ties broken by (sector order, in-sector order), eigenvalues
+ * sectors (or the per-direction limits of dmrg_set_bond_dims), ties broken by
+ * (sector order, in-sector order), eigenvalues
  * <= 1e-13 never kept; kept (may be NULL) receives the per-sector counts.
  * Otherwise kept (host, one int per enlarged sector) and O (host, layout in
  * the header comment) define the new basis; the caller guarantees
@@ -250,7 +252,10 @@ int dmrg_orbital_entropies(dmrg_ctx *ctx, double *s3, double *rho2);
  * over positions 0..L-3 (Davidson then dmrg_renormalize(+1)), backward over
  * L-2..1 (Davidson then dmrg_renormalize(-1)).  Starts from position 0 in the
  * forward direction.  energies (host, may be NULL) receives one energy per
- * Davidson step: nsweeps * 2 * (L - 2) values.
+ * Davidson step: nsweeps * 2 * (L - 2) values.  Each step runs Davidson to tol
+ * with at most 200 matvecs; a step that does not converge keeps its last Ritz
+ * pair and the sweep goes on.  Errors: DMRG_EINVAL (NULL context, nsweeps < 0,
+ * tol <= 0, L < 3), else those of dmrg_davidson and dmrg_renormalize.
  */
 int dmrg_sweep(dmrg_ctx *ctx, int nsweeps, double tol, double *energies);
 
