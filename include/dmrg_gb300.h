@@ -319,6 +319,14 @@ int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, 
  * not change position while the batch lives.  dmrg_batch_layout gives the n+1
  * offsets of each instance's psi in the concatenated vector (dmrg_psi_layout
  * order inside) and the summed algorithmic FLOPs of one batched H.psi.
+ * dmrg_batch_hpsi: psi and sigma of the concatenated length, device pointers
+ * on the shared stream (device_ptrs != 0) or host pointers (copied in and
+ * out); sigma is written, not accumulated.  The batch does not own the
+ * contexts: free the batch first.  Errors: DMRG_EINVAL (n < 1, NULL
+ * arguments, contexts on different streams or precision classes),
+ * DMRG_ESTATE (a context without the blocks of its position),
+ * DMRG_ETIMEOUT (a bounded tensor-core wait ran out; that call's sigma is
+ * invalid), DMRG_ENOMEM / DMRG_ECUDA.
  */
 typedef struct dmrg_batch dmrg_batch;
 int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out);
