@@ -189,3 +189,37 @@ def test_grouped_task_list_is_a_stable_sort_by_output_block(layout):
     order = np.argsort(T0[:, 0], kind="stable")
     assert np.array_equal(T1, T0[order])
     assert np.all(np.diff(T1[:, 0]) >= 0)
+
+
+@pytest.mark.parametrize("seed", range(12))
+def test_grouped_task_list_on_random_layouts(seed):
+    """Random sector tables (dims 1..6, random fillings and spins): the two-pass grouped
+    expansion the GPU path uses equals the stable grouping of the build-order list, and
+    its FLOP count equals the dump's."""
+    import numpy as np
+    from paper_2001_04890_gb300 import binding, workloads
+    rng = np.random.default_rng(100 + seed)
+    L = int(rng.integers(5, 10))
+    k = int(rng.integers(0, L - 1))
+    N = int(rng.integers(1, 2 * L))
+    tsz = int(rng.choice([x for x in range(-N, N + 1, 2) if abs(x) <= N and (N - x) // 2 <= L and (N + x) // 2 <= L]))
+
+    def table(n_sites):
+        if n_sites == 0:
+            return [(0, 0, 1)]
+        out = []
+        for a in range(0, n_sites + 1):
+            for b in range(0, n_sites + 1):
+                if rng.random() < 0.6:
+                    out.append((a, b, int(rng.integers(1, 7))))
+        return out or [(0, 0, 1)]
+    sec_l, sec_r = table(k), table(L - k - 2)
+    h, v = workloads.integrals(L, seed=seed)
+    T0 = binding.debug_tasks(h, v, N, tsz, k, sec_l, sec_r)
+    T1 = binding.debug_tasks(h, v, N, tsz, k, sec_l, sec_r, grouped=True)
+    assert T1.shape == T0.shape
+    if len(T0):
+        order = np.argsort(T0[:, 0], kind="stable")
+        assert np.array_equal(T1, T0[order])
+    f, n = binding.plan_hpsi_flops(h, v, N, tsz, k, sec_l, sec_r)
+    assert n == len(T0)
