@@ -41,10 +41,38 @@ def test_execution_plan_runs_every_task_once(case, tune, tc):
     L, N, tsz, M, k = case
     sl, sr = _tables(L, N, tsz, M, k)
     h, v = workloads.integrals(L, seed=0)
+    _check_plan(h, v, N, tsz, k, sl, sr, tc, tune)
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_execution_plan_on_random_layouts(seed):
+    rng = np.random.default_rng(200 + seed)
+    L = int(rng.integers(5, 9))
+    k = int(rng.integers(0, L - 1))
+    N = int(rng.integers(2, 2 * L - 1))
+    tsz = int(rng.choice([x for x in range(-N, N + 1, 2) if (N - x) // 2 <= L and (N + x) // 2 <= L]))
+
+    def table(n_sites):
+        if n_sites == 0:
+            return [(0, 0, 1)]
+        out = [(a, b, int(rng.integers(1, 40))) for a in range(n_sites + 1) for b in range(n_sites + 1)
+               if rng.random() < 0.7]
+        return out or [(0, 0, 1)]
+    sl, sr = table(k), table(L - k - 2)
+    h, v = workloads.integrals(L, seed=seed)
+    for tc in (False, True):
+        for tune in (None, [64.0, 0.0, 9, 1]):
+            _check_plan(h, v, N, tsz, k, sl, sr, tc, tune)
+
+
+def _check_plan(h, v, N, tsz, k, sl, sr, tc, tune):
     tasks = binding.debug_tasks(h, v, N, tsz, k, sl, sr, grouped=True)
     cnt, xs, ch, red = binding.debug_exec(h, v, N, tsz, k, sl, sr, tensor_cores=tc, tune=tune)
     target, min_chunk, tc_min, by_work = (8192.0, 2e5, 33, 0) if tune is None else tune
     assert cnt["entries"] == len(tasks) == len(xs)
+    if len(tasks) == 0:
+        assert len(ch) == 0 and len(red) == 0
+        return
 
     # output blocks in grouped order, each with its tasks
     blocks = []
