@@ -28,9 +28,35 @@ def test_tensor_core_plan(case, tune):
     L, N, tsz, M, k = case
     sl, sr = _tables(*case)
     h, v = workloads.integrals(L, seed=0)
+    assert _check_tc(h, v, N, tsz, k, sl, sr, tune) > 0
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_tensor_core_plan_on_random_layouts(seed):
+    rng = np.random.default_rng(300 + seed)
+    L = int(rng.integers(5, 9))
+    k = int(rng.integers(0, L - 1))
+    N = int(rng.integers(2, 2 * L - 1))
+    tsz = int(rng.choice([x for x in range(-N, N + 1, 2) if (N - x) // 2 <= L and (N + x) // 2 <= L]))
+
+    def table(n_sites):
+        if n_sites == 0:
+            return [(0, 0, 1)]
+        out = [(a, b, int(rng.integers(1, 90))) for a in range(n_sites + 1) for b in range(n_sites + 1)
+               if rng.random() < 0.7]
+        return out or [(0, 0, 1)]
+    sl, sr = table(k), table(L - k - 2)
+    h, v = workloads.integrals(L, seed=seed)
+    for tune in ([8192.0, 2e5, 1, 0], [64.0, 0.0, 17, 1]):
+        _check_tc(h, v, N, tsz, k, sl, sr, tune)
+
+
+def _check_tc(h, v, N, tsz, k, sl, sr, tune):
     cnt, te, tg, ts, ps = binding.debug_tc(h, v, N, tsz, k, sl, sr, tune=tune)
     _, xs, ch, _ = binding.debug_exec(h, v, N, tsz, k, sl, sr, tensor_cores=True, tune=tune)
-    assert cnt["tasks"] > 0
+    if cnt["tasks"] == 0:
+        assert len(tg) == 0 and cnt["op_bytes"] == 0
+        return 0
     # blocks: the tensor-core chunks of the execution plan, by shape 64x32, 64x64, 128x128
     tc_chunks = ch[ch[:, 0] == 2]
     assert len(tg) == len(tc_chunks) == cnt["blocks"]
@@ -106,3 +132,4 @@ def test_tensor_core_plan(case, tune):
             zv = (-1, 0, 0, p, p) if z == -1 else (4 * z, zcs, zrs, q, p)
             assert tile_of[xv] == xt and tile_of[zv] == zt
             assert psi_of[y] == (yt, n, p)
+    return cnt["tasks"]
