@@ -42,6 +42,25 @@ def test_oracle_single_determinant_has_no_entropy():
         assert np.allclose(fock.orbital_entropies(fock.pair_rdm_dets(x, D, i)), 0.0, atol=1e-14)
 
 
+def test_oracle_pair_matrix_labels_and_two_site_definition():
+    # site 0 holds up, site 1 holds dn: the pair state (b, c) = (up, dn) = index 4*1 + 2
+    D = fock.determinants(3, 1, 1)
+    x = np.zeros(len(D))
+    x[np.nonzero(D == ((1 << 0) | (1 << 3)))[0][0]] = 1.0
+    rho = fock.pair_rdm_dets(x, D, 0)
+    assert rho[6, 6] == 1.0 and np.count_nonzero(rho) == 1
+    # two sites are the whole system: rho is the outer product of the state written over (b, c)
+    rng = np.random.default_rng(3)
+    D = fock.determinants(2, 1, 1)
+    x = rng.normal(size=len(D))
+    v = np.zeros(16)
+    for d, c in zip(D, x):
+        b0 = (d & 1) + 2 * ((d >> 1) & 1)
+        b1 = ((d >> 2) & 1) + 2 * ((d >> 3) & 1)
+        v[4 * b0 + b1] = c
+    assert np.allclose(fock.pair_rdm_dets(x, D, 0), np.outer(v, v), atol=0, rtol=0)
+
+
 def test_oracle_two_site_pure_state_and_subadditivity():
     rng = np.random.default_rng(5)
     D = fock.determinants(2, 1, 1)
