@@ -386,14 +386,17 @@ def sweep_workload(args, wl):
         torch.cuda.synchronize()
         per = []
         energies = []
+        dw_max = []
         for _ in range(args.sweeps):
             t0 = time.perf_counter()
-            e = ctx.sweep(1, tol=wl["tol"])
+            rec = ctx.sweep_record(1, tol=wl["tol"])  # energies, discarded weights, two-site entropies
             torch.cuda.synchronize()
             per.append(time.perf_counter() - t0)
-            energies.append(float(np.min(e)))
+            energies.append(float(np.min(rec["energies"])))
+            dw_max.append(float(np.max(rec["discarded"])))
         st = ctx.stats()
-        r = {"s_per_sweep": per, "min_energy_per_sweep": energies,
+        r = {"s_per_sweep": per, "min_energy_per_sweep": energies, "max_discarded_weight_per_sweep": dw_max,
+             "last_sweep_site_entropies": _site_entropies(rec, L),
              "davidson_iters": st["davidson_iters"], "davidson_iters_lowp": st["davidson_iters_lowp"]}
         if ref is None:
             ref = energies
@@ -404,6 +407,13 @@ def sweep_workload(args, wl):
         print(json.dumps({name: r}), flush=True)
         ctx.close()
     return out
+
+
+def _site_entropies(rec, L):
+    """One-orbital entropy of every site from one sweep's records: the left site of the
+    forward positions 0..L-3, then both sites of the first backward position L-2."""
+    ent = rec["entropies"]
+    return [float(x) for x in list(ent[: L - 2, 0]) + [ent[L - 2, 0], ent[L - 2, 1]]]
 
 
 def mixed_step_workload(args, wl, tol):

@@ -39,3 +39,16 @@ def test_reference_arm_other_ranks_do_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr
     assert r.stdout.strip() == ""
+
+
+def test_sweep_summary_takes_every_site_once():
+    """The sweeps mode's entropy summary reads site s from a step whose two sites include s."""
+    import importlib.util
+    import numpy as np
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(ROOT, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    for L in (3, 6, 9):
+        positions = list(range(0, L - 2)) + list(range(L - 2, 0, -1))   # one sweep, both directions
+        rec = {"entropies": np.array([[k, k + 1, -1.0] for k in positions], dtype=float)}
+        assert bench._site_entropies(rec, L) == [float(s) for s in range(L)]
