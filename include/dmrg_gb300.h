@@ -179,6 +179,18 @@ int dmrg_get_psi(dmrg_ctx *ctx, double *psi, int device_ptr);
 int dmrg_davidson(dmrg_ctx *ctx, double tol, int max_iter, double *energy, int *iters);
 
 /*
+ * dmrg_set_davidson -- refinement variant of the mixed-precision Davidson
+ * (dmrg_davidson): refine_keep = 0 (default) restarts every refinement step
+ * from the current Ritz vector alone; refine_keep = m (1..8) also carries the
+ * next m Ritz vectors of the step's subspace, with their low-precision images,
+ * into the next step (a thick restart; their couplings to x are taken from
+ * the exact H x).  A replica of the algorithm needed far fewer matvecs on
+ * spectra with a dense bottom; not yet measured on a GPU.  No effect in
+ * DMRG_PREC_FP64.  DMRG_EINVAL for a NULL context or refine_keep outside 0..8.
+ */
+int dmrg_set_davidson(dmrg_ctx *ctx, int refine_keep);
+
+/*
  * dmrg_renormalize -- truncate the enlarged block and renormalize its
  * operators (Eqs. renorm, renorm_mat; Sec. 2.2.2), then move one position.
  * direction +1: new left block l' = l (x) s_l, position k -> k+1.

@@ -1060,6 +1060,7 @@ struct dmrg_ctx {
   dmrg::ChainTune tune;     // launch shape of H.psi task lists (dmrg_autotune)
   // density-matrix truncations: gap at the cut of the last one, smallest gap,
   // count, and how many had a near-degenerate cluster across the cut
+  int refine_keep = 0;  // Ritz vectors carried between refinement steps (dmrg_set_davidson)
   double cut_gap = std::numeric_limits<double>::infinity();
   double min_cut_gap = std::numeric_limits<double>::infinity();
   long long truncations = 0, straddled = 0;
@@ -2064,6 +2065,17 @@ static bool davidson_refine(dmrg_ctx *c, double tol, int max_iter, double *energ
   bool ok = true;
   conv = false;
   std::vector<double> Gh(32 * 32, 0.0);
+  // thick restart (refine_keep > 0): the next Ritz vectors of an outer step's
+  // subspace and their low-precision images join x in the next outer step
+  const int keep = std::min(c->refine_keep, kmax - 2);
+  DBuf<double> Xv, Xa;
+  int nx = 0;
+  if (keep > 0) {
+    Xv.alloc((size_t)keep * n);
+    Xa.alloc((size_t)keep * n);
+  }
+  std::vector<double> Ylast;
+  int klast = 0;
   for (;;) {
     // ---- outer step: exact H x, theta, residual
     hpsi_dev(c, c->V.p, c->AV.p, true);
@@ -2089,6 +2101,31 @@ static bool davidson_refine(dmrg_ctx *c, double tol, int max_iter, double *energ
     std::fill(Gh.begin(), Gh.end(), 0.0);
     Gh[0] = theta;
     int k = 1;
+    bool solved = false;
+    for (int j = 0; j < nx && k < kmax - 1; ++j) {
+      double *vk = c->V.p + (int64_t)k * n, *ak = c->AV.p + (int64_t)k * n;
+      CK(cudaMemcpyAsync(vk, Xv.p + (int64_t)j * n, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      CK(cudaMemcpyAsync(ak, Xa.p + (int64_t)j * n, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
+      for (int pass = 0; pass < 2; ++pass) {  // orthogonal to V[0..k); the image follows
+        CK(launch_dots(c->V.p, k, n, vk, c->partial.p, dots, s));
+        CK(launch_sub_proj(vk, c->V.p, dots, k, n, s));
+        CK(launch_sub_proj(ak, c->AV.p, dots, k, n, s));
+      }
+      if (!(norm2(vk) > 1e-16)) continue;  // leaves |vk|^2 in scal[1]
+      CK(launch_scale(vk, scal + 1, 1, n, s));
+      CK(launch_scale(ak, scal + 1, 1, n, s));
+      CK(launch_dots(c->V.p, k + 1, n, ak, c->partial.p, dots, s));
+      CK(launch_dots(c->AV.p, 1, n, vk, c->partial.p, dot0, s));  // exact (H x) . v
+      std::vector<double> col(k + 1);
+      CK(cudaMemcpyAsync(col.data(), dots, (k + 1) * sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaMemcpyAsync(col.data(), dot0, sizeof(double), cudaMemcpyDeviceToHost, s));
+      CK(cudaStreamSynchronize(s));
+      for (int i = 0; i <= k; ++i) {
+        Gh[i * 32 + k] = col[i];
+        Gh[k * 32 + i] = col[i];
+      }
+      ++k;
+    }
     // ---- inner expansion with low-precision matvecs
     for (;;) {
       CK(launch_precond(c->t.p, c->r.p, P.diag.p, scal, n, s));
@@ -2127,6 +2164,11 @@ static bool davidson_refine(dmrg_ctx *c, double tol, int max_iter, double *energ
       CK(cudaMemcpyAsync(&th, evals, sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaMemcpyAsync(Y.data(), evecs, (size_t)k * k * sizeof(double), cudaMemcpyDeviceToHost, s));
       CK(cudaStreamSynchronize(s));
+      solved = true;
+      if (keep > 0) {
+        Ylast = Y;
+        klast = k;
+      }
       std::vector<double> y0(k);
       for (int i = 0; i < k; ++i) y0[i] = Y[(size_t)i * k];
       CK(cudaMemcpyAsync(dots, y0.data(), k * sizeof(double), cudaMemcpyHostToDevice, s));
@@ -2137,9 +2179,20 @@ static bool davidson_refine(dmrg_ctx *c, double tol, int max_iter, double *energ
       const double rest = std::sqrt(std::max(norm2(c->r.p), 0.0));
       if (rest <= std::max(0.01 * rnorm, 0.5 * tol) || k == kmax || it >= max_iter) break;
     }
-    if (k == 1) {
+    if (k == 1 || (keep > 0 && !solved)) {
       ok = false;  // the subspace could not grow
       break;
+    }
+    if (keep > 0) {  // next Ritz vectors of this subspace and their images, for the next step
+      nx = std::min(keep, klast - 1);
+      for (int j = 0; j < nx; ++j) {
+        std::vector<double> yj(klast);
+        for (int i = 0; i < klast; ++i) yj[i] = Ylast[(size_t)i * klast + (j + 1)];
+        CK(cudaMemcpyAsync(dots, yj.data(), klast * sizeof(double), cudaMemcpyHostToDevice, s));
+        CK(launch_combine(Xv.p + (int64_t)j * n, c->V.p, dots, klast, n, 0.0, s));
+        CK(launch_combine(Xa.p + (int64_t)j * n, c->AV.p, dots, klast, n, 0.0, s));
+        CK(cudaStreamSynchronize(s));  // yj is released at the end of the iteration
+      }
     }
     // the Ritz vector becomes x of the next outer step
     CK(cudaMemcpyAsync(c->V.p, c->psi.p, n * sizeof(double), cudaMemcpyDeviceToDevice, s));
@@ -3200,6 +3253,14 @@ extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk
   c->tune.tc_min = tc_min;
   c->tune.by_work = by_work;
   c->plan.valid = false;
+  API_END
+}
+
+extern "C" int dmrg_set_davidson(dmrg_ctx *c, int refine_keep) {
+  API_BEGIN
+  if (!c || refine_keep < 0 || refine_keep > 8)
+    throw Fail{DMRG_EINVAL, "dmrg_set_davidson: NULL context or refine_keep outside 0..8"};
+  c->refine_keep = refine_keep;
   API_END
 }
 
