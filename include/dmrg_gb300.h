@@ -186,9 +186,11 @@ int dmrg_davidson(dmrg_ctx *ctx, double tol, int max_iter, double *energy, int *
  * into the next step (a thick restart; their couplings to x are taken from
  * the exact H x).  A replica of the algorithm needed far fewer matvecs on
  * spectra with a dense bottom; not yet measured on a GPU.  No effect in
- * DMRG_PREC_FP64.  DMRG_EINVAL for a NULL context or refine_keep outside 0..8.
+ * DMRG_PREC_FP64.  sweep_max_iter: the matvec cap of every Davidson step of
+ * dmrg_sweep / dmrg_sweep_record (default 200).  DMRG_EINVAL for a NULL
+ * context, refine_keep outside 0..8 or sweep_max_iter < 1.
  */
-int dmrg_set_davidson(dmrg_ctx *ctx, int refine_keep);
+int dmrg_set_davidson(dmrg_ctx *ctx, int refine_keep, int sweep_max_iter);
 
 /*
  * dmrg_renormalize -- truncate the enlarged block and renormalize its
@@ -265,7 +267,8 @@ int dmrg_orbital_entropies(dmrg_ctx *ctx, double *s3, double *rho2);
  * L-2..1 (Davidson then dmrg_renormalize(-1)).  Starts from position 0 in the
  * forward direction.  energies (host, may be NULL) receives one energy per
  * Davidson step: nsweeps * 2 * (L - 2) values.  Each step runs Davidson to tol
- * with at most 200 matvecs; a step that does not converge keeps its last Ritz
+ * with at most 200 matvecs (dmrg_set_davidson changes the cap); a step that
+ * does not converge keeps its last Ritz
  * pair and the sweep goes on.  Errors: DMRG_EINVAL (NULL context, nsweeps < 0,
  * tol <= 0, L < 3), else those of dmrg_davidson and dmrg_renormalize.
  */

@@ -76,7 +76,7 @@ def lib():
         "dmrg_orbital_entropies": (C.c_int, [vp, dp, dp]),
         "dmrg_block_basis": (C.c_int, [vp, C.c_int, C.c_int, ip, ip, dp, llp]),
         "dmrg_sweep_record": (C.c_int, [vp, C.c_int, C.c_double, dp, dp, dp]),
-        "dmrg_set_davidson": (C.c_int, [vp, C.c_int]),
+        "dmrg_set_davidson": (C.c_int, [vp, C.c_int, C.c_int]),
         "dmrg_debug_pair_rdm": (C.c_int, [C.c_int, ip, llp, dp, dp, dp]),
         "dmrg_debug_truncation": (C.c_int, [C.c_int, ip, dp, C.c_int, ip, ip, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
@@ -439,9 +439,10 @@ class DMRG:
         _check(lib().dmrg_truncation_stats(self.ctx, C.byref(last), C.byref(low), C.byref(n), C.byref(straddled)))
         return dict(last_gap=last.value, min_gap=low.value, truncations=n.value, straddled=straddled.value)
 
-    def set_davidson(self, refine_keep):
-        """Ritz vectors carried between refinement steps of the mixed-precision Davidson (0: none)."""
-        _check(lib().dmrg_set_davidson(self.ctx, int(refine_keep)))
+    def set_davidson(self, refine_keep=0, sweep_max_iter=200):
+        """Ritz vectors carried between refinement steps of the mixed-precision Davidson (0: none)
+        and the matvec cap of each Davidson step of a sweep."""
+        _check(lib().dmrg_set_davidson(self.ctx, int(refine_keep), int(sweep_max_iter)))
 
     def set_bond_dims(self, m_forward, m_backward):
         """Kept states of new left blocks (forward) and new right blocks (backward) in RDM truncations."""

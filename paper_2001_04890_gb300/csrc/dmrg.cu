@@ -1060,7 +1060,8 @@ struct dmrg_ctx {
   dmrg::ChainTune tune;     // launch shape of H.psi task lists (dmrg_autotune)
   // density-matrix truncations: gap at the cut of the last one, smallest gap,
   // count, and how many had a near-degenerate cluster across the cut
-  int refine_keep = 0;  // Ritz vectors carried between refinement steps (dmrg_set_davidson)
+  int refine_keep = 0;       // Ritz vectors carried between refinement steps (dmrg_set_davidson)
+  int sweep_max_iter = 200;  // matvec cap of each Davidson step of a sweep
   double cut_gap = std::numeric_limits<double>::infinity();
   double min_cut_gap = std::numeric_limits<double>::infinity();
   long long truncations = 0, straddled = 0;
@@ -2530,7 +2531,7 @@ static void sweep_impl(dmrg_ctx *c, int nsweeps, double tol, double *energies, d
     double e, dw = 0.0;
     int it;
     bool conv;
-    davidson(c, tol, 200, &e, &it, conv);
+    davidson(c, tol, c->sweep_max_iter, &e, &it, conv);
     if (energies) energies[idx] = e;
     if (entropies) current_entropies(c, entropies + 3 * idx, nullptr);
     do_renormalize(c, direction, nullptr, nullptr, &dw, nullptr);
@@ -3256,11 +3257,12 @@ extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk
   API_END
 }
 
-extern "C" int dmrg_set_davidson(dmrg_ctx *c, int refine_keep) {
+extern "C" int dmrg_set_davidson(dmrg_ctx *c, int refine_keep, int sweep_max_iter) {
   API_BEGIN
-  if (!c || refine_keep < 0 || refine_keep > 8)
-    throw Fail{DMRG_EINVAL, "dmrg_set_davidson: NULL context or refine_keep outside 0..8"};
+  if (!c || refine_keep < 0 || refine_keep > 8 || sweep_max_iter < 1)
+    throw Fail{DMRG_EINVAL, "dmrg_set_davidson: NULL context, refine_keep outside 0..8 or sweep_max_iter < 1"};
   c->refine_keep = refine_keep;
+  c->sweep_max_iter = sweep_max_iter;
   API_END
 }
 

@@ -59,7 +59,7 @@ def test_tune_calls_reject_bad_arguments_without_a_gpu():
     assert lib.dmrg_orbital_entropies(None, None, None) == binding.DMRG_EINVAL
     assert lib.dmrg_block_basis(None, 0, 1, None, None, None, None) == binding.DMRG_EINVAL
     assert lib.dmrg_sweep_record(None, 1, 1e-8, None, None, None) == binding.DMRG_EINVAL
-    assert lib.dmrg_set_davidson(None, 3) == binding.DMRG_EINVAL
+    assert lib.dmrg_set_davidson(None, 3, 200) == binding.DMRG_EINVAL
 
 
 def test_init_rejects_bad_problems_without_a_gpu():
