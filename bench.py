@@ -377,12 +377,14 @@ def sweep_workload(args, wl):
     L, N, two_sz, M = wl["L"], wl["N"], wl["two_sz"], wl["M"]
     h, v = workloads.integrals(L, seed=0)
     out = {"workload": wl["name"], "sweeps": args.sweeps, "davidson_tol": wl["tol"],
-           "positions_per_sweep": 2 * (L - 2)}
+           "positions_per_sweep": 2 * (L - 2), "refine_keep": args.refine_keep,
+           "sweep_max_iter": args.sweep_max_iter}
     ref = None
     for name, prec in (("fp64", 0), ("fp32", 1), ("bf16x3", 2)):
         ctx = binding.DMRG(h, v, N, two_sz, M, prec, stream=stream.cuda_stream)
         if args.tune:
             ctx.set_tune(**_fixed_tune(args.tune))
+        ctx.set_davidson(args.refine_keep, args.sweep_max_iter)
         torch.cuda.synchronize()
         per = []
         energies = []
@@ -554,6 +556,9 @@ def main():
     ap.add_argument("--tune", default="", metavar="T,MIN,TC,ORDER,WIDE",
                     help="fixed launch shape (target_chunks,min_chunk,tc_min,by_work,flat_wide); no autotuning")
     ap.add_argument("--M", type=int, default=0, help="override the workload's bond dimension (profiling)")
+    ap.add_argument("--refine-keep", type=int, default=0,
+                    help="sweeps: Ritz vectors carried between mixed-precision refinement steps")
+    ap.add_argument("--sweep-max-iter", type=int, default=200, help="sweeps: matvec cap of each Davidson step")
     ap.add_argument("--large", action="store_true",
                     help="middle-bond measurement of a large workload in every precision (JSON lines)")
     args = ap.parse_args()
