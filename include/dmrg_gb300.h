@@ -452,6 +452,22 @@ int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, 
                     long long *counts, long long *xs_out, long long *grp_out, long long *red_out);
 
 /*
+ * dmrg_debug_validate -- host-only bounds check of the execution plan that
+ * dmrg_debug_exec describes (default launch shape).  The four operand arenas
+ * (stored operators and pre-summed temporaries of both blocks) are given
+ * distinct element bases, so every operand address names its arena.  Every
+ * operand view of every chunk (rows x columns with its strides) must lie
+ * inside its arena, every psi view inside psi, every chunk slot and every
+ * reduction inside the scratch array, identity sides must be square.
+ * *checked receives the number of views and slots checked, *bad the number
+ * of violations (the first one is described in dmrg_last_error).  No GPU is
+ * used.
+ */
+int dmrg_debug_validate(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                        const int *sec_l, int nr, const int *sec_r, int tensor_cores, long long *checked,
+                        long long *bad);
+
+/*
  * dmrg_debug_tc -- host-only dump of the tensor-core launch plan for the same
  * task list as dmrg_debug_exec with tensor_cores = 1 (FP32 operand addresses):
  * the blocks routed to the tensor cores, ordered by kernel shape, their tasks

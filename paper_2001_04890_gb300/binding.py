@@ -86,6 +86,8 @@ def lib():
                                        C.c_int, ip, C.c_longlong, llp]),
         "dmrg_debug_exec": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
                                       C.c_int, dp, llp, llp, llp, llp]),
+        "dmrg_debug_validate": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
+                                          C.c_int, llp, llp]),
         "dmrg_debug_tc": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip, dp,
                                     llp, llp, llp, llp, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -162,6 +164,17 @@ def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
                                  red.ctypes.data_as(llp)))
     keys = ("entries", "tile_chunks", "flat_chunks", "tc_chunks", "reduce_groups", "tiles", "scratch", "reduced")
     return dict(zip(keys, (int(x) for x in cnt))), xs, ch, red
+
+
+def debug_validate(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False):
+    """Host-only bounds check of the execution plan: (views checked, violations, first violation)."""
+    h, v = _f64(h), _f64(v)
+    tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
+    tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
+    chk, bad = C.c_longlong(), C.c_longlong()
+    _check(lib().dmrg_debug_validate(h.shape[0], N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr),
+                                     _iptr(tr), int(tensor_cores), C.byref(chk), C.byref(bad)))
+    return chk.value, bad.value, (lib().dmrg_last_error().decode() if bad.value else "")
 
 
 def debug_tc(h, v, N, two_sz, k, sec_l, sec_r, tune=None):

@@ -2803,6 +2803,102 @@ extern "C" int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const 
   API_END
 }
 
+extern "C" int dmrg_debug_validate(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
+                                   const int *sec_l, int nr, const int *sec_r, int tensor_cores,
+                                   long long *checked, long long *bad) {
+  API_BEGIN
+  if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r || !checked || !bad)
+    throw Fail{DMRG_EINVAL, "dmrg_debug_validate: bad arguments"};
+  if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
+  Integrals I;
+  I.L = L;
+  I.h.assign(h, h + (size_t)L * L);
+  I.v.assign(v, v + (size_t)L * L * L * L);
+  auto sectors = [](int n, const int *t) {
+    std::vector<Sector> out;
+    for (int i = 0; i < n; ++i) out.push_back({t[3 * i], t[3 * i + 1], t[3 * i + 2]});
+    return out;
+  };
+  std::vector<int> ls, rs;
+  for (int s = 0; s < k; ++s) ls.push_back(s);
+  for (int s = k + 2; s < L; ++s) rs.push_back(s);
+  BlockLayout lb, rb;
+  build_layout(lb, 0, L, ls, sectors(nl, sec_l));
+  build_layout(rb, 1, L, rs, sectors(nr, sec_r));
+  Psi Y = psi_layout(lb, rb, (N + two_sz) / 2, (N - two_sz) / 2);
+  TempSet temps;
+  auto rps = resolve_pieces(I, k, lb, rb, temps);
+  const BlockLayout *lay[2] = {&lb, &rb};
+  temps.layout(lay);
+  // four operand arenas at distinct, far-apart element bases, so that every
+  // operand address names its arena
+  const uint64_t base[4] = {1ull << 40, 1ull << 41, 1ull << 42, 1ull << 43};
+  const int64_t size[4] = {lb.total, rb.total, temps.total[0], temps.total[1]};
+  const void *ptr[4];
+  for (int a = 0; a < 4; ++a) ptr[a] = reinterpret_cast<const void *>((uintptr_t)(base[a] * 8));
+  Arenas A{{&lb, &rb}, {ptr[0], ptr[1]}, &temps, {ptr[2], ptr[3]}, 8};
+  ChainList CL;
+  double f = 0.0;
+  expand_hpsi_grouped(rps, A, Y, lb, CL, f);
+  ExecPlan X;
+  plan_exec(CL, tensor_cores != 0, true, ChainTune(), X);
+  long long nchk = 0, nbad = 0;
+  std::string first;
+  auto view = [&](const char *what, uint64_t at, int rows, int cols, int rst, int cst, bool op) {
+    ++nchk;
+    if (rows < 1 || cols < 1 || rst < 0 || cst < 0) {
+      if (!nbad++) first = std::string(what) + ": bad shape or stride";
+      return;
+    }
+    const uint64_t last = at + (uint64_t)(rows - 1) * rst + (uint64_t)(cols - 1) * cst;
+    uint64_t lo = 0, hi = (uint64_t)Y.dim;  // psi and slots are relative offsets
+    if (op) {
+      int a = -1;
+      for (int i = 0; i < 4; ++i)
+        if (at >= base[i]) a = i;
+      if (a < 0) {
+        if (!nbad++) first = std::string(what) + ": address outside every arena";
+        return;
+      }
+      lo = base[a];
+      hi = base[a] + (uint64_t)size[a];
+    }
+    if (at < lo || last >= hi)
+      if (!nbad++) first = std::string(what) + ": view leaves its array";
+  };
+  const std::vector<ChainGroup> *kinds[3] = {&X.vb, &X.vf, &X.vt};
+  for (const auto *kv : kinds)
+    for (const ChainGroup &t : *kv) {
+      ++nchk;
+      const uint64_t slot_last = t.d + (uint64_t)(t.m - 1) * t.drs + (uint64_t)(t.q - 1) * t.dcs;
+      if (t.m < 1 || t.q < 1 || slot_last >= (uint64_t)X.soff)
+        if (!nbad++) first = "chunk slot leaves the scratch array";
+      for (int i = t.first; i < t.first + t.count; ++i) {
+        const ChainEntry &e = X.xs[(size_t)i];
+        if (e.x == ~0ull) {
+          if (e.n != t.m && !nbad++) first = "identity X is not square";
+        } else {
+          view("X", e.x, t.m, e.n, e.xrs, e.xcs, true);
+        }
+        view("Y", e.y, e.n, e.p, e.yrs, e.ycs, false);
+        if (e.z == ~0ull) {
+          if (e.p != t.q && !nbad++) first = "identity Z is not square";
+        } else {
+          view("Z", e.z, e.p, t.q, e.zrs, e.zcs, true);
+        }
+      }
+    }
+  for (const ReduceGroup &r : X.vr) {
+    view("output block", r.d, r.m, r.q, r.drs, r.dcs, false);
+    ++nchk;
+    if (r.soff + (int64_t)r.nsplit * r.m * r.q > X.soff && !nbad++) first = "reduction slots leave the scratch array";
+  }
+  *checked = nchk;
+  *bad = nbad;
+  if (nbad) set_error("dmrg_debug_validate: " + first);
+  API_END
+}
+
 extern "C" int dmrg_debug_tc(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
                              const int *sec_l, int nr, const int *sec_r, const double *tune, long long *counts,
                              long long *te_out, long long *tg_out, long long *ts_out, long long *ps_out) {

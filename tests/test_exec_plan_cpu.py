@@ -177,3 +177,37 @@ def test_execution_plan_orientation_rule_is_applied():
             e = xs[first:first + count]
             got += int(np.sum((e[:, 3] != e[:, 2]) | (e[:, 4] != 1)))
     assert want > 0 and got == want
+
+
+@pytest.mark.parametrize("case", CASES + [(24, 24, 0, 512, 11)])
+@pytest.mark.parametrize("tc", [False, True])
+def test_every_operand_view_stays_inside_its_array(case, tc):
+    """Host bounds check of the execution plan (the descriptors the kernels read): every
+    X / Z view inside its operator arena, every psi view inside psi, every chunk slot and
+    reduction inside the scratch array."""
+    L, N, tsz, M, k = case
+    sl, sr = _tables(L, N, tsz, M, k)
+    h, v = workloads.integrals(L, seed=0)
+    checked, bad, first = binding.debug_validate(h, v, N, tsz, k, sl, sr, tensor_cores=tc)
+    assert checked > 0 and bad == 0, first
+
+
+@pytest.mark.parametrize("seed", range(10))
+def test_operand_views_in_bounds_on_random_layouts(seed):
+    rng = np.random.default_rng(400 + seed)
+    L = int(rng.integers(4, 10))
+    k = int(rng.integers(0, L - 1))
+    N = int(rng.integers(1, 2 * L))
+    tsz = int(rng.choice([x for x in range(-N, N + 1, 2) if (N - x) // 2 <= L and (N + x) // 2 <= L]))
+
+    def table(n_sites):
+        if n_sites == 0:
+            return [(0, 0, 1)]
+        out = [(a, b, int(rng.integers(1, 70))) for a in range(n_sites + 1) for b in range(n_sites + 1)
+               if rng.random() < 0.7]
+        return out or [(0, 0, 1)]
+    sl, sr = table(k), table(L - k - 2)
+    h, v = workloads.integrals(L, seed=seed)
+    for tc in (False, True):
+        checked, bad, first = binding.debug_validate(h, v, N, tsz, k, sl, sr, tensor_cores=tc)
+        assert bad == 0, first
