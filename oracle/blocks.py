@@ -30,6 +30,7 @@ import scipy.sparse as sp
 from . import fock
 
 TRUNC_DROP = 1e-13
+TRUNC_CLUSTER = 1e-10  # eigenvalues closer than this are one near-degenerate cluster
 
 
 class Block:
@@ -384,9 +385,15 @@ def rdm_blocks(psi, lb: Block, rb: Block, n_up: int, n_dn: int, direction: int):
 def truncate(rho: dict, M: int, drop: float = TRUNC_DROP):
     """Keep the M eigenvectors with the largest eigenvalues over all sectors.
 
-    Ties are broken by (sector order, in-sector order); eigenvalues <= drop are
-    never kept.  Returns (O per sector, kept per sector in sector order,
-    discarded weight = trace - sum of kept eigenvalues, all eigenvalues).
+    Order: descending eigenvalue, ties by (sector order, in-sector order);
+    eigenvalues <= drop are never kept.  "The M largest" is not defined when
+    the M-th and the next eigenvalue above drop are (near-)equal: the cut then
+    moves down past that whole cluster (consecutive eigenvalues closer than
+    TRUNC_CLUSTER), so that the kept space does not depend on how a
+    degenerate cluster is split; only if that would keep nothing does the
+    cut stay at M (ties then by the order above).  Returns (O per sector,
+    kept per sector in sector order, discarded weight = trace - sum of kept
+    eigenvalues, all eigenvalues).
     """
     cand = []
     eig = {}
@@ -397,16 +404,19 @@ def truncate(rho: dict, M: int, drop: float = TRUNC_DROP):
         for j, x in enumerate(ev):
             cand.append((-x, si, j, E))
     cand.sort(key=lambda z: (z[0], z[1], z[2]))
-    keep = {E: [] for E in rho}
     total = sum(float(np.trace(R)) for R in rho.values())
+    above = [c for c in cand if -c[0] > drop]
+    n = min(M, len(above))
+    cut = n
+    while 0 < cut < len(above) and (-above[cut - 1][0]) - (-above[cut][0]) < TRUNC_CLUSTER:
+        cut -= 1
+    if cut == 0:
+        cut = n
+    keep = {E: [] for E in rho}
     kept_w = 0.0
-    n = 0
-    for negx, si, j, E in cand:
-        if n >= M or -negx <= drop:
-            break
+    for negx, si, j, E in above[:cut]:
         keep[E].append(j)
         kept_w += -negx
-        n += 1
     O, kept = {}, []
     for E in rho:
         js = sorted(keep[E])

@@ -1085,16 +1085,23 @@ KeptSet choose_kept(const std::vector<std::vector<double>> &ev_ascending, int mk
   });
   r.kept.assign(ne, 0);
   r.cols.assign(ne, {});
-  int nk = 0;
-  while (nk < (int)cand.size() && nk < mkeep && cand[nk].v > drop) {
-    const Cand &c = cand[nk];
+  // candidates above the drop threshold, and the first mkeep of them
+  int nabove = 0;
+  while (nabove < (int)cand.size() && cand[nabove].v > drop) ++nabove;
+  const int n = std::max(0, std::min(mkeep, nabove));
+  // a near-degenerate cluster across the cut: move the cut below the whole
+  // cluster, unless nothing would be kept
+  int nk = n;
+  while (nk > 0 && nk < nabove && cand[nk - 1].v - cand[nk].v < kTruncCluster) --nk;
+  if (nk == 0) nk = n;
+  for (int i = 0; i < nk; ++i) {
+    const Cand &c = cand[i];
     r.kept[c.e]++;
     r.kept_weight += c.v;
     r.cols[c.e].push_back((int)ev_ascending[c.e].size() - 1 - c.j);
-    ++nk;
   }
   r.cut_gap = std::numeric_limits<double>::infinity();
-  if (nk > 0 && nk < (int)cand.size() && cand[nk].v > drop) r.cut_gap = cand[nk - 1].v - cand[nk].v;
+  if (nk > 0 && nk < nabove) r.cut_gap = cand[nk - 1].v - cand[nk].v;
   for (auto &c : r.cols) std::sort(c.begin(), c.end(), std::greater<int>());
   return r;
 }

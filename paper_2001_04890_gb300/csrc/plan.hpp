@@ -308,11 +308,17 @@ std::vector<int> stack_runs(const std::vector<uint64_t> &sorted_keys, int cap);
 // eigenvectors with the largest eigenvalues over all sectors.  Input: per sector,
 // the eigenvalues in ascending order (as a symmetric eigensolver returns them).
 // Order: descending eigenvalue, ties by (sector, in-sector rank from the top);
-// eigenvalues <= drop are never kept.  cols[e] lists the kept columns of sector e
-// (indices into the ascending order) by descending eigenvalue.  cut_gap is the
-// smallest kept eigenvalue minus the largest eigenvalue above drop that was not
-// kept (+infinity when nothing above drop was cut, or nothing was kept): a gap
-// below 1e-10 means a near-degenerate cluster straddles the cut.
+// eigenvalues <= drop are never kept.  When the mkeep-th and the next eigenvalue
+// above drop differ by less than kTruncCluster, "the mkeep largest" is not
+// defined: the cut moves down past that whole cluster (consecutive eigenvalues
+// closer than kTruncCluster), so the kept space does not depend on how the
+// cluster is split; only if nothing would be kept does the cut stay at mkeep.
+// cols[e] lists the kept columns of sector e (indices into the ascending order)
+// by descending eigenvalue.  cut_gap is the smallest kept eigenvalue minus the
+// largest eigenvalue above drop that was not kept (+infinity when nothing above
+// drop was cut, or nothing was kept): a gap below kTruncCluster remains only
+// when the top cluster alone holds more than mkeep states.
+constexpr double kTruncCluster = 1e-10;
 struct KeptSet {
   std::vector<int> kept;
   std::vector<std::vector<int>> cols;

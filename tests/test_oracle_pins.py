@@ -258,8 +258,10 @@ def test_renormalized_product_equals_product_on_complete_basis():
 
 def test_truncation_rule_on_a_known_spectrum():
     """Reading of "keep the M largest eigenvalues": global order, ties by (sector
-    order, in-sector order), eigenvalues <= 1e-13 never kept, discarded weight =
-    trace - kept.  Checked on density matrices with known eigenpairs."""
+    order, in-sector order), eigenvalues <= 1e-13 never kept, a near-degenerate
+    cluster across the cut is cut as a whole unless nothing would remain,
+    discarded weight = trace - kept.  Checked on density matrices with known
+    eigenpairs."""
     import numpy as np
     from oracle import blocks as ob
     rng = np.random.default_rng(5)
@@ -272,9 +274,19 @@ def test_truncation_rule_on_a_known_spectrum():
     assert kept == [1, 1, 2]
     trace = sum(sum(ev) for ev in spectra.values())
     assert abs(dw - (trace - 0.90)) < 1e-12
-    # M = 5: the tie at 0.05 goes to the earlier sector
+    # M = 5: the two 0.05 straddle the cut, so both are cut (the 4 above remain)
     O, kept, dw, _ = ob.truncate(rho, 5)
-    assert kept == [2, 1, 2]
+    assert kept == [1, 1, 2]
+    assert abs(dw - (trace - 0.90)) < 1e-12
+    # M = 1: the top cluster (0.30 twice) holds more than M: the cut stays at M and
+    # the tie goes to the earlier sector
+    O, kept, dw, _ = ob.truncate(rho, 1)
+    assert kept == [1, 0, 0]
+    # near-equal (within 1e-10) is one cluster too; 1e-9 apart is not
+    near = {(0, 0): np.diag([0.4, 0.2 + 5e-11]), (1, 0): np.diag([0.2])}
+    assert ob.truncate(near, 2)[1] == [1, 0]
+    apart = {(0, 0): np.diag([0.4, 0.2 + 1e-9]), (1, 0): np.diag([0.2])}
+    assert ob.truncate(apart, 2)[1] == [2, 0]
     # M large: 1e-14 and 0.0 are never kept
     O, kept, dw, _ = ob.truncate(rho, 100)
     assert kept == [2, 2, 2]

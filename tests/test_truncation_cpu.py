@@ -1,7 +1,9 @@
 """The library's density-matrix truncation rule (Sec. 2.1: keep the eigenvectors
 with the largest eigenvalues over all sectors) against the oracle's, on the
 host: the same spectra give the same kept set, in the same order, including
-exact ties and eigenvalues at the drop threshold."""
+exact ties, near-degenerate clusters across the cut and eigenvalues at the
+drop threshold; the kept count also against a brute-force statement of the
+rule."""
 import numpy as np
 import pytest
 
@@ -66,12 +68,36 @@ def test_library_truncation_equals_oracle(case):
         assert (np.isinf(gap) and np.isinf(g)) or abs(gap - g) <= 1e-15
 
 
+def _brute_kept_count(spectra, M, drop=1e-13, cluster=1e-10):
+    """The documented rule by brute force: the largest prefix of the global order
+    with at most M states whose cut does not split a cluster (gap >= 1e-10 to the
+    next eigenvalue above drop); M itself (capped) if that prefix is empty."""
+    vals = sorted([x for ev in spectra for x in ev if x > drop], reverse=True)
+    n = min(M, len(vals))
+    for c in range(n, 0, -1):
+        if c == len(vals) or vals[c - 1] - vals[c] >= cluster:
+            return c
+    return n
+
+
+@pytest.mark.parametrize("case", range(len(CASES)))
+def test_library_truncation_count_equals_brute_force(case):
+    spectra = [np.asarray(s, dtype=np.float64) for s in CASES[case]]
+    total = sum(len(s) for s in spectra)
+    for M in range(0, total + 2):
+        kept = binding.debug_truncation(spectra, M)[0]
+        assert int(np.sum(kept)) == _brute_kept_count(spectra, M), (spectra, M)
+
+
 def test_library_truncation_gap_flags_straddling_cluster():
     # 0.3 kept in one sector, its exact twin cut in another: gap 0
     kept, cols, trace, kw, gap = binding.debug_truncation([np.array([0.1, 0.3]), np.array([0.3])], 1)
     assert list(kept) == [1, 0] and gap == 0.0
     kept, cols, trace, kw, gap = binding.debug_truncation([np.array([0.1, 0.3]), np.array([0.3])], 2)
     assert list(kept) == [1, 1] and abs(gap - 0.2) < 1e-15
+    # a straddling tie below the top cluster: the cut moves above it
+    kept, cols, trace, kw, gap = binding.debug_truncation([np.array([0.3, 0.5]), np.array([0.3])], 2)
+    assert list(kept) == [1, 0] and abs(gap - 0.2) < 1e-15
     # nothing above the drop threshold cut: no gap
     kept, cols, trace, kw, gap = binding.debug_truncation([np.array([0.0, 1e-13, 0.5])], 1)
     assert list(kept) == [1] and np.isinf(gap)
