@@ -142,10 +142,25 @@ int dmrg_hpsi(dmrg_ctx *ctx, const double *psi, double *sigma, int device_ptrs);
  * runtime call); make it before any stream capture.  The array is shared by
  * all calls and contexts in the process and keeps the last call's contents;
  * each call clears the part it uses.  Calls that overlap on the GPU race on
- * it: order them on one stream.
+ * it: order them on one stream.  The call does not synchronize, so a
+ * tensor-core completion wait that runs out in it (DMRG_PREC_BF16X3) is not
+ * seen on return: dmrg_check_status reports it (DMRG_ETIMEOUT), as does the
+ * next synchronizing call on the context; the call clears any such report
+ * left by an earlier call first, so a report always belongs to the calls
+ * made since.
  */
 int dmrg_hpsi_noalloc(dmrg_ctx *ctx, const double *psi, double *sigma);
 long long dmrg_hpsi_noalloc_capacity(void);
+
+/*
+ * dmrg_check_status -- waits for the work queued on the context's stream and
+ * reports whether a bounded device-side wait of that work ran out:
+ * DMRG_ETIMEOUT (the results of those calls are invalid; the message names the
+ * wait) or DMRG_OK.  The report is cleared once read.  Needed only after calls
+ * that do not synchronize (dmrg_hpsi_noalloc); every other call checks on its
+ * own before it returns.  No paper counterpart (error reporting).
+ */
+int dmrg_check_status(dmrg_ctx *ctx);
 
 /* Algorithmic FLOPs of one dmrg_hpsi at the current position (host-counted from the task list). */
 int dmrg_hpsi_flops(dmrg_ctx *ctx, double *flops, long long *tasks);
@@ -173,10 +188,28 @@ int dmrg_get_psi(dmrg_ctx *ctx, double *psi, int device_ptr);
  * (E - diag H)^-1 with |denominator| >= 1e-8, subspace <= 24, thick restart
  * with 2 vectors, converged when ||H psi - E psi|| <= tol for normalized psi.
  * Starts from the current psi when one is set, else from a fixed pseudo-random
- * vector.  *energy, *iters (host; may be NULL).  DMRG_ENOCONV if max_iter is
- * reached (energy and psi still hold the last Ritz pair).
+ * vector; a fixed seeded admixture of relative size ~6e-4 is added to the
+ * start vector, because a state carried over from the previous position lies
+ * in one symmetry subspace of H (spin, spin flip) that an FP64 Krylov space
+ * never leaves, while the lowest state may lie in another.  *energy, *iters
+ * (host; may be NULL).  DMRG_ENOCONV if max_iter is reached (energy and psi
+ * still hold the last Ritz pair).
  */
 int dmrg_davidson(dmrg_ctx *ctx, double tol, int max_iter, double *energy, int *iters);
+
+/*
+ * dmrg_davidson_lowp -- the first phase of dmrg_davidson alone: Davidson with
+ * every matvec in the context's working precision (FP32 operators or split-BF16
+ * x3 tensor-core products in the mixed precisions, FP64 otherwise) until
+ * ||H psi - E psi|| <= tol or max_iter iterations, without the FP64
+ * refinement (the residual is that of the low-precision operator).  Vectors,
+ * subspace and residuals are FP64 as in dmrg_davidson.  For measurements of
+ * the working-precision iteration and for cheap warm-up iterations.  *energy,
+ * *iters (host; may be NULL): the Ritz value and the number of H.psi
+ * applications (the start vector's included).  DMRG_ENOCONV if max_iter is
+ * reached.
+ */
+int dmrg_davidson_lowp(dmrg_ctx *ctx, double tol, int max_iter, double *energy, int *iters);
 
 /*
  * dmrg_set_davidson -- refinement variant of the mixed-precision Davidson
@@ -201,7 +234,10 @@ int dmrg_set_davidson(dmrg_ctx *ctx, int refine_keep, int sweep_max_iter);
  * (rho^R = psi^T psi) of the current psi: the M largest eigenvalues over all
  * sectors (or the per-direction limits of dmrg_set_bond_dims), ties broken by
  * (sector order, in-sector order), eigenvalues
- * <= 1e-13 never kept; kept (may be NULL) receives the per-sector counts.
+ * <= 1e-13 never kept; where the M-th and the next eigenvalue differ by less
+ * than 1e-10 the cut moves down past that near-degenerate cluster (unless
+ * nothing would remain), so the kept space is unique; kept (may be NULL)
+ * receives the per-sector counts.
  * Otherwise kept (host, one int per enlarged sector) and O (host, layout in
  * the header comment) define the new basis; the caller guarantees
  * orthonormal columns.  *discarded_weight (may be NULL) = trace(rho) - kept
@@ -217,11 +253,13 @@ int dmrg_renormalize(dmrg_ctx *ctx, int direction, const int *kept, const double
  * (dmrg_renormalize with O NULL, and the steps of dmrg_sweep) since dmrg_init.
  * The gap of one truncation is the smallest kept eigenvalue minus the largest
  * eigenvalue above 1e-13 that was cut (+infinity when no such eigenvalue was
- * cut).  A gap below 1e-10 means a near-degenerate cluster straddles the cut:
- * the kept space, and the energies after it, then depend on rounding (the
- * paper's rule names no order for equal eigenvalues).  Outputs (host, each
- * may be NULL): the last gap, the smallest gap, the number of truncations and
- * the number with gap < 1e-10.  Errors: DMRG_EINVAL (NULL context).
+ * cut).  The cut is moved below near-degenerate clusters (see
+ * dmrg_renormalize), so a gap below 1e-10 remains only where the top cluster
+ * alone holds more than M states: the kept space, and the energies after it,
+ * then depend on rounding (the paper's rule names no order for equal
+ * eigenvalues).  Outputs (host, each may be NULL): the last gap, the smallest
+ * gap, the number of truncations and the number with gap < 1e-10.  Errors:
+ * DMRG_EINVAL (NULL context).
  */
 int dmrg_truncation_stats(dmrg_ctx *ctx, double *last_gap, double *min_gap, long long *truncations,
                           long long *straddled);
@@ -417,6 +455,28 @@ int dmrg_plan_hpsi_flops(int L, int N, int two_sz, const double *h, const double
 int dmrg_selftest_tcgen05(int N, int K, const float *A, const float *B, float *C);
 
 /*
+ * dmrg_debug_set_wait_limit -- fault detection test hook (no paper
+ * counterpart), process-wide.  Sets the number of polls of every pipeline wait
+ * of the tensor-core kernel (a job's operands landed, a stage freed, T or D
+ * complete) for launches made from now on; tries < 0 restores the default
+ * (2^22 polls).  When a wait runs out the kernel records the time-out, lets
+ * its copies and MMAs in flight finish (those drain waits keep the default
+ * limit), releases its tensor memory and returns, and the call reports
+ * DMRG_ETIMEOUT; the context stays usable.  tries = 0 makes every pipeline
+ * wait give up at once, before any copy or MMA is issued.  Always DMRG_OK.
+ */
+int dmrg_debug_set_wait_limit(long long tries);
+
+/*
+ * dmrg_debug_fail_alloc -- fault injection on the host (no paper
+ * counterpart), process-wide: for n > 0, the n-th device allocation of the
+ * library from now fails as if the device were out of memory, so the call
+ * making it returns DMRG_ENOMEM; later allocations succeed.  n <= 0 disarms.
+ * Always DMRG_OK.
+ */
+int dmrg_debug_fail_alloc(long long n);
+
+/*
  * dmrg_debug_tasks -- host-only dump of the H.psi task list the planner builds
  * for the same arguments as dmrg_plan_hpsi_flops: per task 7 ints (output psi
  * block index, m, n, p, q, identity flags (1: left identity, 2: right
@@ -512,7 +572,9 @@ int dmrg_debug_newops(int L, const double *h, const double *v, int k, int side, 
  * dmrg_debug_truncation -- host-only run of the truncation rule that
  * dmrg_renormalize applies to the density-matrix spectrum (Sec. 2.1): the
  * mkeep largest eigenvalues over all sectors, ties by (sector, in-sector rank
- * from the top), eigenvalues <= 1e-13 never kept.  In: nsectors, dims (one
+ * from the top), eigenvalues <= 1e-13 never kept, the cut moved below a
+ * near-degenerate cluster (consecutive eigenvalues closer than 1e-10) that
+ * straddles it unless nothing would remain.  In: nsectors, dims (one
  * int per sector), ev_ascending (sum of dims doubles: each sector's spectrum in
  * ascending order, sectors concatenated).  Out: kept (one int per sector),
  * cols (may be NULL; sum of kept ints: per sector, the kept columns as indices

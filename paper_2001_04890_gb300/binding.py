@@ -51,9 +51,13 @@ def lib():
         "dmrg_hpsi_flops": (C.c_int, [vp, dp, llp]),
         "dmrg_hpsi_noalloc": (C.c_int, [vp, vp, vp]),
         "dmrg_hpsi_noalloc_capacity": (C.c_longlong, []),
+        "dmrg_check_status": (C.c_int, [vp]),
+        "dmrg_debug_set_wait_limit": (C.c_int, [C.c_longlong]),
+        "dmrg_debug_fail_alloc": (C.c_int, [C.c_longlong]),
         "dmrg_set_psi": (C.c_int, [vp, vp, C.c_int]),
         "dmrg_get_psi": (C.c_int, [vp, vp, C.c_int]),
         "dmrg_davidson": (C.c_int, [vp, C.c_double, C.c_int, dp, ip]),
+        "dmrg_davidson_lowp": (C.c_int, [vp, C.c_double, C.c_int, dp, ip]),
         "dmrg_renormalize": (C.c_int, [vp, C.c_int, ip, dp, dp]),
         "dmrg_sweep": (C.c_int, [vp, C.c_int, C.c_double, dp]),
         "dmrg_block_op": (C.c_int, [vp, C.c_int, C.c_int, C.c_int, C.c_int, dp, llp]),
@@ -246,6 +250,17 @@ def debug_pair_rdm(layout, psi):
     return rho.reshape(16, 16), tuple(s3)
 
 
+def debug_set_wait_limit(tries):
+    """Process-wide polls per pipeline wait of the tensor-core kernel (0: give up at once,
+    < 0: the default)."""
+    _check(lib().dmrg_debug_set_wait_limit(int(tries)))
+
+
+def debug_fail_alloc(n):
+    """Process-wide: the n-th device allocation from now fails (n <= 0 disarms)."""
+    _check(lib().dmrg_debug_fail_alloc(int(n)))
+
+
 def selftest_tcgen05(A, B):
     """C = A B^T on the tensor cores (A: 128 x K, B: N x K, float32)."""
     A = np.ascontiguousarray(A, dtype=np.float32)
@@ -335,9 +350,23 @@ class DMRG:
         return sigma
 
     def hpsi_noalloc(self, psi, sigma):
-        """sigma = H psi (CUDA torch tensors, float64) without any device allocation in the call."""
+        """sigma = H psi (CUDA torch tensors, float64) without any device allocation in the call.
+
+        The call does not wait for the GPU: check_status() reports a tensor-core
+        time-out of the calls made since the last check."""
+        import torch
+        _, dim = self.psi_layout()
+        for name, t in (("psi", psi), ("sigma", sigma)):
+            if not (isinstance(t, torch.Tensor) and t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()
+                    and t.numel() == dim):
+                raise ValueError(f"{name} must be a contiguous float64 CUDA tensor of {dim} elements")
         _check(lib().dmrg_hpsi_noalloc(self.ctx, psi.data_ptr(), sigma.data_ptr()))
         return sigma
+
+    def check_status(self):
+        """Wait for the context's stream; raise DMRGError (DMRG_ETIMEOUT) if a bounded
+        device wait of the work queued since the last check ran out."""
+        _check(lib().dmrg_check_status(self.ctx))
 
     def hpsi_flops(self):
         f, t = C.c_double(), C.c_longlong()
@@ -366,6 +395,15 @@ class DMRG:
     def davidson(self, tol=1e-9, max_iter=200, allow_noconv=False):
         e, it = C.c_double(), C.c_int()
         code = lib().dmrg_davidson(self.ctx, tol, max_iter, C.byref(e), C.byref(it))
+        if code == DMRG_ENOCONV and allow_noconv:
+            return e.value, it.value
+        _check(code)
+        return e.value, it.value
+
+    def davidson_lowp(self, tol=1e-9, max_iter=200, allow_noconv=False):
+        """Davidson in the working precision only (no FP64 refinement): (Ritz value, H.psi count)."""
+        e, it = C.c_double(), C.c_int()
+        code = lib().dmrg_davidson_lowp(self.ctx, tol, max_iter, C.byref(e), C.byref(it))
         if code == DMRG_ENOCONV and allow_noconv:
             return e.value, it.value
         _check(code)

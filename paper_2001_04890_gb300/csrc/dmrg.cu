@@ -75,6 +75,22 @@ struct NoInitAlloc : std::allocator<T> {
   }
 };
 
+// Host-side fault injection for the error paths: when positive, the n-th
+// device allocation from now fails as if the device were out of memory
+// (dmrg_debug_fail_alloc).  No GPU fault is involved.
+static std::atomic<long long> g_fail_alloc_after{0};
+
+static cudaError_t device_alloc(void **p, size_t bytes) {
+  long long n = g_fail_alloc_after.load();
+  while (n > 0) {
+    if (g_fail_alloc_after.compare_exchange_weak(n, n - 1)) {
+      if (n == 1) return cudaErrorMemoryAllocation;
+      break;
+    }
+  }
+  return cudaMalloc(p, bytes);
+}
+
 template <class T>
 struct DBuf {
   T *p = nullptr;
@@ -92,7 +108,7 @@ struct DBuf {
     if (count <= n && p) return;
     release();
     if (count == 0) return;
-    CK(cudaMalloc(&p, count * sizeof(T)));
+    CK(device_alloc(reinterpret_cast<void **>(&p), count * sizeof(T)));
     n = count;
   }
   template <class A>
@@ -894,10 +910,14 @@ struct DevChain {
     }
   }
 
+  // The launch sequence.  The chunk partials of a split task list go to the
+  // list's own scratch array, or to ext (at least scratch_n doubles, cleared
+  // here) when the caller provides one; nothing is allocated here.
   void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s,
-              int *status = nullptr) const {
-    const uint64_t tb = split ? (uint64_t)(uintptr_t)scratch.p : db;
-    if (split && scratch_n > 0) CK(cudaMemsetAsync(scratch.p, 0, scratch_n * sizeof(double), s));
+              int *status = nullptr, double *ext = nullptr) const {
+    double *part = ext ? ext : scratch.p;
+    const uint64_t tb = split ? (uint64_t)(uintptr_t)part : db;
+    if (split && scratch_n > 0) CK(cudaMemsetAsync(part, 0, scratch_n * sizeof(double), s));
     if (f32ops) {
       CK(launch_chain_f32ops(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_f32ops(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
@@ -906,24 +926,7 @@ struct DevChain {
       CK(launch_chain_fp64(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_fp64(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
     }
-    if (split) CK(launch_reduce_partials(red.p, nred, red_total, scratch.p, (double *)(uintptr_t)db, s));
-  }
-
-  // Same launch sequence with the chunk partials in caller-provided scratch
-  // (at least scratch_n doubles); no device memory is allocated here.
-  void launch_with_scratch(double *ext, bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db,
-                           cudaStream_t s, int *status) const {
-    const uint64_t tb = (uint64_t)(uintptr_t)ext;
-    if (scratch_n > 0) CK(cudaMemsetAsync(ext, 0, scratch_n * sizeof(double), s));
-    if (f32ops) {
-      CK(launch_chain_f32ops(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_f32ops(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
-      launch_tc(yb, tb, status, s);
-    } else {
-      CK(launch_chain_fp64(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
-      CK(launch_chain_flat_fp64(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
-    }
-    CK(launch_reduce_partials(red.p, nred, red_total, ext, (double *)(uintptr_t)db, s));
+    if (split) CK(launch_reduce_partials(red.p, nred, red_total, part, (double *)(uintptr_t)db, s));
   }
 };
 
@@ -1673,7 +1676,7 @@ static void rdm_truncate(dmrg_ctx *c, int direction, const Enlarged &enl, std::v
   c->cut_gap = ks.cut_gap;
   c->min_cut_gap = std::min(c->min_cut_gap, ks.cut_gap);
   c->truncations++;
-  if (ks.cut_gap < 1e-10) c->straddled++;
+  if (ks.cut_gap < kTruncCluster) c->straddled++;
   Ooff.assign(ne, 0);
   int64_t otot = 0;
   for (int e = 0; e < ne; ++e) {
@@ -1866,6 +1869,10 @@ static void do_renormalize(dmrg_ctx *c, int direction, const int *kept_in, const
 
 // ---------------------------------------------------------------- Davidson
 
+// Relative size of the seeded admixture added to every Davidson start vector
+// (see davidson_core).
+static constexpr double kGuessAdmixture = 1e-3;
+
 // One Davidson run (Sec. 2.2.1) from the current psi.  fp64: matvecs with the
 // FP64 task list; otherwise the context's working precision.  floor: extra
 // residual threshold (the attainable residual of low-precision matvecs).
@@ -1901,6 +1908,17 @@ static void davidson_core(dmrg_ctx *c, double tol, double floor_rel, int max_ite
     CK(launch_scale(x, scal + 1, 1, n, s));
   };
   normalize(c->V.p);
+  if (n > 1) {
+    // A start vector from the previous step lies in the symmetry subspace of
+    // that step's state (H commutes with S^2 and with the spin flip), and an
+    // FP64 Krylov space never leaves it: if the lowest state of this position
+    // lies in another subspace, it would never be found.  A fixed seeded
+    // admixture of relative size ~6e-4 restores a component along every
+    // eigenvector, as in a Lanczos run from a random start.
+    CK(launch_fill_guess(c->t.p, n, 0x5eedull, s));
+    CK(launch_axpy(c->V.p, c->t.p, kGuessAdmixture / std::sqrt((double)n), n, s));
+    normalize(c->V.p);
+  }
   int k = 1;
   hpsi_dev(c, c->V.p, c->AV.p, fp64);
   // G[0][0]
@@ -2506,6 +2524,20 @@ extern "C" int dmrg_davidson(dmrg_ctx *c, double tol, int max_iter, double *ener
   API_END
 }
 
+extern "C" int dmrg_davidson_lowp(dmrg_ctx *c, double tol, int max_iter, double *energy, int *iters) {
+  API_BEGIN
+  if (!c || !(tol > 0.0) || max_iter < 1) throw Fail{DMRG_EINVAL, "bad arguments"};
+  build_hplan(c);
+  bool conv = false;
+  const long long h0 = c->hpsi_calls;
+  davidson_core(c, tol, 0.0, max_iter, !c->plan.lowp, energy, nullptr, conv);
+  if (c->plan.lowp) c->dav_iters_lowp += c->hpsi_calls - h0;
+  if (iters) *iters = (int)(c->hpsi_calls - h0);
+  check_status(c);
+  if (!conv) throw Fail{DMRG_ENOCONV, "Davidson did not reach the tolerance"};
+  API_END
+}
+
 extern "C" int dmrg_renormalize(dmrg_ctx *c, int direction, const int *kept, const double *O,
                                 double *discarded_weight) {
   API_BEGIN
@@ -3044,6 +3076,23 @@ static double *noalloc_scratch() {
 
 extern "C" long long dmrg_hpsi_noalloc_capacity(void) { return kNoAllocScratchDoubles; }
 
+extern "C" int dmrg_check_status(dmrg_ctx *c) {
+  API_BEGIN
+  if (!c) throw Fail{DMRG_EINVAL, "ctx is NULL"};
+  check_status(c);
+  API_END
+}
+
+extern "C" int dmrg_debug_set_wait_limit(long long tries) {
+  set_tc_wait_tries(tries);
+  return DMRG_OK;
+}
+
+extern "C" int dmrg_debug_fail_alloc(long long n) {
+  g_fail_alloc_after.store(n > 0 ? n : 0);
+  return DMRG_OK;
+}
+
 extern "C" int dmrg_hpsi_noalloc(dmrg_ctx *c, const double *psi, double *sigma) {
   API_BEGIN
   if (!c || !psi || !sigma) throw Fail{DMRG_EINVAL, "NULL argument"};
@@ -3059,9 +3108,11 @@ extern "C" int dmrg_hpsi_noalloc(dmrg_ctx *c, const double *psi, double *sigma) 
                                 " doubles of H.psi scratch; the no-allocation scratch holds " +
                                 std::to_string(kNoAllocScratchDoubles) + " (use dmrg_hpsi)"};
   double *scratch = noalloc_scratch();
+  // a time-out left by an earlier call is not this call's: clear the status word
+  // (a time-out of this call is read by dmrg_check_status or the next synchronizing call)
+  CK(cudaMemsetAsync(c->dstatus.p, 0, 8 * sizeof(int), c->stream));
   CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
-  ch.launch_with_scratch(scratch, lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream,
-                         c->dstatus.p);
+  ch.launch(lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream, c->dstatus.p, scratch);
   API_END
 }
 

@@ -123,6 +123,8 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 // shape 1: every group has m, q <= 64 and every entry p <= 64 (MMA M = 64, four CTAs per SM);
 // shape 2: m <= 64, q and p <= 32 (five CTAs per SM); shape 0: the rest;
 // *status (8 ints) is raised if an mbarrier wait ran out
+// pipeline-wait limit of the tensor-core kernel (tries <= 0: the default)
+void set_tc_wait_tries(long long tries);
 cudaError_t launch_chain_tc2(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
                              const uint8_t *psitiles, uint64_t db, int *counter, int *status, int shape,
                              cudaStream_t s);

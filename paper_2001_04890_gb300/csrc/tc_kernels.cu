@@ -14,6 +14,15 @@ namespace dmrg {
 
 static constexpr long long kMaxWaitTries = 1ll << 22;  // bounded mbarrier waits
 
+// Polls of the tensor-core kernel's pipeline waits (the waits that order the
+// jobs); the drain waits before TMEM is released and the CTA exits always take
+// kMaxWaitTries.  Changed only by dmrg_debug_set_wait_limit, so that a test can
+// make the pipeline waits run out and see the time-out reported: with 0 polls
+// every pipeline wait gives up at once, before any copy or MMA is issued.
+static std::atomic<long long> g_tc_wait_tries{kMaxWaitTries};
+
+void set_tc_wait_tries(long long tries) { g_tc_wait_tries.store(tries >= 0 ? tries : kMaxWaitTries); }
+
 __global__ void __launch_bounds__(128) tc_selftest_kernel(const float *__restrict__ A,
                                                           const float *__restrict__ B, float *C,
                                                           int N, int K, int *status) {
@@ -254,8 +263,8 @@ __device__ __noinline__ void t2_timeout(int *status, uint64_t *bar, int site, ui
 
 // single-thread bounded wait that gives up early when another role aborted
 __device__ __forceinline__ bool t2_wait1(uint64_t *bar, uint32_t parity, volatile int *abort, int *status,
-                                         int site, int aux0, int aux1) {
-  for (long long i = 0; i < kMaxWaitTries; ++i) {
+                                         int site, int aux0, int aux1, long long tries) {
+  for (long long i = 0; i < tries; ++i) {
     if (tc::mbar_try_wait(bar, parity)) return true;
     if ((i & 63) == 63 && *abort) return false;
   }
@@ -266,8 +275,8 @@ __device__ __forceinline__ bool t2_wait1(uint64_t *bar, uint32_t parity, volatil
 
 // warp-uniform bounded wait (all 32 lanes take the same decision)
 __device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatile int *abort, int *status,
-                                         int site, int aux0, int aux1) {
-  for (long long i = 0; i < kMaxWaitTries; ++i) {
+                                         int site, int aux0, int aux1, long long tries) {
+  for (long long i = 0; i < tries; ++i) {
     if (__all_sync(0xffffffffu, tc::mbar_try_wait(bar, parity))) return true;
     if ((i & 63) == 63 && __any_sync(0xffffffffu, *abort)) return false;
   }
@@ -286,7 +295,8 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
                                                                const TcGroup *__restrict__ G, int ngroups,
                                                                const uint8_t *__restrict__ optiles,
                                                                const uint8_t *__restrict__ psitiles,
-                                                               uint64_t db, int *counter, int *status) {
+                                                               uint64_t db, int *counter, int *status,
+                                                               long long tries) {
   extern __shared__ __align__(1024) uint8_t smem[];
   using S = T2Shape<MR, TC, CTAS>;
   T2Bars *B = reinterpret_cast<T2Bars *>(smem + S::BAR_OFF);
@@ -334,7 +344,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
       for (int gl = 0; ok; ++gl) {
         // take the next output block and publish it to the other roles
         const int r = gl % T2_GR;
-        if (!t2_wait1(&B->gempty[r], ((uint32_t)(gl / T2_GR) & 1u) ^ 1u, abort, status, 101, j, gl)) break;
+        if (!t2_wait1(&B->gempty[r], ((uint32_t)(gl / T2_GR) & 1u) ^ 1u, abort, status, 101, j, gl, tries)) break;
         const int gi0 = atomicAdd(counter, 1);
         const int gi = gi0 < ngroups ? gi0 : -1;
         gidx[r] = gi;
@@ -358,7 +368,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
           for (int c = 0; c < nch1 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 102, j, (int)u)) {
+            if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 102, j, (int)u, tries)) {
               ok = false;
               break;
             }
@@ -378,7 +388,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
             for (int c = 0; c < nch2 && ok; ++c, ++j) {
               const int s = j % T2_NS;
               const uint32_t u = (uint32_t)(j / T2_NS);
-              if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 103, j, (int)u)) {
+              if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 103, j, (int)u, tries)) {
                 ok = false;
                 break;
               }
@@ -406,7 +416,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
       bool ok = true;
       for (; ok; ++gl) {
         const int r = gl % T2_GR;
-        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 104, j, ls)) break;
+        if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 104, j, ls, tries)) break;
         const int gi = gidx[r];
         tc::mbar_arrive(&B->gempty[r]);
         if (gi < 0) break;
@@ -420,7 +430,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
           const int n16 = ceil16(e.n), p16 = ceil16(e.p);
           const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
           if (ls > 0) {  // T of the previous stack has been read
-            if (!t2_wait1(&B->tempty, (uint32_t)(ls - 1) & 1u, abort, status, 105, j, ls)) {
+            if (!t2_wait1(&B->tempty, (uint32_t)(ls - 1) & 1u, abort, status, 105, j, ls, tries)) {
               ok = false;
               break;
             }
@@ -430,7 +440,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
           for (int c = 0; c < nch1 && ok; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 106, j, ls)) {
+            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 106, j, ls, tries)) {
               ok = false;
               break;
             }
@@ -451,7 +461,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
           if (!ok) break;
           tc::mma_commit(&B->tfull);
           if (dfirst && gl > 0) {  // D of the previous block has been written out
-            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 107, j, ls)) {
+            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 107, j, ls, tries)) {
               ok = false;
               break;
             }
@@ -461,8 +471,8 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
             for (int c = 0; c < nch2 && ok; ++c, ++j) {
               const int s = j % T2_NS;
               const uint32_t u = (uint32_t)(j / T2_NS);
-              if (!t2_wait1(&B->full[s], u & 1u, abort, status, 108, j, ls) ||
-                  !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 109, j, ls)) {
+              if (!t2_wait1(&B->full[s], u & 1u, abort, status, 108, j, ls, tries) ||
+                  !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 109, j, ls, tries)) {
                 ok = false;
                 break;
               }
@@ -497,7 +507,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
     bool ok = true;
     for (; ok; ++gl) {
       const int r = gl % T2_GR;
-      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 110, j, ls)) break;
+      if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 110, j, ls, tries)) break;
       const int gi = gidx[r];
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&B->gempty[r]);
@@ -513,7 +523,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
         const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
         const float f = mine >= 0 && mine < ns ? E[ei + mine].f : 0.f;
         j += nch1;
-        if (!t2_waitw(&B->tfull, (uint32_t)ls & 1u, abort, status, 111, j, ls)) {
+        if (!t2_waitw(&B->tfull, (uint32_t)ls & 1u, abort, status, 111, j, ls, tries)) {
           ok = false;
           break;
         }
@@ -523,7 +533,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
           for (int c = 0; c < nch2; ++c, ++j) {
             const int s = j % T2_NS;
             const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 112, j, (int)u)) {
+            if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 112, j, (int)u, tries)) {
               ok = false;
               break;
             }
@@ -558,7 +568,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
       }
       if (!ok) break;
       // ---- output block: D (TMEM) -> FP64 global, then release D
-      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status, 113, j, ls)) {
+      if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status, 113, j, ls, tries)) {
         ok = false;
         break;
       }
@@ -588,6 +598,7 @@ template <int MR, int TC, int CTAS>
 static cudaError_t launch_tc2_shape(const TcEntry *e, const TcGroup *g, int ngroups, const uint8_t *optiles,
                                    const uint8_t *psitiles, uint64_t db, int *counter, int *status,
                                    cudaStream_t s) {
+  const long long tries = g_tc_wait_tries.load();
   using S = T2Shape<MR, TC, CTAS>;
   static_assert(S::BAR_OFF + (int)sizeof(T2Bars) <= S::SMEM_LAUNCH, "shared memory budget");
   // the launch size caps resident CTAs per SM at CTAS, so their TMEM fits the SM's 512 columns
@@ -605,7 +616,7 @@ static cudaError_t launch_tc2_shape(const TcEntry *e, const TcGroup *g, int ngro
   if (err != cudaSuccess) return err;
   const int grid = std::min(ngroups, CTAS * std::max(sms, 1));
   add_kernel_launches(1);
-  kern<<<grid, T2_THREADS, S::SMEM_LAUNCH, s>>>(e, g, ngroups, optiles, psitiles, db, counter, status);
+  kern<<<grid, T2_THREADS, S::SMEM_LAUNCH, s>>>(e, g, ngroups, optiles, psitiles, db, counter, status, tries);
   return cudaGetLastError();
 }
 
