@@ -1,12 +1,16 @@
 """Benchmark of the two-site QC-DMRG hot path on GB300 (one JSON line on rank 0).
 
-A step is one two-site DMRG iteration at the middle bond of the workload:
-Davidson to tolerance from a fixed start vector (every H.psi of Eq. dgemm),
-density-matrix truncation and renormalization of the new left block
-(Sec. 2.1, Sec. 2.2.1-2.2.3).  Inputs are synthetic (seeded integrals and
-seeded random sector-orthonormal block bases) with the workload's shape.
+Default: the FeMoco-shaped middle bond (L=76, N=113, 2Sz=1, M=3000; block
+bases grown from seeded random sector-orthonormal O), split-BF16 x3 tensor-core
+H.psi (Eq. dgemm, Sec. 2.2.1).  A step is a fixed chunk of the working-precision
+Davidson iteration (dmrg_davidson_lowp from a fixed start vector: one H.psi per
+iteration plus FP64 orthogonalisation, subspace eigenproblem and residual).
+Untimed extras: the FP32 and FP64 sigma of the same psi (relative error), the
+FP64 H.psi and Davidson iteration, one renormalization (Eq. renorm_mat), and a
+sub-line with the FP64 L=24/M=512 step (Davidson to 1e-8 + renormalization)
+against its mixed-precision runs (|dE|, overlap).
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c2] [--impl reference]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--workload c5a] [--impl reference]
 """
 from __future__ import annotations
 
@@ -26,27 +30,39 @@ sys.path.insert(0, ROOT)
 
 METRIC = "H·ψ TFLOP/s & Davidson s/iter at M; mixed vs FP64 GPU at |ΔE|≤1e-6 Eh"
 
+# hpsi_flops: algorithmic FLOPs of one middle-bond H.psi (sum over the task list of
+# 2 min(mnp + mpq, npq + mnq), identity sides free), counted once by the host
+# planner from the workload's sector tables (checked against the planner by
+# tests/test_workloads_cpu.py), so that the oracle arm needs no library call.
+# oracle: the workload the FP64 oracle times as the CPU baseline and reference arm
+# (it cannot build the L=40 or L=76 blocks within host memory and time).
 WORKLOADS = {
     # FP64 two-site DMRG, L=24, N=24, Sz=0, M=512, Davidson tol 1e-8, middle bond
     "c2": dict(name="L24_N24_Sz0_M512_fp64_middle_bond", L=24, N=24, two_sz=0, M=512, tol=1e-8,
-               precision=0),
+               precision=0, hpsi_flops=19930869124.0, oracle="c2"),
     # mixed-precision workload: L=40, N=40, Sz=0, M=2000 (middle bond)
     "c3": dict(name="L40_N40_Sz0_M2000_middle_bond", L=40, N=40, two_sz=0, M=2000, tol=1e-8,
-               precision=1),
+               precision=2, hpsi_flops=1200097633784.0, oracle="c2"),
     # FeMoco-shaped: L=76, N=113, 2Sz=1, M=3000 / 6000 (middle bond)
     "c5a": dict(name="L76_N113_Sz1_M3000_middle_bond", L=76, N=113, two_sz=1, M=3000, tol=1e-8,
-                precision=1),
+                precision=2, hpsi_flops=4254718080252.0, oracle="c2"),
     "c5b": dict(name="L76_N113_Sz1_M6000_middle_bond", L=76, N=113, two_sz=1, M=6000, tol=1e-8,
-                precision=1),
+                precision=2, hpsi_flops=31452027390656.0, oracle="c2"),
     # batched: 256 independent instances (seeds 0..255), L in 10..20, N=L, M in 64..256
     "c4": dict(name="batched_256_L10-20_M64-256_middle_bonds", L=0, N=0, two_sz=0, M=0, tol=1e-8,
-               precision=1, instances=256),
+               precision=1, instances=256, oracle="c2"),
     # small case: L=8, N=8, M=64
     "c1": dict(name="L8_N8_Sz0_M64_fp64_middle_bond", L=8, N=8, two_sz=0, M=64, tol=1e-9,
-               precision=0),
+               precision=0, hpsi_flops=26282476.0, oracle="c1"),
 }
 
+for _key, _wl in WORKLOADS.items():
+    _wl["key"] = _key
+
+DAVIDSON_ITERS_PER_STEP = 4  # working-precision Davidson iterations per timed step
+
 FP64_NOMINAL_TFLOPS = 1.25  # GB300 FP64 (nominal, recipe table)
+FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA units x 2 FLOP x max SM clock
 
 # DRAM bytes (read + write) per launch of the dominant H.psi kernel, from one ncu
 # capture of the unchanged kernel at that workload and precision (else null)
@@ -118,14 +134,10 @@ def _peaks():
         return {}
 
 
-def _flops_fn(wl):
-    """Algorithmic H.psi FLOPs for given block sector tables (host-only planner of the library)."""
-    from paper_2001_04890_gb300 import binding, workloads
-    h, v = workloads.integrals(wl["L"], seed=0)
-
-    def f(sec_l, sec_r, k):
-        return binding.plan_hpsi_flops(h, v, wl["N"], wl["two_sz"], k, sec_l, sec_r)[0]
-    return f
+def _oracle_workload(wl):
+    """The workload the oracle times for this one, and its recorded H.psi FLOPs."""
+    owl = dict(WORKLOADS[wl.get("oracle", "c2")])
+    return owl, owl["hpsi_flops"]
 
 
 def _setup(wl, precision, stream, dev, release=False):
@@ -230,6 +242,128 @@ def run_gpu(args, wl, rank, world, precision, e2e=True, sample_clocks=True):
     return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st, plan_s=plan_s,
                 step_ms=step_ms_max, iters=iters, energy=energy, e2e_ms=e2e_ms, tune=tune,
                 h2d=psi0_host.nbytes, d2h=d2h_bytes, clocks=clocks, k=k, e_mid=e_mid, psi_mid=psi_mid)
+
+
+def run_davidson_bench(args, wl, rank, world, precision):
+    """The default measurement: working-precision Davidson iterations at the middle bond.
+
+    Each timed step runs DAVIDSON_ITERS_PER_STEP iterations of dmrg_davidson_lowp
+    from the same start vector (one H.psi per iteration and one for the start
+    vector); every block goes to the tensor-core kernel in split-BF16 x3.
+    """
+    import torch
+    from paper_2001_04890_gb300 import binding, workloads
+
+    dev = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(dev)
+    stream = torch.cuda.Stream()
+    t0 = time.perf_counter()
+    ctx, k = _setup(wl, precision, stream, dev, release=True)  # only the middle-bond blocks stay resident
+    setup_s = time.perf_counter() - t0
+    if precision == binding.PREC_BF16X3:
+        ctx.set_tune(tc_min=1, by_work=1)  # every output block on the tensor cores
+    blocks, dim = ctx.psi_layout()
+    t_plan = time.perf_counter()
+    flops_per_hpsi, ntasks = ctx.hpsi_flops()  # builds the position's H.psi plan (host lists + upload)
+    plan_s = time.perf_counter() - t_plan
+    tune = ctx.get_tune()
+    psi0_host = workloads.gaussian(dim, seed=1)
+    psi0_host /= np.linalg.norm(psi0_host)
+    with torch.cuda.stream(stream):
+        psi0_dev = torch.from_numpy(psi0_host).to(f"cuda:{dev}")
+        flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=f"cuda:{dev}")
+    stream.synchronize()
+    nit = DAVIDSON_ITERS_PER_STEP
+
+    def step():
+        ctx.set_psi(psi0_dev)
+        return ctx.davidson_lowp(tol=1e-300, max_iter=nit, allow_noconv=True)
+
+    for _ in range(args.warmup):
+        step()
+    stream.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    ctx.stats(reset=True)
+    sampler, clk_path = _clock_sampler()
+    time.sleep(0.3)
+    ev, energy = [], None
+    for _ in range(args.steps):
+        with torch.cuda.stream(stream):
+            flush.fill_(1.0)  # L2 flush between timed steps (256 MB > 129 MB L2)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        energy, _ = step()
+        b.record(stream)
+        ev.append((a, b))
+    stream.synchronize()
+    st = ctx.stats(reset=True)
+    step_ms = sum(a.elapsed_time(b) for a, b in ev)
+    # end to end through the C ABI with HOST buffers: H2D of the start vector and D2H of
+    # the Ritz vector inside the timed region
+    pin_in = torch.from_numpy(psi0_host).pin_memory()
+    out = np.empty(dim)
+    e2e_ms = 0.0
+    for _ in range(args.steps):
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        ctx.set_psi(pin_in.numpy())
+        ctx.davidson_lowp(tol=1e-300, max_iter=nit, allow_noconv=True)
+        ctx.get_psi(out)
+        e2e_ms += (time.perf_counter() - t1) * 1e3
+    time.sleep(0.2)
+    if sampler is not None:
+        sampler.terminate()
+        sampler.wait()
+    clocks = _clock_summary(clk_path, dev) if sampler is not None else None
+    step_ms_max = max_over_ranks(step_ms, f"cuda:{dev}")
+    extra = {}
+    if rank == 0 and not args.no_extras:
+        extra = _precision_extras(ctx, psi0_dev, k)
+    ctx.close()
+    return dict(dim=dim, flops_per_hpsi=flops_per_hpsi, ntasks=ntasks, stats=st, plan_s=plan_s,
+                setup_s=setup_s, step_ms=step_ms_max, energy=energy, e2e_ms=e2e_ms, tune=tune,
+                h2d=psi0_host.nbytes, d2h=out.nbytes, clocks=clocks, k=k, extra=extra)
+
+
+def _precision_extras(ctx, psi_dev, k):
+    """Untimed: sigma of one psi in each precision (relative error against FP64), the
+    H.psi time and one Davidson iteration in FP32 and FP64, and one renormalization."""
+    import torch
+    from paper_2001_04890_gb300 import binding
+    out = {}
+    sig = {}
+    for name, prec in (("bf16x3", binding.PREC_BF16X3), ("fp32", binding.PREC_FP32), ("fp64", binding.PREC_FP64)):
+        if name != "bf16x3":
+            ctx.set_precision(prec)
+        t0 = time.perf_counter()
+        ctx.hpsi(psi_dev)  # builds this precision's task list
+        torch.cuda.synchronize()
+        plan_s = time.perf_counter() - t0
+        ctx.stats(reset=True)
+        sig[name] = ctx.hpsi(psi_dev).cpu().numpy()
+        st = ctx.stats(reset=True)
+        r = {"hpsi_ms": st["hpsi_ms"], "hpsi_tflops": st["hpsi_flops"] / (st["hpsi_ms"] * 1e-3) / 1e12,
+             "plan_s": plan_s}
+        if name != "bf16x3":
+            ctx.set_psi(psi_dev)
+            t0 = time.perf_counter()
+            _, it = ctx.davidson_lowp(tol=1e-300, max_iter=1, allow_noconv=True)
+            torch.cuda.synchronize()
+            r["davidson_s_per_iter"] = (time.perf_counter() - t0) / max(it, 1)
+        out[name] = r
+        print(json.dumps({name: r}), file=sys.stderr, flush=True)
+    ref = sig["fp64"]
+    for name in ("bf16x3", "fp32"):
+        out[name]["sigma_rel_err_vs_fp64"] = float(np.max(np.abs(sig[name] - ref)) / np.max(np.abs(ref)))
+    ctx.set_position(k, 1)
+    ctx.set_psi(psi_dev)
+    t0 = time.perf_counter()
+    ctx.renormalize(+1)
+    torch.cuda.synchronize()
+    out["renormalize_s"] = time.perf_counter() - t0
+    return out
 
 
 def _shape_key(tune):
@@ -538,15 +672,19 @@ def large_workload(wl, iters=4):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="c5a", choices=sorted(WORKLOADS))
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--no-mixed", action="store_true", help="skip the FP32-matvec comparison run")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the untimed FP32 / FP64 comparisons, the renormalization and the sub-line")
+    ap.add_argument("--no-mixed", action="store_true", help="FP64 step mode: skip the mixed-precision runs")
+    ap.add_argument("--fp64-step", action="store_true",
+                    help="the FP64 step mode (Davidson to tol + renormalization, mixed runs beside it)")
     ap.add_argument("--profile-hpsi", type=int, default=0, metavar="N",
                     help="setup, then N H.psi calls in an NVTX range 'hpsi' (for ncu); no JSON line")
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "bf16x3"])
+    ap.add_argument("--precision", default="bf16x3", choices=["fp64", "fp32", "bf16x3"])
     ap.add_argument("--no-autotune", dest="autotune", action="store_false",
                     help="keep the default launch shape instead of timing candidates at plan time")
     ap.add_argument("--mixed-step", type=float, default=0.0, metavar="TOL",
@@ -566,13 +704,18 @@ def main():
     if args.M:
         wl["M"] = args.M
         wl["name"] = wl["name"].replace(f"M{WORKLOADS[args.workload]['M']}", f"M{args.M}")
+        wl.pop("hpsi_flops", None)
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if args.impl == "reference":
         if rank != 0:
             return 0
         from oracle import baseline
-        line = baseline.reference_line(wl, args.steps, args.warmup, METRIC, _flops_fn(wl))
+        owl, oflops = _oracle_workload(wl)
+        note = "" if owl["name"] == wl["name"] else (
+            f"; the oracle cannot build the {wl['name']} blocks within host memory and time, so it is timed "
+            f"on {owl['name']}")
+        line = baseline.reference_line(owl, args.steps, args.warmup, METRIC, oflops, note)
         print(json.dumps(line))
         return 0
     prec = {"fp64": 0, "fp32": 1, "bf16x3": 2}[args.precision]
@@ -594,15 +737,107 @@ def main():
     if world > 1:
         import torch
         torch.distributed.init_process_group("nccl")
-    r = run_gpu(args, wl, rank, world, prec)
+    if args.fp64_step:
+        line = fp64_step_line(args, wl, rank, world)
+    else:
+        line = davidson_line(args, wl, rank, world, prec)
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline at N = 1 only
+        try:
+            from oracle import baseline
+            owl, oflops = _oracle_workload(wl)
+            note = "" if owl["name"] == wl["name"] else (
+                f"; the oracle cannot build the {wl['name']} blocks within host memory and time, so its "
+                f"H.psi rate is measured on {owl['name']}")
+            line["cpu_baseline"] = baseline.cpu_baseline(owl, oflops, note=note)
+        except Exception as exc:  # reported, never silently replaced
+            line["cpu_baseline"] = {"error": str(exc)}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        import torch
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def davidson_line(args, wl, rank, world, prec):
+    """The default JSON line: working-precision Davidson iterations at the middle bond."""
+    r = run_davidson_bench(args, wl, rank, world, prec)
+    st = r["stats"]
+    K = args.steps
+    value = whole_job_tflops(st["hpsi_flops"], world, r["step_ms"])
+    kernel_tflops = st["hpsi_flops"] / (st["hpsi_ms"] * 1e-3) / 1e12 if st["hpsi_ms"] > 0 else None
+    peaks = _peaks()
+    if prec == 2:
+        peak = peaks.get("bf16_tflops")
+        roof = {"bound": "tensor", "kernel": "chain_tc2_kernel (H.psi, split-BF16 x3 on tcgen05)",
+                "achieved": kernel_tflops, "peak": peak / 3.0 if peak else None,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) / 3: three bf16 passes per product"
+                               " (of measured)",
+                "unit": "TFLOP/s"}
+    else:
+        roof = {"bound": "alu", "kernel": "chain kernels (SIMT)", "achieved": kernel_tflops,
+                "peak": FP64_NOMINAL_TFLOPS if prec == 0 else FP32_SIMT_TFLOPS,
+                "peak_source": "unit counts x 2.07 GHz (no measured SIMT peak)", "unit": "TFLOP/s"}
+    roof["frac"] = (kernel_tflops / roof["peak"]) if (kernel_tflops and roof["peak"]) else None
+    roof["traffic"] = TRAFFIC_PER_LAUNCH.get((args.workload, prec, wl["M"], _shape_key(r["tune"])))
+    hps = st["hpsi_calls"] / K
+    line = {
+        "metric": METRIC,
+        "value": value,
+        "unit": "TFLOP/s",
+        "n_gpus": world,
+        "steps": K,
+        "warmup": args.warmup,
+        "ms_per_step": r["step_ms"] / K,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": {0: "f64", 1: "f32", 2: "bf16x3"}[prec],
+        "data": "synthetic",
+        "config": {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"],
+                   "M": wl["M"], "position": r["k"], "psi_dim": r["dim"], "hpsi_tasks": r["ntasks"],
+                   "step": f"{DAVIDSON_ITERS_PER_STEP} working-precision Davidson iterations from a fixed "
+                           f"start vector ({hps:g} H.psi per step)",
+                   "l2": "flushed between timed steps (256 MB write)", "launch_shape": r["tune"],
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "davidson_s_per_iter": (r["step_ms"] * 1e-3) / max(st["hpsi_calls"], 1),
+        "hpsi_per_step": hps,
+        "hpsi_kernel_tflops": kernel_tflops,
+        "hpsi_ms": st["hpsi_ms"] / max(st["hpsi_calls"], 1),
+        "hpsi_gflop_per_call": r["flops_per_hpsi"] / 1e9,
+        "hpsi_plan_s": r["plan_s"],
+        "setup_s": r["setup_s"],
+        "energy": r["energy"],
+        "roofline": roof,
+        "e2e": {"value": st["hpsi_flops"] / (r["e2e_ms"] * 1e-3) / 1e12, "unit": "TFLOP/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": st["kernel_launches"],
+        "clocks": r["clocks"],
+        "cpu_baseline": None,
+    }
+    if r["extra"]:
+        line["precisions"] = r["extra"]
+    if rank == 0 and world == 1 and not args.no_extras:
+        sub = argparse.Namespace(**vars(args))
+        sub.steps, sub.warmup, sub.autotune, sub.tune = 2, 1, True, ""
+        sl = fp64_step_line(sub, dict(WORKLOADS["c2"]), rank, world)
+        line["c2_fp64_step"] = {k: sl[k] for k in ("value", "ms_per_step", "davidson_s_per_iter",
+                                                   "davidson_iters_per_step", "hpsi_kernel_tflops",
+                                                   "roofline", "energy", "mixed_fp32", "mixed_bf16x3", "config")
+                                if k in sl}
+    return line
+
+
+def fp64_step_line(args, wl, rank, world):
+    """The FP64 step: Davidson to tol from a fixed start + one renormalization, with the
+    same step in the mixed precisions beside it (|dE| and overlap of the refined state)."""
+    r = run_gpu(args, wl, rank, world, 0)
     st = r["stats"]
     K = args.steps
     hpsi_flops = st["hpsi_flops"]
     value = whole_job_tflops(hpsi_flops, world, r["step_ms"])
     kernel_tflops = st["hpsi_flops"] / (st["hpsi_ms"] * 1e-3) / 1e12 if st["hpsi_ms"] > 0 else None
     dav_iters = st["davidson_iters"]
-    peaks = _peaks()
-    sm_mhz = r["clocks"].get("sm_mhz")
     line = {
         "metric": METRIC,
         "value": value,
@@ -635,7 +870,7 @@ def main():
             "peak_source": "nominal GB300 FP64 from the recipe table (no measured FP64 peak in MEASURED_PEAKS.json)",
             "unit": "TFLOP/s",
             "frac": (kernel_tflops / FP64_NOMINAL_TFLOPS) if kernel_tflops else None,
-            "traffic": TRAFFIC_PER_LAUNCH.get((args.workload, prec, wl["M"], _shape_key(r["tune"]))),
+            "traffic": TRAFFIC_PER_LAUNCH.get((wl.get("key", ""), 0, wl["M"], _shape_key(r["tune"]))),
         },
         "e2e": {"value": hpsi_flops / (r["e2e_ms"] * 1e-3) / 1e12, "unit": "TFLOP/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
@@ -643,7 +878,7 @@ def main():
         "clocks": r["clocks"],
         "cpu_baseline": None,
     }
-    if not args.no_mixed and prec == 0:
+    if not args.no_mixed:
         for key, lp, what in (
                 ("mixed_fp32", 1, "FP32 operator copies for the Davidson matvecs"),
                 ("mixed_bf16x3", 2, "split-BF16x3 tensor-core matvecs (FP32 SIMT below the routing threshold)")):
@@ -663,19 +898,7 @@ def main():
                 "overlap_vs_fp64": float(abs(np.dot(m["psi_mid"], r["psi_mid"]))),
                 "energy": m["e_mid"],
             }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:  # the oracle baseline at N = 1 only
-        try:
-            from oracle import baseline
-            line["cpu_baseline"] = baseline.cpu_baseline(wl, _flops_fn(wl))
-        except Exception as exc:  # reported, never silently replaced
-            line["cpu_baseline"] = {"error": str(exc)}
-    if rank == 0:
-        print(json.dumps(line))
-
-    if world > 1:
-        import torch
-        torch.distributed.destroy_process_group()
-    return 0
+    return line
 
 
 if __name__ == "__main__":

@@ -82,11 +82,11 @@ def sector_tables(lb, rb):
     return tl, tr
 
 
-def cpu_baseline(wl, flops_fn, budget_s=20.0):
+def cpu_baseline(wl, flops, budget_s=20.0, note=""):
     """Oracle H.psi at the middle bond, timed on the host cores for about budget_s seconds.
 
-    flops_fn(sector_table_left, sector_table_right, k) gives the algorithmic FLOPs of
-    one H.psi (the same count the GPU arm uses), so value is in the GPU arm's unit.
+    flops: the algorithmic FLOPs of one H.psi of this workload (the count the GPU
+    arm uses, recorded with the workload), so value is in the GPU arm's unit.
     """
     I, k, lb, rb, nu, nd = middle_bond(wl)
     t0 = time.perf_counter()
@@ -100,16 +100,15 @@ def cpu_baseline(wl, flops_fn, budget_s=20.0):
         hp.apply(psi)
         t += time.perf_counter() - t1
         n += 1
-    flops = flops_fn(*sector_tables(lb, rb), k)
     s = t / n
     return {"value": flops / s / 1e12, "unit": "TFLOP/s", "cores": _threads(), "kind": "oracle",
             "sample": (f"{n} oracle H.psi applications at the middle bond of {wl['name']} (psi dim "
                        f"{hp.dim}, {len(hp.terms)} two-half terms), {s:.3f} s each; block growth and "
-                       f"the oracle's operator pre-summation ({t_build:.1f} s) not timed"),
+                       f"the oracle's operator pre-summation ({t_build:.1f} s) not timed" + note),
             "s_per_hpsi": s}
 
 
-def reference_line(wl, steps, warmup, metric, flops_fn):
+def reference_line(wl, steps, warmup, metric, flops, note=""):
     """bench.py --impl reference: the oracle timed on the host cores, same metric and config."""
     I, k, lb, rb, nu, nd = middle_bond(wl)
     hp = od.HPsi(I, k, lb, rb, nu, nd)
@@ -122,7 +121,6 @@ def reference_line(wl, steps, warmup, metric, flops_fn):
         t0 = time.perf_counter()
         hp.apply(psi)
         ts.append(time.perf_counter() - t0)
-    flops = flops_fn(*sector_tables(lb, rb), k)
     s = float(np.mean(ts))
     value = flops / s / 1e12
     cores = _threads()
@@ -131,7 +129,7 @@ def reference_line(wl, steps, warmup, metric, flops_fn):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"],
                        "M": wl["M"], "position": k, "psi_dim": hp.dim,
-                       "step": "one FP64 oracle H.psi application at the middle bond (bounded sample)"},
+                       "step": "one FP64 oracle H.psi application at the middle bond (bounded sample)" + note},
             "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": cores, "kind": "oracle",
                              "sample": f"{steps} oracle H.psi applications at the middle bond after "
                                        f"{warmup} untimed ones"},

@@ -35,6 +35,36 @@ def test_reference_arm_prints_one_contract_line():
     assert d["config"]["workload"].startswith("L8_N8_Sz0_M64")
 
 
+def test_reference_arm_loads_no_library():
+    """The oracle arm times the oracle alone: the GPU library is never loaded."""
+    code = ("import runpy, sys\nsys.argv = ['bench.py', '--impl', 'reference', '--workload', 'c1', "
+            "'--steps', '1', '--warmup', '0']\n"
+            "try:\n    runpy.run_path('bench.py', run_name='__main__')\nexcept SystemExit as e:\n"
+            "    assert not e.code\n"
+            "import sys as _s\n"
+            "maps = open('/proc/self/maps').read()\n"
+            "assert 'libdmrg_gb300' not in maps, 'library loaded'\n"
+            "assert 'paper_2001_04890_gb300.binding' not in _s.modules\n"
+            "print('CLEAN')")
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=600, cwd=ROOT,
+                       env=dict(os.environ, RANK="0", WORLD_SIZE="1"))
+    assert r.returncode == 0, r.stderr
+    assert r.stdout.strip().splitlines()[-1] == "CLEAN"
+
+
+def test_large_workload_reference_arm_times_the_oracle_on_its_own_workload():
+    """For workloads whose blocks the oracle cannot build on the host, the reference
+    arm names the workload it timed instead."""
+    env = dict(os.environ, RANK="0", WORLD_SIZE="1")
+    cmd = [sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--workload", "c5a",
+           "--steps", "1", "--warmup", "0"]
+    r = subprocess.run(cmd, capture_output=True, text=True, timeout=900, env=env, cwd=ROOT)
+    assert r.returncode == 0, r.stderr
+    d = json.loads(r.stdout.strip().splitlines()[-1])
+    assert d["config"]["workload"].startswith("L24_N24_Sz0_M512")
+    assert "cannot build the L76_N113_Sz1_M3000" in d["config"]["step"]
+
+
 def test_reference_arm_other_ranks_do_nothing():
     r = _run({"RANK": "1", "WORLD_SIZE": "2"})
     assert r.returncode == 0, r.stderr

@@ -41,3 +41,24 @@ def test_integrals_are_symmetric_and_seeded():
     w = np.linalg.eigvalsh(v.reshape(49, 49))
     assert w.min() > -1e-12
     assert np.allclose(np.diag(h), -2 + 4 * np.arange(7) / 7)
+
+
+@pytest.mark.parametrize("key", ["c1", "c2", "c3", "c5a", "c5b"])
+def test_recorded_hpsi_flops_equal_the_planner_count(key):
+    """bench.py records each workload's algorithmic H.psi FLOPs (so that its oracle arm
+    loads no library); they equal the host planner's count on the same sector tables."""
+    import importlib.util
+    import os
+    from paper_2001_04890_gb300 import binding
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    spec = importlib.util.spec_from_file_location("bench_module", os.path.join(root, "bench.py"))
+    bench = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(bench)
+    wl = bench.WORKLOADS[key]
+    L, N, tsz, M = wl["L"], wl["N"], wl["two_sz"], wl["M"]
+    k = (L - 2) // 2
+    left, right = workloads.middle_bond_sectors(L, (N + tsz) // 2, (N - tsz) // 2, M, k)
+    tl = [(a, b, d) for (a, b), d in sorted(left.items()) if d > 0]
+    tr = [(a, b, d) for (a, b), d in sorted(right.items()) if d > 0]
+    h, v = workloads.integrals(L, seed=0)
+    assert binding.plan_hpsi_flops(h, v, N, tsz, k, tl, tr)[0] == wl["hpsi_flops"]
