@@ -606,47 +606,56 @@ def mixed_step_workload(args, wl, tol):
     return out
 
 
-def large_workload(wl, iters=4):
+def large_workload(wl, args, iters=4):
     """Middle bond of a large workload, grown once; each working precision in turn.
 
     Reports the block-growth time, H.psi time and TFLOP/s per precision, a few
-    Davidson iterations (s/iter) and one renormalization (on a copy of the
-    state: the renormalization itself is FP64 in every mode), plus the
-    relative difference of each low-precision sigma from the FP64 sigma.
+    Davidson iterations in the working precision (s/iter; one iteration in FP64,
+    whose H.psi takes a minute at M=6000), one renormalization, and the
+    relative difference of each low-precision sigma from the FP64 sigma.  The
+    bases are grown with FP32 renormalization products when --renorm fp32 (the
+    same bases then serve every precision); --M-right sets a smaller bond
+    dimension for the right blocks (the non-enlarged block of the paper's
+    largest run).
     """
     import torch
-    from paper_2001_04890_gb300 import workloads
+    from paper_2001_04890_gb300 import binding, workloads
     torch.cuda.set_device(0)
     stream = torch.cuda.Stream()
-    out = {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"], "M": wl["M"]}
+    out = {"workload": wl["name"], "L": wl["L"], "N": wl["N"], "two_sz": wl["two_sz"], "M": wl["M"],
+           "M_right": args.M_right or wl["M"], "renorm": args.renorm}
+    L, N, two_sz, M = wl["L"], wl["N"], wl["two_sz"], wl["M"]
+    nu, nd = (N + two_sz) // 2, (N - two_sz) // 2
+    k = (L - 2) // 2
+    h, v = workloads.integrals(L, seed=0)
+    ctx = binding.DMRG(h, v, N, two_sz, M, 0, stream=stream.cuda_stream)
+    if args.renorm == "fp32":
+        ctx.set_renorm_precision(binding.PREC_FP32)
     t0 = time.perf_counter()
-    ctx, k = _setup(wl, 0, stream, 0, release=True)  # only the middle-bond blocks stay resident
+    workloads.grow_middle_bond(ctx, L, nu, nd, M, k, seed=0, release=True, M_right=args.M_right or None)
+    torch.cuda.synchronize()
     out["setup_s"] = time.perf_counter() - t0
     _, dim = ctx.psi_layout()
     out["psi_dim"] = dim
+    out["sectors"] = [int(len(ctx.block_sectors(0))), int(len(ctx.block_sectors(1)))]
+    out["max_sector"] = [int(ctx.block_sectors(0)[:, 2].max()), int(ctx.block_sectors(1)[:, 2].max())]
     psi = torch.from_numpy(workloads.gaussian(dim, seed=1)).cuda()
     sig64 = None
-    for name, prec in (("fp64", 0), ("fp32", 1), ("bf16x3", 2)):
+    for name, prec in (("fp64", 0), ("bf16x3", 2), ("fp32", 1)):
         ctx.set_precision(prec)
+        if prec == 2:
+            ctx.set_tune(tc_min=1, by_work=1)
         t0 = time.perf_counter()
         sig = ctx.hpsi(psi)  # builds task list + temporaries
         torch.cuda.synchronize()
         plan_s = time.perf_counter() - t0
-        t0 = time.perf_counter()
-        if prec == 0:  # FP64 H.psi takes seconds here: the shape tuned at L=24/M=512, not re-timed
-            ctx.set_tune(target_chunks=32768, min_chunk=5e4, tc_min=33, by_work=0, flat_wide=0)
-            ctx.hpsi(psi)
-            tune = ctx.get_tune()
-        else:
-            tune_ms, tune = ctx.autotune(reps=1)
-        tune_s = time.perf_counter() - t0
         ctx.stats(reset=True)
-        for _ in range(3):
+        for _ in range(1 if prec == 0 else 3):
             sig = ctx.hpsi(psi)
         st = ctx.stats(reset=True)
         fl, tasks = ctx.hpsi_flops()
         ms = st["hpsi_ms"] / max(st["hpsi_calls"], 1)
-        r = {"plan_s": plan_s, "autotune_s": tune_s, "launch_shape": tune, "hpsi_ms": ms,
+        r = {"plan_s": plan_s, "launch_shape": ctx.get_tune(), "hpsi_ms": ms,
              "hpsi_tflops": fl / (ms * 1e-3) / 1e12, "gflop_per_hpsi": fl / 1e9, "tasks": tasks}
         s = sig.double().cpu().numpy()
         if sig64 is None:
@@ -656,15 +665,18 @@ def large_workload(wl, iters=4):
         ctx.set_position(k, 1)
         ctx.set_psi(psi)
         t0 = time.perf_counter()
-        e, it = ctx.davidson(tol=1e-14, max_iter=iters, allow_noconv=True)
+        e, it = ctx.davidson_lowp(tol=1e-300, max_iter=1 if prec == 0 else iters, allow_noconv=True)
         torch.cuda.synchronize()
         r["davidson_s_per_iter"] = (time.perf_counter() - t0) / max(it, 1)
+        r["davidson_hpsi"] = it
         out[name] = r
         print(json.dumps({name: r}), flush=True)
+    ctx.set_position(k, 1)
+    ctx.set_psi(psi)
     t0 = time.perf_counter()
     ctx.renormalize(+1)
     torch.cuda.synchronize()
-    out["renormalize_s_fp64"] = time.perf_counter() - t0
+    out["renormalize_s"] = time.perf_counter() - t0
     ctx.close()
     return out
 
@@ -699,6 +711,9 @@ def main():
     ap.add_argument("--sweep-max-iter", type=int, default=200, help="sweeps: matvec cap of each Davidson step")
     ap.add_argument("--large", action="store_true",
                     help="middle-bond measurement of a large workload in every precision (JSON lines)")
+    ap.add_argument("--renorm", default="fp64", choices=["fp64", "fp32"],
+                    help="--large: arithmetic of the renormalizations that grow the bases")
+    ap.add_argument("--M-right", type=int, default=0, help="--large: bond dimension of the right blocks")
     args = ap.parse_args()
     wl = dict(WORKLOADS[args.workload])
     if args.M:
@@ -723,7 +738,7 @@ def main():
         print(json.dumps(batched_workload(args, wl)))
         return 0
     if args.large:
-        print(json.dumps(large_workload(wl)))
+        print(json.dumps(large_workload(wl, args)))
         return 0
     if args.sweeps:
         print(json.dumps(sweep_workload(args, wl)))

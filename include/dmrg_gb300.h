@@ -226,6 +226,18 @@ int dmrg_davidson_lowp(dmrg_ctx *ctx, double tol, int max_iter, double *energy, 
 int dmrg_set_davidson(dmrg_ctx *ctx, int refine_keep, int sweep_max_iter);
 
 /*
+ * dmrg_set_renorm_precision -- arithmetic of the renormalization products
+ * O^T (sum of block op (x) site op) O of Eq. renorm_mat (Sec. 2.2.2), in every
+ * later dmrg_renormalize and sweep step: DMRG_PREC_FP64 (default) or
+ * DMRG_PREC_FP32 (O and the old block's operators rounded to FP32 in the
+ * products, FP32 accumulation within each chunk of products, FP64 result and
+ * FP64 sums across chunks).  The density matrix, its eigenvectors and the
+ * truncation stay FP64.  Independent of the working precision of H.psi.
+ * DMRG_EINVAL for a NULL context or another precision.
+ */
+int dmrg_set_renorm_precision(dmrg_ctx *ctx, int precision);
+
+/*
  * dmrg_renormalize -- truncate the enlarged block and renormalize its
  * operators (Eqs. renorm, renorm_mat; Sec. 2.2.2), then move one position.
  * direction +1: new left block l' = l (x) s_l, position k -> k+1.

@@ -81,6 +81,7 @@ def lib():
         "dmrg_block_basis": (C.c_int, [vp, C.c_int, C.c_int, ip, ip, dp, llp]),
         "dmrg_sweep_record": (C.c_int, [vp, C.c_int, C.c_double, dp, dp, dp]),
         "dmrg_set_davidson": (C.c_int, [vp, C.c_int, C.c_int]),
+        "dmrg_set_renorm_precision": (C.c_int, [vp, C.c_int]),
         "dmrg_debug_pair_rdm": (C.c_int, [C.c_int, ip, llp, dp, dp, dp]),
         "dmrg_debug_truncation": (C.c_int, [C.c_int, ip, dp, C.c_int, ip, ip, dp]),
         "dmrg_batch_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
@@ -494,6 +495,10 @@ class DMRG:
         """Ritz vectors carried between refinement steps of the mixed-precision Davidson (0: none)
         and the matvec cap of each Davidson step of a sweep."""
         _check(lib().dmrg_set_davidson(self.ctx, int(refine_keep), int(sweep_max_iter)))
+
+    def set_renorm_precision(self, precision):
+        """Arithmetic of the renormalization products: PREC_FP64 (default) or PREC_FP32."""
+        _check(lib().dmrg_set_renorm_precision(self.ctx, precision))
 
     def set_bond_dims(self, m_forward, m_backward):
         """Kept states of new left blocks (forward) and new right blocks (backward) in RDM truncations."""

@@ -761,12 +761,12 @@ static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, 
       const ChainEntry &e = xs[idx[j]];
       TcEntry &t = P.te[(size_t)base[k] + j];
       if (remaining == 0) {  // first member of a stack: the run of tasks on this psi block
-        t.stack = runs[run_i++];
+        t.stack = (uint8_t)runs[run_i++];
         remaining = t.stack;
       }
       --remaining;
-      t.n = e.n;
-      t.p = e.p;
+      t.n = (uint8_t)e.n;
+      t.p = (uint8_t)e.p;
       t.f = (float)e.f;
       src[(size_t)base[k] + j] = idx[j];
       blk[(size_t)base[k] + j] = (int)k;
@@ -803,11 +803,12 @@ static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, 
     P.ps.push_back(PsiTileSpec{(int64_t)e.y, P.psibytes, e.n, e.p});
     P.psibytes += c16(e.p) * c16(e.n) * 4;
   }
+  if (P.psibytes >= (1ull << 32)) throw Fail{DMRG_EINVAL, "psi tiles exceed the 4 GiB a task descriptor addresses"};
   parallel_for((T + 65535) / 65536, [&](size_t c) {
     for (size_t i = c * 65536; i < std::min(T, (c + 1) * 65536); ++i) {
       P.te[i].xt = voff[vid[2 * i]];
       P.te[i].zt = voff[vid[2 * i + 1]];
-      P.te[i].yt = yoff[yid[i]];
+      P.te[i].yt = (uint32_t)yoff[yid[i]];
     }
   });
   if (entry_of) entry_of->swap(src);
@@ -886,6 +887,7 @@ struct DevChain {
     ntc = (int)tg.size();
     npts = (int)ps.size();
     if (ntc == 0) return;
+    te.resize(te.size() + kTcChunkCopy, TcEntry{});  // the kernel's fixed-size descriptor chunks read past the end
     tce.upload(te, s);
     tcg.upload(tg, s);
     pts.upload(ps, s);
@@ -1065,6 +1067,7 @@ struct dmrg_ctx {
   // count, and how many had a near-degenerate cluster across the cut
   int refine_keep = 0;       // Ritz vectors carried between refinement steps (dmrg_set_davidson)
   int sweep_max_iter = 200;  // matvec cap of each Davidson step of a sweep
+  int renorm_prec = DMRG_PREC_FP64;  // renormalization products: FP64 or FP32 O (dmrg_set_renorm_precision)
   double cut_gap = std::numeric_limits<double>::infinity();
   double min_cut_gap = std::numeric_limits<double>::infinity();
   long long truncations = 0, straddled = 0;
@@ -1539,9 +1542,27 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
   }
   CL.finish(protos);
   DevChain dc;
-  dc.upload(CL, c->stream);
-  dc.launch(false, 0, 0, 0, 0, c->stream);
-  CK(cudaStreamSynchronize(c->stream));
+  if (c->renorm_prec == DMRG_PREC_FP32) {
+    // FP32 products: O (both X = O^T and Z = O) rounded to FP32, the old block's
+    // operators converted to FP32 as the kernel reads them, FP32 accumulation per
+    // output block, FP64 result
+    DBuf<float> O32;
+    const int64_t nO = (int64_t)Odev.n;
+    O32.alloc((size_t)std::max<int64_t>(nO, 1));
+    if (nO > 0) CK(launch_to_f32(O32.p, Odev.p, nO, c->stream));
+    const uint64_t d64 = eaddr(Op), f32b = (uint64_t)(uintptr_t)O32.p / 4;
+    for (auto &ce : CL.flat) {
+      ce.x = f32b + (ce.x - d64);
+      ce.z = f32b + (ce.z - d64);
+    }
+    dc.upload(CL, c->stream);
+    dc.launch(true, 0, 0, 0, 0, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+  } else {
+    dc.upload(CL, c->stream);
+    dc.launch(false, 0, 0, 0, 0, c->stream);
+    CK(cudaStreamSynchronize(c->stream));
+  }
   nb->parent = enl;
   nb->kept = kept;
   nb->Ooff = Ooff;
@@ -3401,6 +3422,14 @@ extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk
   c->tune.tc_min = tc_min;
   c->tune.by_work = by_work;
   c->plan.valid = false;
+  API_END
+}
+
+extern "C" int dmrg_set_renorm_precision(dmrg_ctx *c, int precision) {
+  API_BEGIN
+  if (!c || (precision != DMRG_PREC_FP64 && precision != DMRG_PREC_FP32))
+    throw Fail{DMRG_EINVAL, "dmrg_set_renorm_precision: NULL context or precision not FP64 / FP32"};
+  c->renorm_prec = precision;
   API_END
 }
 

@@ -99,14 +99,23 @@ struct PsiTileSpec {
   uint64_t dst;     // byte offset of its transposed tile (rows p, K n)
   int n, p;
 };
-// One task of the pipelined tensor-core chain: D += f X Y Z with X, Y^T, Z^T given as tiles
+// One task of the pipelined tensor-core chain: D += f X Y Z with X, Y^T, Z^T given as tiles.
+// 32 bytes, so any run of entries is one aligned bulk copy.
 struct TcEntry {
-  uint64_t xt, yt, zt;  // byte offsets: X tile (op arena), Y^T tile (psi tiles), Z^T tile (op arena)
-  int n, p;             // inner dims (<= 128)
+  uint64_t xt, zt;      // byte offsets of the X and Z^T tiles in the operator tile arena
+  uint32_t yt;          // byte offset of the Y^T tile in the psi tile arena
   float f;
-  int stack;            // first task of a stack: the number of consecutive tasks (same Y, same
+  uint8_t n, p;         // inner dims (<= 128)
+  uint8_t stack;        // first task of a stack: the number of consecutive tasks (same Y, same
                         // output block) whose X run stacked along M in one stage 1; others 0
+  uint8_t pad0;
+  uint32_t pad1;
 };
+static_assert(sizeof(TcEntry) == 32, "TcEntry is 32 bytes");
+// The tensor-core kernel reads task descriptors in chunks of kTcChunkCopy entries,
+// kTcChunk apart: the entry array carries kTcChunkCopy zero entries after its end.
+constexpr int kTcChunk = 56;
+constexpr int kTcChunkCopy = 64;
 struct TcGroup {
   uint64_t d;       // element offset of the output block (or scratch slot)
   int drs, dcs, m, q;

@@ -209,6 +209,15 @@ cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi
 
 static constexpr int T2_NS = 3;
 static constexpr int T2_MAXSTACK = 8;  // tasks stacked along M in one stage 1 (128 rows / 16)
+// Task descriptors reach the roles through a ring of T2_DR shared-memory chunks,
+// each one bulk copy of T2_DCOPY entries: the stacks that start among the
+// chunk's first T2_DC entries (a stack has at most T2_MAXSTACK members, so all of
+// them are in the copy).  The producer requests chunks ahead of use, so no role
+// waits on a global load per stack.
+static constexpr int T2_DR = 3;
+static constexpr int T2_DC = kTcChunk;
+static constexpr int T2_DCOPY = kTcChunkCopy;
+static_assert(T2_DCOPY >= T2_DC + T2_MAXSTACK, "a chunk copy holds every stack that starts in it");
 static constexpr int T2_THREADS = 192;
 
 // Three shapes of the kernel, by the size of the output blocks they take:
@@ -223,10 +232,11 @@ struct T2Shape {
   static constexpr int BHALF = TC * T2_W * 4;  // B operand: at most TC rows, hi + lo
   static constexpr int ALO = MR * T2_W * 2;    // lo part of the converter-written A operand
   static constexpr int STAGE = AHALF + BHALF;
-  static constexpr int BAR_OFF = T2_NS * STAGE;
+  static constexpr int DESC_OFF = T2_NS * STAGE;  // ring of task-descriptor chunks
+  static constexpr int BAR_OFF = DESC_OFF + T2_DR * T2_DCOPY * (int)sizeof(TcEntry);
   static constexpr int TCOLS = TC;             // T and D regions of TMEM
   static constexpr int CTAS_PER_SM = CTAS;
-  static constexpr int SMEM_LAUNCH = CTAS == 2 ? 100 * 1024 : CTAS == 4 ? 50 * 1024 : 40 * 1024;
+  static constexpr int SMEM_LAUNCH = CTAS == 2 ? 104 * 1024 : CTAS == 4 ? 55 * 1024 : 44 * 1024;
   // accumulator row held by TMEM lane L (-1: none)
   __device__ static __forceinline__ int row_of_lane(int L) {
     if (MR == 128) return L;
@@ -240,6 +250,8 @@ struct T2Bars {
   uint64_t full[T2_NS], cvf[T2_NS], empty[T2_NS];
   uint64_t tfull, tempty, dfull, dempty, drain;
   uint64_t gfull[T2_GR], gempty[T2_GR];
+  uint64_t qfull[T2_DR], qempty[T2_DR];  // descriptor chunks: landed / released by all six roles
+  TcGroup gdesc[T2_GR];                  // header of each published output block
   int gidx[T2_GR];
   uint32_t tslot;
   int abort;
@@ -300,6 +312,7 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
   extern __shared__ __align__(1024) uint8_t smem[];
   using S = T2Shape<MR, TC, CTAS>;
   T2Bars *B = reinterpret_cast<T2Bars *>(smem + S::BAR_OFF);
+  TcEntry *dring = reinterpret_cast<TcEntry *>(smem + S::DESC_OFF);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (warp == 0) {
     tc::tmem_alloc(&B->tslot, 2 * S::TCOLS);
@@ -320,6 +333,10 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
       tc::mbar_init(&B->gfull[r], 1);
       tc::mbar_init(&B->gempty[r], 5);  // MMA issuer + 4 converter warps
     }
+    for (int s = 0; s < T2_DR; ++s) {
+      tc::mbar_init(&B->qfull[s], 1);
+      tc::mbar_init(&B->qempty[s], 6);  // producer + MMA issuer + 4 converter warps
+    }
     B->abort = 0;
   }
   // A halves: rows beyond a block's 16-row padding only feed discarded TMEM lanes,
@@ -335,71 +352,104 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
   const uint32_t tbase = B->tslot, tT = tbase, tD = tbase + S::TCOLS;
   volatile int *abort = &B->abort;
   volatile int *gidx = B->gidx;
+  // descriptor chunk q (the CTA's running chunk count) lives in ring slot q % T2_DR
+  auto chunk = [&](int q) { return dring + (q % T2_DR) * T2_DCOPY; };
 
   if (warp == 4) {
     // ---------------- producer
     if (lane == 0) {
-      int j = 0;
+      int j = 0, qacc = 0, qreq = 0;
+      int qlast[T2_DR];
+#pragma unroll
+      for (int s = 0; s < T2_DR; ++s) qlast[s] = -1;
       bool ok = true;
       for (int gl = 0; ok; ++gl) {
-        // take the next output block and publish it to the other roles
+        // take the next output block and publish it (index and header) to the other roles
         const int r = gl % T2_GR;
         if (!t2_wait1(&B->gempty[r], ((uint32_t)(gl / T2_GR) & 1u) ^ 1u, abort, status, 101, j, gl, tries)) break;
         const int gi0 = atomicAdd(counter, 1);
         const int gi = gi0 < ngroups ? gi0 : -1;
+        TcGroup g{};
+        if (gi >= 0) g = G[gi];
+        B->gdesc[r] = g;
         gidx[r] = gi;
-        tc::mbar_arrive(&B->gfull[r]);  // release: the index is visible to the waiters
+        tc::mbar_arrive(&B->gfull[r]);  // release: index and header are visible to the waiters
         if (gi < 0) break;
-        const TcGroup g = G[gi];
         const int m16 = ceil16(g.m), q16 = ceil16(g.q), e_end = g.first + g.count;
-        for (int ei = g.first; ei < e_end && ok;) {
-          const TcEntry e = E[ei];
-          const int ns = min(max(e.stack, 1), T2_MAXSTACK);
-          uint64_t xts[T2_MAXSTACK], zts[T2_MAXSTACK];
-#pragma unroll
-          for (int i = 0; i < T2_MAXSTACK; ++i)
-            if (i < ns) {
-              xts[i] = E[ei + i].xt;
-              zts[i] = E[ei + i].zt;
-            }
-          const int n16 = ceil16(e.n), p16 = ceil16(e.p);
-          const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-          // stage 1 of the stack: the X chunks of every member, rows stacked, and one Y^T chunk
-          for (int c = 0; c < nch1 && ok; ++c, ++j) {
-            const int s = j % T2_NS;
-            const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 102, j, (int)u, tries)) {
+        const int nch = (g.count + T2_DC - 1) / T2_DC;
+        // request descriptor chunks up to T2_DR - 1 ahead of the one in use
+        auto request_upto = [&](int qhi) {
+          for (; ok && qreq <= qhi && qreq < qacc + nch; ++qreq) {
+            const int s = qreq % T2_DR;
+            const uint32_t u = (uint32_t)(qreq / T2_DR);
+            if (!t2_wait1(&B->qempty[s], (u & 1u) ^ 1u, abort, status, 114, j, qreq, tries)) {
               ok = false;
               break;
             }
-            uint8_t *st = smem + s * S::STAGE;
-            const int w = min(T2_W, n16 - c * T2_W);
-            const uint32_t bx = (uint32_t)(m16 * w * 2), by = (uint32_t)(p16 * w * 4);
-            tc::mbar_arrive_expect_tx(&B->full[s], 2 * bx * ns + by);
-            for (int i = 0; i < ns; ++i) {
-              const uint8_t *src = optiles + xts[i] + (uint64_t)4 * T2_W * m16 * c;
-              tc::bulk_g2s(st + i * bx, src, bx, &B->full[s]);                 // hi rows
-              tc::bulk_g2s(st + S::ALO + i * bx, src + bx, bx, &B->full[s]);   // lo rows
-            }
-            tc::bulk_g2s(st + S::AHALF, psitiles + e.yt + (uint64_t)4 * T2_W * p16 * c, by, &B->full[s]);
+            tc::mbar_arrive_expect_tx(&B->qfull[s], T2_DCOPY * (uint32_t)sizeof(TcEntry));
+            tc::bulk_g2s(chunk(qreq), E + g.first + (size_t)(qreq - qacc) * T2_DC,
+                         T2_DCOPY * (uint32_t)sizeof(TcEntry), &B->qfull[s]);
+            qlast[s] = qreq;
           }
-          // stage 2 of each member: its Z^T chunks
-          for (int i = 0; i < ns && ok; ++i)
-            for (int c = 0; c < nch2 && ok; ++c, ++j) {
+        };
+        int ei = g.first;
+        for (int c = 0; c < nch && ok; ++c) {
+          const int q = qacc + c;
+          request_upto(q + T2_DR - 1);
+          if (!ok || !t2_wait1(&B->qfull[q % T2_DR], (uint32_t)(q / T2_DR) & 1u, abort, status, 115, j, q,
+                               tries)) {
+            ok = false;
+            break;
+          }
+          const TcEntry *D0 = chunk(q);  // entry e of this block at D0[e - e0]
+          const int e0 = g.first + c * T2_DC;
+          const int c_end = min(e_end, g.first + (c + 1) * T2_DC);
+          for (; ei < c_end && ok;) {
+            const int ns = min(max((int)D0[ei - e0].stack, 1), T2_MAXSTACK);
+            const int n16 = ceil16(D0[ei - e0].n), p16 = ceil16(D0[ei - e0].p);
+            const uint32_t yt = D0[ei - e0].yt;
+            const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+            // stage 1 of the stack: the X chunks of every member, rows stacked, and one Y^T chunk
+            for (int cc = 0; cc < nch1 && ok; ++cc, ++j) {
               const int s = j % T2_NS;
               const uint32_t u = (uint32_t)(j / T2_NS);
-              if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 103, j, (int)u, tries)) {
+              if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 102, j, (int)u, tries)) {
                 ok = false;
                 break;
               }
-              const int w = min(T2_W, p16 - c * T2_W);
-              const uint32_t bz = (uint32_t)(q16 * w * 4);
-              tc::mbar_arrive_expect_tx(&B->full[s], bz);
-              tc::bulk_g2s(smem + s * S::STAGE + S::AHALF, optiles + zts[i] + (uint64_t)4 * T2_W * q16 * c, bz,
-                           &B->full[s]);
+              uint8_t *st = smem + s * S::STAGE;
+              const int w = min(T2_W, n16 - cc * T2_W);
+              const uint32_t bx = (uint32_t)(m16 * w * 2), by = (uint32_t)(p16 * w * 4);
+              tc::mbar_arrive_expect_tx(&B->full[s], 2 * bx * ns + by);
+              for (int i = 0; i < ns; ++i) {
+                const uint8_t *src = optiles + D0[ei - e0 + i].xt + (uint64_t)4 * T2_W * m16 * cc;
+                tc::bulk_g2s(st + i * bx, src, bx, &B->full[s]);                 // hi rows
+                tc::bulk_g2s(st + S::ALO + i * bx, src + bx, bx, &B->full[s]);   // lo rows
+              }
+              tc::bulk_g2s(st + S::AHALF, psitiles + yt + (uint64_t)4 * T2_W * p16 * cc, by, &B->full[s]);
             }
-          ei += ns;
+            // stage 2 of each member: its Z^T chunks
+            for (int i = 0; i < ns && ok; ++i) {
+              const uint64_t zt = D0[ei - e0 + i].zt;
+              for (int cc = 0; cc < nch2 && ok; ++cc, ++j) {
+                const int s = j % T2_NS;
+                const uint32_t u = (uint32_t)(j / T2_NS);
+                if (!t2_wait1(&B->empty[s], (u & 1u) ^ 1u, abort, status, 103, j, (int)u, tries)) {
+                  ok = false;
+                  break;
+                }
+                const int w = min(T2_W, p16 - cc * T2_W);
+                const uint32_t bz = (uint32_t)(q16 * w * 4);
+                tc::mbar_arrive_expect_tx(&B->full[s], bz);
+                tc::bulk_g2s(smem + s * S::STAGE + S::AHALF, optiles + zt + (uint64_t)4 * T2_W * q16 * cc, bz,
+                             &B->full[s]);
+              }
+            }
+            ei += ns;
+          }
+          if (ok) tc::mbar_arrive(&B->qempty[q % T2_DR]);  // done with this chunk's descriptors
         }
+        qacc += nch;
       }
       // copies in flight land before the CTA exits (bounded)
       for (int s = 0; s < T2_NS; ++s) {
@@ -407,93 +457,108 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
         while (jl >= 0 && jl % T2_NS != s) --jl;
         if (jl >= 0) tc::mbar_wait(&B->full[s], (uint32_t)(jl / T2_NS) & 1u, kMaxWaitTries);
       }
+      for (int s = 0; s < T2_DR; ++s)
+        if (qlast[s] >= 0) tc::mbar_wait(&B->qfull[s], (uint32_t)(qlast[s] / T2_DR) & 1u, kMaxWaitTries);
     }
   } else if (warp == 5) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      int j = 0, ls = 0, gl = 0;
+      int j = 0, ls = 0, gl = 0, qacc = 0;
       uint32_t cvpar = 0;
       bool ok = true;
       for (; ok; ++gl) {
         const int r = gl % T2_GR;
         if (!t2_wait1(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 104, j, ls, tries)) break;
         const int gi = gidx[r];
+        const TcGroup g = B->gdesc[r];
         tc::mbar_arrive(&B->gempty[r]);
         if (gi < 0) break;
-        const TcGroup g = G[gi];
         const int q16 = ceil16(g.q), e_end = g.first + g.count;
+        const int nch = (g.count + T2_DC - 1) / T2_DC;
         const uint32_t id2 = tc::idesc_bf16(MR, q16);
         bool dfirst = true;
-        for (int ei = g.first; ei < e_end && ok; ++ls) {
-          const TcEntry e = E[ei];
-          const int ns = min(max(e.stack, 1), T2_MAXSTACK);
-          const int n16 = ceil16(e.n), p16 = ceil16(e.p);
-          const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-          if (ls > 0) {  // T of the previous stack has been read
-            if (!t2_wait1(&B->tempty, (uint32_t)(ls - 1) & 1u, abort, status, 105, j, ls, tries)) {
-              ok = false;
-              break;
-            }
-            tc::fence_after();
+        int ei = g.first;
+        for (int c = 0; c < nch && ok; ++c) {
+          const int q = qacc + c;
+          if (!t2_wait1(&B->qfull[q % T2_DR], (uint32_t)(q / T2_DR) & 1u, abort, status, 116, j, q, tries)) {
+            ok = false;
+            break;
           }
-          const uint32_t id1 = tc::idesc_bf16(MR, p16);
-          for (int c = 0; c < nch1 && ok; ++c, ++j) {
-            const int s = j % T2_NS;
-            const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_wait1(&B->full[s], u & 1u, abort, status, 106, j, ls, tries)) {
-              ok = false;
-              break;
-            }
-            tc::fence_after();
-            const int w = min(T2_W, n16 - c * T2_W);
-            const uint32_t sbo = (uint32_t)(w / 8) * 128;
-            const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
-            const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(p16 * w * 2);
-            for (int ks = 0; ks < w / 16; ++ks) {
-              const uint32_t o = (uint32_t)ks * 256;
-              tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1,
-                           (c == 0 && ks == 0) ? 0u : 1u);
-              tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id1, 1u);
-              tc::mma_bf16(tT, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1, 1u);
-            }
-            tc::mma_commit(&B->empty[s]);
-          }
-          if (!ok) break;
-          tc::mma_commit(&B->tfull);
-          if (dfirst && gl > 0) {  // D of the previous block has been written out
-            if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 107, j, ls, tries)) {
-              ok = false;
-              break;
-            }
-            tc::fence_after();
-          }
-          for (int i = 0; i < ns && ok; ++i)
-            for (int c = 0; c < nch2 && ok; ++c, ++j) {
-              const int s = j % T2_NS;
-              const uint32_t u = (uint32_t)(j / T2_NS);
-              if (!t2_wait1(&B->full[s], u & 1u, abort, status, 108, j, ls, tries) ||
-                  !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 109, j, ls, tries)) {
+          const TcEntry *D0 = chunk(q);
+          const int e0 = g.first + c * T2_DC;
+          const int c_end = min(e_end, g.first + (c + 1) * T2_DC);
+          for (; ei < c_end && ok; ++ls) {
+            const int ns = min(max((int)D0[ei - e0].stack, 1), T2_MAXSTACK);
+            const int n16 = ceil16(D0[ei - e0].n), p16 = ceil16(D0[ei - e0].p);
+            const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+            if (ls > 0) {  // T of the previous stack has been read
+              if (!t2_wait1(&B->tempty, (uint32_t)(ls - 1) & 1u, abort, status, 105, j, ls, tries)) {
                 ok = false;
                 break;
               }
-              cvpar ^= 1u << s;
               tc::fence_after();
-              const int w = min(T2_W, p16 - c * T2_W);
+            }
+            const uint32_t id1 = tc::idesc_bf16(MR, p16);
+            for (int cc = 0; cc < nch1 && ok; ++cc, ++j) {
+              const int s = j % T2_NS;
+              const uint32_t u = (uint32_t)(j / T2_NS);
+              if (!t2_wait1(&B->full[s], u & 1u, abort, status, 106, j, ls, tries)) {
+                ok = false;
+                break;
+              }
+              tc::fence_after();
+              const int w = min(T2_W, n16 - cc * T2_W);
               const uint32_t sbo = (uint32_t)(w / 8) * 128;
               const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
-              const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(q16 * w * 2);
+              const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(p16 * w * 2);
               for (int ks = 0; ks < w / 16; ++ks) {
                 const uint32_t o = (uint32_t)ks * 256;
-                tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
-                             dfirst ? 0u : 1u);
-                dfirst = false;
-                tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
-                tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+                tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1,
+                             (cc == 0 && ks == 0) ? 0u : 1u);
+                tc::mma_bf16(tT, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id1, 1u);
+                tc::mma_bf16(tT, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id1, 1u);
               }
               tc::mma_commit(&B->empty[s]);
             }
-          ei += ns;
+            if (!ok) break;
+            tc::mma_commit(&B->tfull);
+            if (dfirst && gl > 0) {  // D of the previous block has been written out
+              if (!t2_wait1(&B->dempty, (uint32_t)(gl - 1) & 1u, abort, status, 107, j, ls, tries)) {
+                ok = false;
+                break;
+              }
+              tc::fence_after();
+            }
+            for (int i = 0; i < ns && ok; ++i)
+              for (int cc = 0; cc < nch2 && ok; ++cc, ++j) {
+                const int s = j % T2_NS;
+                const uint32_t u = (uint32_t)(j / T2_NS);
+                if (!t2_wait1(&B->full[s], u & 1u, abort, status, 108, j, ls, tries) ||
+                    !t2_wait1(&B->cvf[s], (cvpar >> s) & 1u, abort, status, 109, j, ls, tries)) {
+                  ok = false;
+                  break;
+                }
+                cvpar ^= 1u << s;
+                tc::fence_after();
+                const int w = min(T2_W, p16 - cc * T2_W);
+                const uint32_t sbo = (uint32_t)(w / 8) * 128;
+                const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
+                const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(q16 * w * 2);
+                for (int ks = 0; ks < w / 16; ++ks) {
+                  const uint32_t o = (uint32_t)ks * 256;
+                  tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
+                               dfirst ? 0u : 1u);
+                  dfirst = false;
+                  tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
+                  tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+                }
+                tc::mma_commit(&B->empty[s]);
+              }
+            ei += ns;
+          }
+          if (ok) tc::mbar_arrive(&B->qempty[q % T2_DR]);
         }
+        qacc += nch;
         if (ok) tc::mma_commit(&B->dfull);
       }
       tc::mma_commit(&B->drain);  // every MMA issued above has finished before TMEM is released
@@ -503,69 +568,84 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
     // ---------------- converters (thread = TMEM lane = accumulator row, if any)
     const int R = S::row_of_lane(tid);
     const uint32_t lane_off = (uint32_t)(32 * warp) << 16;
-    int j = 0, ls = 0, gl = 0;
+    int j = 0, ls = 0, gl = 0, qacc = 0;
     bool ok = true;
     for (; ok; ++gl) {
       const int r = gl % T2_GR;
       if (!t2_waitw(&B->gfull[r], (uint32_t)(gl / T2_GR) & 1u, abort, status, 110, j, ls, tries)) break;
       const int gi = gidx[r];
+      const TcGroup g = B->gdesc[r];
       __syncwarp();
       if (lane == 0) tc::mbar_arrive(&B->gempty[r]);
       if (gi < 0) break;
-      const TcGroup g = G[gi];
       const int m = g.m, q = g.q, m16 = ceil16(m), q16 = ceil16(q), e_end = g.first + g.count;
+      const int nch = (g.count + T2_DC - 1) / T2_DC;
       // this thread's T row belongs to stack member R / m16, output row R % m16
       const int mine = R >= 0 ? R / m16 : -1, orow = R >= 0 ? R % m16 : 0;
-      for (int ei = g.first; ei < e_end && ok; ++ls) {
-        const TcEntry e = E[ei];
-        const int ns = min(max(e.stack, 1), T2_MAXSTACK);
-        const int n16 = ceil16(e.n), p16 = ceil16(e.p);
-        const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
-        const float f = mine >= 0 && mine < ns ? E[ei + mine].f : 0.f;
-        j += nch1;
-        if (!t2_waitw(&B->tfull, (uint32_t)ls & 1u, abort, status, 111, j, ls, tries)) {
+      int ei = g.first;
+      for (int c = 0; c < nch && ok; ++c) {
+        const int qc = qacc + c;
+        if (!t2_waitw(&B->qfull[qc % T2_DR], (uint32_t)(qc / T2_DR) & 1u, abort, status, 117, j, qc, tries)) {
           ok = false;
           break;
         }
-        tc::fence_after();
-        for (int i = 0; i < ns && ok; ++i) {
-          const bool writes = mine == i && orow < m;
-          for (int c = 0; c < nch2; ++c, ++j) {
-            const int s = j % T2_NS;
-            const uint32_t u = (uint32_t)(j / T2_NS);
-            if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 112, j, (int)u, tries)) {
-              ok = false;
-              break;
-            }
-            tc::fence_after();
-            const int w = min(T2_W, p16 - c * T2_W);
-            uint8_t *A = smem + s * S::STAGE;
-            for (int h = 0; h < w / 16; ++h) {
-              float v[16];
-              tc::tmem_ld16(tT + lane_off + (uint32_t)(c * T2_W + h * 16), v);
-              if (writes) {
+        const TcEntry *D0 = chunk(qc);
+        const int e0 = g.first + c * T2_DC;
+        const int c_end = min(e_end, g.first + (c + 1) * T2_DC);
+        for (; ei < c_end && ok; ++ls) {
+          const int ns = min(max((int)D0[ei - e0].stack, 1), T2_MAXSTACK);
+          const int n16 = ceil16(D0[ei - e0].n), p16 = ceil16(D0[ei - e0].p);
+          const int nch1 = (n16 + T2_W - 1) / T2_W, nch2 = (p16 + T2_W - 1) / T2_W;
+          const float f = mine >= 0 && mine < ns ? D0[ei - e0 + mine].f : 0.f;
+          j += nch1;
+          if (!t2_waitw(&B->tfull, (uint32_t)ls & 1u, abort, status, 111, j, ls, tries)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          for (int i = 0; i < ns && ok; ++i) {
+            const bool writes = mine == i && orow < m;
+            for (int cc = 0; cc < nch2; ++cc, ++j) {
+              const int s = j % T2_NS;
+              const uint32_t u = (uint32_t)(j / T2_NS);
+              if (!t2_waitw(&B->empty[s], (u & 1u) ^ 1u, abort, status, 112, j, (int)u, tries)) {
+                ok = false;
+                break;
+              }
+              tc::fence_after();
+              const int w = min(T2_W, p16 - cc * T2_W);
+              uint8_t *A = smem + s * S::STAGE;
+              for (int h = 0; h < w / 16; ++h) {
+                float v[16];
+                tc::tmem_ld16(tT + lane_off + (uint32_t)(cc * T2_W + h * 16), v);
+                if (writes) {
 #pragma unroll
-                for (int g2 = 0; g2 < 2; ++g2) {
-                  __align__(16) __nv_bfloat16 hb[8], lb[8];
+                  for (int g2 = 0; g2 < 2; ++g2) {
+                    __align__(16) __nv_bfloat16 hb[8], lb[8];
 #pragma unroll
-                  for (int k = 0; k < 8; ++k) tc::split_bf16(f * v[8 * g2 + k], hb[k], lb[k]);
-                  uint8_t *dst = A + ((orow >> 3) * (w >> 3) + 2 * h + g2) * 128 + (orow & 7) * 16;
-                  *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
-                  *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
+                    for (int k = 0; k < 8; ++k) tc::split_bf16(f * v[8 * g2 + k], hb[k], lb[k]);
+                    uint8_t *dst = A + ((orow >> 3) * (w >> 3) + 2 * h + g2) * 128 + (orow & 7) * 16;
+                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
+                    *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
+                  }
                 }
               }
+              tc::fence_async_smem();
+              __syncwarp();
+              if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
             }
-            tc::fence_async_smem();
-            __syncwarp();
-            if (lane == 0) tc::mbar_arrive(&B->cvf[s]);
           }
+          if (!ok) break;
+          tc::fence_before();
+          __syncwarp();
+          if (lane == 0) tc::mbar_arrive(&B->tempty);
+          ei += ns;
         }
         if (!ok) break;
-        tc::fence_before();
         __syncwarp();
-        if (lane == 0) tc::mbar_arrive(&B->tempty);
-        ei += ns;
+        if (lane == 0) tc::mbar_arrive(&B->qempty[qc % T2_DR]);
       }
+      qacc += nch;
       if (!ok) break;
       // ---- output block: D (TMEM) -> FP64 global, then release D
       if (!t2_waitw(&B->dfull, (uint32_t)gl & 1u, abort, status, 113, j, ls, tries)) {
@@ -573,14 +653,14 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
         break;
       }
       tc::fence_after();
-      double *D = reinterpret_cast<double *>(db + g.d * 8ull);
+      double *Dout = reinterpret_cast<double *>(db + g.d * 8ull);
       for (int c0 = 0; c0 < q16; c0 += 16) {
         float v[16];
         tc::tmem_ld16(tD + lane_off + (uint32_t)c0, v);
         if (R >= 0 && R < m) {
 #pragma unroll
           for (int i = 0; i < 16; ++i)
-            if (c0 + i < q) D[(int64_t)R * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
+            if (c0 + i < q) Dout[(int64_t)R * g.drs + (int64_t)(c0 + i) * g.dcs] += (double)v[i];
         }
       }
       tc::fence_before();
