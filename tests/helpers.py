@@ -84,3 +84,15 @@ def rebuild_blocks(exports, L, side, n_sites):
         assert pos == len(O)
         blk = ob.grow_left(blk, j - 1, blocks) if side == 0 else ob.grow_right(blk, L - j, blocks)
     return blk
+
+
+def oracle_middle_bond(h, v, n_up, n_dn, M, k, seed):
+    """The operator-based FP64 oracle at position k, its blocks grown from the same
+    seeded random O as workloads.grow_middle_bond gives a GPU context."""
+    from oracle import baseline
+    from oracle import dmrg as od
+    L = h.shape[0]
+    b = baseline.OracleBuilder(h, v)
+    workloads.grow_middle_bond(b, L, n_up, n_dn, M, k, seed=seed)
+    lb, rb = b._blocks()
+    return od.HPsi(b.I, k, lb, rb, n_up, n_dn)
