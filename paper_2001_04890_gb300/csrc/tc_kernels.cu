@@ -302,6 +302,12 @@ __device__ __forceinline__ bool t2_waitw(uint64_t *bar, uint32_t parity, volatil
 
 __device__ __forceinline__ int ceil16(int x) { return (x + 15) & ~15; }
 
+// Stage-2 jobs: when the inner dimension p of a stack is at most 16, the K chunk
+// is 16 wide and two members share one job (their A tiles side by side in the
+// stage's A half, their Z^T tiles side by side in its B half, one MMA chain
+// each into D); otherwise one member per job.
+__device__ __forceinline__ int t2_members_per_job(int p16) { return p16 == 16 ? 2 : 1; }
+
 template <int MR, int TC, int CTAS>
 __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEntry *__restrict__ E,
                                                                const TcGroup *__restrict__ G, int ngroups,
@@ -428,9 +434,10 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
               }
               tc::bulk_g2s(st + S::AHALF, psitiles + yt + (uint64_t)4 * T2_W * p16 * cc, by, &B->full[s]);
             }
-            // stage 2 of each member: its Z^T chunks
-            for (int i = 0; i < ns && ok; ++i) {
-              const uint64_t zt = D0[ei - e0 + i].zt;
+            // stage 2: the members' Z^T chunks (two members to a job when K is 16 wide)
+            const int per = t2_members_per_job(p16);
+            for (int i0 = 0; i0 < ns && ok; i0 += per) {
+              const int nm = min(per, ns - i0);
               for (int cc = 0; cc < nch2 && ok; ++cc, ++j) {
                 const int s = j % T2_NS;
                 const uint32_t u = (uint32_t)(j / T2_NS);
@@ -440,9 +447,10 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
                 }
                 const int w = min(T2_W, p16 - cc * T2_W);
                 const uint32_t bz = (uint32_t)(q16 * w * 4);
-                tc::mbar_arrive_expect_tx(&B->full[s], bz);
-                tc::bulk_g2s(smem + s * S::STAGE + S::AHALF, optiles + zt + (uint64_t)4 * T2_W * q16 * cc, bz,
-                             &B->full[s]);
+                tc::mbar_arrive_expect_tx(&B->full[s], bz * nm);
+                for (int t = 0; t < nm; ++t)
+                  tc::bulk_g2s(smem + s * S::STAGE + S::AHALF + t * bz,
+                               optiles + D0[ei - e0 + i0 + t].zt + (uint64_t)4 * T2_W * q16 * cc, bz, &B->full[s]);
               }
             }
             ei += ns;
@@ -529,7 +537,9 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
               }
               tc::fence_after();
             }
-            for (int i = 0; i < ns && ok; ++i)
+            const int per = t2_members_per_job(p16);
+            for (int i0 = 0; i0 < ns && ok; i0 += per) {
+              const int nm = min(per, ns - i0);
               for (int cc = 0; cc < nch2 && ok; ++cc, ++j) {
                 const int s = j % T2_NS;
                 const uint32_t u = (uint32_t)(j / T2_NS);
@@ -542,18 +552,22 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
                 tc::fence_after();
                 const int w = min(T2_W, p16 - cc * T2_W);
                 const uint32_t sbo = (uint32_t)(w / 8) * 128;
-                const uint32_t a = tc::smem_u32(smem + s * S::STAGE), b = a + S::AHALF;
-                const uint32_t alo = a + S::ALO, blo = b + (uint32_t)(q16 * w * 2);
-                for (int ks = 0; ks < w / 16; ++ks) {
-                  const uint32_t o = (uint32_t)ks * 256;
-                  tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
-                               dfirst ? 0u : 1u);
-                  dfirst = false;
-                  tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
-                  tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+                const uint32_t a0 = tc::smem_u32(smem + s * S::STAGE);
+                for (int t = 0; t < nm; ++t) {  // member t of the job: its A tile and its B tile
+                  const uint32_t a = a0 + (uint32_t)(t * MR * w * 2), alo = a + S::ALO;
+                  const uint32_t b = a0 + S::AHALF + (uint32_t)(t * q16 * w * 4), blo = b + (uint32_t)(q16 * w * 2);
+                  for (int ks = 0; ks < w / 16; ++ks) {
+                    const uint32_t o = (uint32_t)ks * 256;
+                    tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2,
+                                 dfirst ? 0u : 1u);
+                    dfirst = false;
+                    tc::mma_bf16(tD, tc::make_desc(a + o, 128, sbo), tc::make_desc(blo + o, 128, sbo), id2, 1u);
+                    tc::mma_bf16(tD, tc::make_desc(alo + o, 128, sbo), tc::make_desc(b + o, 128, sbo), id2, 1u);
+                  }
                 }
                 tc::mma_commit(&B->empty[s]);
               }
+            }
             ei += ns;
           }
           if (ok) tc::mbar_arrive(&B->qempty[q % T2_DR]);
@@ -603,8 +617,16 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
             break;
           }
           tc::fence_after();
-          for (int i = 0; i < ns && ok; ++i) {
-            const bool writes = mine == i && orow < m;
+          const int per = t2_members_per_job(p16);
+          for (int i0 = 0; i0 < ns && ok; i0 += per) {
+            const int nm = min(per, ns - i0);
+            const bool writes = mine >= i0 && mine < i0 + nm && orow < m;
+            const int t = writes ? mine - i0 : 0;  // this thread's member within the job
+            // a warp that holds no T row of this job's members only signals (the
+            // TMEM load is warp-collective, so the test is warp-uniform)
+            const int r_lo = i0 * m16, r_hi = (i0 + nm - 1) * m16 + m;
+            const int w_lo = (MR == 128 ? 32 : 16) * warp, w_hi = w_lo + (MR == 128 ? 32 : 16);
+            const bool warp_busy = r_lo < w_hi && w_lo < r_hi;
             for (int cc = 0; cc < nch2; ++cc, ++j) {
               const int s = j % T2_NS;
               const uint32_t u = (uint32_t)(j / T2_NS);
@@ -614,19 +636,28 @@ __global__ void __launch_bounds__(T2_THREADS, CTAS) chain_tc2_kernel(const TcEnt
               }
               tc::fence_after();
               const int w = min(T2_W, p16 - cc * T2_W);
-              uint8_t *A = smem + s * S::STAGE;
-              for (int h = 0; h < w / 16; ++h) {
-                float v[16];
-                tc::tmem_ld16(tT + lane_off + (uint32_t)(cc * T2_W + h * 16), v);
+              uint8_t *A = smem + s * S::STAGE + t * MR * w * 2;
+              if (warp_busy) {
+                float v[2][16];
+                const uint32_t ta = tT + lane_off + (uint32_t)(cc * T2_W);
+                if (w == 32) {
+                  tc::tmem_ld16x2(ta, ta + 16, v[0], v[1]);
+                } else {
+                  tc::tmem_ld16(ta, v[0]);
+                }
                 if (writes) {
 #pragma unroll
-                  for (int g2 = 0; g2 < 2; ++g2) {
-                    __align__(16) __nv_bfloat16 hb[8], lb[8];
+                  for (int h = 0; h < 2; ++h) {
+                    if (h * 16 >= w) break;
 #pragma unroll
-                    for (int k = 0; k < 8; ++k) tc::split_bf16(f * v[8 * g2 + k], hb[k], lb[k]);
-                    uint8_t *dst = A + ((orow >> 3) * (w >> 3) + 2 * h + g2) * 128 + (orow & 7) * 16;
-                    *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
-                    *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
+                    for (int g2 = 0; g2 < 2; ++g2) {
+                      __align__(16) __nv_bfloat16 hb[8], lb[8];
+#pragma unroll
+                      for (int k = 0; k < 8; ++k) tc::split_bf16(f * v[h][8 * g2 + k], hb[k], lb[k]);
+                      uint8_t *dst = A + ((orow >> 3) * (w >> 3) + 2 * h + g2) * 128 + (orow & 7) * 16;
+                      *reinterpret_cast<uint4 *>(dst) = *reinterpret_cast<const uint4 *>(hb);
+                      *reinterpret_cast<uint4 *>(dst + S::ALO) = *reinterpret_cast<const uint4 *>(lb);
+                    }
                   }
                 }
               }
