@@ -312,6 +312,30 @@ int dmrg_block_basis(dmrg_ctx *ctx, int side, int sites, int *nsec, int *kept, d
 int dmrg_orbital_entropies(dmrg_ctx *ctx, double *s3, double *rho2);
 
 /*
+ * dmrg_mutual_information -- one-orbital entropies of every orbital and the
+ * mutual information I_ij = s_i + s_j - s_ij of every orbital pair (the
+ * quantities Sec. 3 uses to order the orbitals), from the wave function at
+ * position 0 and the right blocks of every length as stored (one backward
+ * pass, e.g. dmrg_sweep, which ends at position 0; run dmrg_davidson there
+ * first for the converged state).  Each right block state is a column of its
+ * renormalization matrix over (site state) x (next right block state) with
+ * orthonormal columns, so the two-orbital reduced density matrix of orbitals
+ * i < j follows by carrying a density matrix with orbital i's states open
+ * through the sites between them (each traced; an element that changes the
+ * parity of orbital i picks up (-1)^(particles) of each, the Jordan-Wigner
+ * string of moving orbital j next to orbital i) and tracing everything right
+ * of j.  Host arithmetic on copies of psi and the renormalization matrices,
+ * O(L^2) transfers of sector-blocked matrices.  Outputs (host, each may be
+ * NULL, not all): I (L*L, row-major, symmetric, zero diagonal), s1 (L
+ * entropies), rho_pairs (L*L*256: the 16 x 16 matrix of pair (i, j), i < j, at
+ * (i*L + j)*256, rows and columns 4 b + c with b, c the site states of i and
+ * j in the order 0, up, dn, updn; other entries 0).  Errors: DMRG_EINVAL,
+ * DMRG_ESTATE (not at position 0, no wave function, or a right block missing
+ * or released).
+ */
+int dmrg_mutual_information(dmrg_ctx *ctx, double *I, double *s1, double *rho_pairs);
+
+/*
  * dmrg_sweep -- nsweeps two-site sweeps (Sec. 2.1, Fig. dmrg_blocks): forward
  * over positions 0..L-3 (Davidson then dmrg_renormalize(+1)), backward over
  * L-2..1 (Davidson then dmrg_renormalize(-1)).  Starts from position 0 in the

@@ -306,6 +306,46 @@ def pair_rdm_dets(x: np.ndarray, D: np.ndarray, i: int) -> np.ndarray:
     return rho
 
 
+def pair_rdm_dets_ij(x: np.ndarray, D: np.ndarray, i: int, j: int) -> np.ndarray:
+    """Two-orbital reduced density matrix of orbitals i < j (not necessarily
+    adjacent) of the state sum_D x_D |D>, indexed by 4 b + c with b, c the site
+    states of orbitals i and j (the matrix behind the mutual information the
+    paper uses for the orbital ordering, Sec. 3).
+
+    Moving the two modes of orbital j (in front of every mode between the two
+    orbitals) next to those of orbital i reorders the Jordan-Wigner string:
+    each determinant picks up (-1)^(n_j * n_between), n_j the electrons on
+    orbital j and n_between those on the orbitals strictly between.  In that
+    order the pair is adjacent, and rho[(b c), (b' c')] = sum over the other
+    modes' occupations of the two reordered amplitudes (as pair_rdm_dets).
+    """
+    if not (0 <= i < j):
+        raise ValueError("pair_rdm_dets_ij needs 0 <= i < j")
+    li = (D >> (2 * i)) & 3
+    lj = (D >> (2 * j)) & 3
+    b = (li & 1) + 2 * ((li >> 1) & 1)
+    c = (lj & 1) + 2 * ((lj >> 1) & 1)
+    between = ((np.int64(1) << (2 * j)) - 1) & ~((np.int64(1) << (2 * i + 2)) - 1)
+    n_between = popcount(D & between)
+    n_j = popcount(lj)
+    sign = np.where((n_j * n_between) % 2 == 1, -1.0, 1.0)
+    pair = (4 * b + c).astype(np.int64)
+    rest = D & ~(np.int64(3) << (2 * i)) & ~(np.int64(3) << (2 * j))
+    rho = np.zeros((16, 16))
+    order = np.argsort(rest, kind="stable")
+    rs, ps, xs = rest[order], pair[order], (sign * x)[order]
+    start = 0
+    while start < len(rs):
+        end = start
+        while end < len(rs) and rs[end] == rs[start]:
+            end += 1
+        v = np.zeros(16)
+        v[ps[start:end]] = xs[start:end]
+        rho += np.outer(v, v)
+        start = end
+    return rho
+
+
 def orbital_entropies(rho: np.ndarray):
     """(s_i, s_{i+1}, s_{i,i+1}): von Neumann entropies -tr(r ln r) of the
     trace-normalised one-orbital matrices (partial traces of the pair matrix)

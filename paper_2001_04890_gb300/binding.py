@@ -78,6 +78,7 @@ def lib():
         "dmrg_get_tune": (C.c_int, [vp, dp]),
         "dmrg_truncation_stats": (C.c_int, [vp, dp, dp, llp, llp]),
         "dmrg_orbital_entropies": (C.c_int, [vp, dp, dp]),
+        "dmrg_mutual_information": (C.c_int, [vp, dp, dp, dp]),
         "dmrg_block_basis": (C.c_int, [vp, C.c_int, C.c_int, ip, ip, dp, llp]),
         "dmrg_sweep_record": (C.c_int, [vp, C.c_int, C.c_double, dp, dp, dp]),
         "dmrg_set_davidson": (C.c_int, [vp, C.c_int, C.c_int]),
@@ -476,12 +477,26 @@ class DMRG:
 
     def orbital_entropies(self):
         """Entropies of the two sites of the current wave function (k and k+1): dict with
-        s_left, s_right, s_pair, mutual_information and the 16 x 16 two-orbital matrix rho2."""
+        s_left, s_right, s_pair and the 16 x 16 two-orbital matrix rho2."""
         s3 = np.zeros(3)
         rho = np.zeros(256)
         _check(lib().dmrg_orbital_entropies(self.ctx, _dptr(s3), _dptr(rho)))
-        return dict(s_left=s3[0], s_right=s3[1], s_pair=s3[2], mutual_information=s3[0] + s3[1] - s3[2],
-                    rho2=rho.reshape(16, 16))
+        return dict(s_left=s3[0], s_right=s3[1], s_pair=s3[2], rho2=rho.reshape(16, 16))
+
+    def mutual_information(self, pair_matrices=False):
+        """Mutual information of every orbital pair of the wave function at position 0:
+        dict with I (L x L), s1 (the L one-orbital entropies) and, if asked, rho (L x L x
+        16 x 16 two-orbital matrices, filled for i < j)."""
+        L = self.L
+        I = np.zeros(L * L)
+        s1 = np.zeros(L)
+        rho = np.zeros(L * L * 256) if pair_matrices else None
+        _check(lib().dmrg_mutual_information(self.ctx, _dptr(I), _dptr(s1),
+                                             _dptr(rho) if rho is not None else None))
+        out = dict(I=I.reshape(L, L), s1=s1)
+        if rho is not None:
+            out["rho"] = rho.reshape(L, L, 16, 16)
+        return out
 
     def truncation_stats(self):
         """Record of the density-matrix truncations since init: gap at the cut of the

@@ -8,6 +8,7 @@
 #include <cusolverDn.h>
 
 #include <algorithm>
+#include <array>
 #include <atomic>
 #include <cmath>
 #include <functional>
@@ -3490,6 +3491,225 @@ static void current_entropies(dmrg_ctx *c, double s3[3], double *rho2) {
   if (rho2)
     for (int i = 0; i < 256; ++i) rho2[i] = rho[i];
   if (s3) orbital_entropies(rho, s3);
+}
+
+// ---------------------------------------------------------------- orbital mutual information
+
+// Two-orbital reduced density matrices of every orbital pair, for the orbital
+// ordering of Sec. 3 (mutual information I_ij = s_i + s_j - s_ij), from the
+// wave function at position 0 and the right blocks of sites 2..L-1 as stored:
+// each right block state is a column of its renormalization matrix over
+// (site state) x (next right block state), and those columns are orthonormal,
+// so tracing every site right of the second orbital is the identity.  Working
+// from site 0 to the right, a density matrix over the current right block with
+// the first orbital's states left open (V) is carried through the sites
+// between the two orbitals, each traced, and closed at the second orbital.
+// Fermionic signs: the pair's matrix is that of the two orbitals moved next to
+// each other in the Jordan-Wigner order (lattice order, up before down), so an
+// element that changes the parity of the pair's first orbital picks up
+// (-1)^(particles of each traced site between the two).
+namespace {
+struct HostExp {  // a right block's states over (site state s) x (next block state y)
+  struct Piece {
+    int s, y, my;
+    const double *P;  // my x dim(new sector) rows of the block's O, row stride = dim(new sector)
+  };
+  std::vector<int> dim;
+  std::vector<std::vector<Piece>> pieces;  // per new sector
+  std::vector<double> O;
+};
+using SecMat = std::map<std::pair<int, int>, std::vector<double>>;  // (ket sector, bra sector) -> dense
+}  // namespace
+
+static void host_expansion(const DevBlock &b, cudaStream_t s, HostExp &X) {
+  X.O.resize(b.O.n);
+  if (b.O.n) CK(cudaMemcpyAsync(X.O.data(), b.O.p, b.O.n * sizeof(double), cudaMemcpyDeviceToHost, s));
+  CK(cudaStreamSynchronize(s));
+  X.dim.clear();
+  X.pieces.clear();
+  for (size_t e = 0; e < b.parent.size(); ++e) {
+    const int ma = b.kept[e];
+    if (ma <= 0) continue;
+    X.dim.push_back(ma);
+    std::vector<HostExp::Piece> ps;
+    for (const ESub &sb : b.parent[e].sub)
+      ps.push_back({sb.x, sb.y, sb.m, X.O.data() + b.Ooff[e] + (int64_t)sb.roff * ma});
+    X.pieces.push_back(ps);
+  }
+}
+
+// C (m x n) += alpha * A (m x k, row stride lda) * op(B); B is k x n (row stride ldb) or, with
+// bt, n x k read transposed
+static void hgemm(double *C, const double *A, int lda, const double *B, int ldb, int m, int n, int k, bool bt,
+                  double alpha) {
+  for (int i = 0; i < m; ++i)
+    for (int p = 0; p < k; ++p) {
+      const double a = alpha * A[(int64_t)i * lda + p];
+      if (a == 0.0) continue;
+      double *c = C + (int64_t)i * n;
+      if (bt)
+        for (int j = 0; j < n; ++j) c[j] += a * B[(int64_t)j * ldb + p];
+      else
+        for (int j = 0; j < n; ++j) c[j] += a * B[(int64_t)p * ldb + j];
+    }
+}
+
+// out[(y, y')] += sgn * P_{A,s,y} V[(A, A')] P_{A',s',y'}^T over pieces with (s, s') accepted by keep
+template <class Keep>
+static void mi_expand(const HostExp &X, const SecMat &V, SecMat &out, const std::vector<int> &ydim, Keep keep) {
+  for (const auto &kv : V) {
+    const int A = kv.first.first, A2 = kv.first.second;
+    const int da = X.dim[A], da2 = X.dim[A2];
+    for (const auto &p : X.pieces[A]) {
+      std::vector<double> T;
+      bool have_t = false;
+      for (const auto &q : X.pieces[A2]) {
+        double w;
+        if (!keep(p.s, q.s, w)) continue;
+        if (!have_t) {  // T = P_p V (my x da2)
+          T.assign((size_t)p.my * da2, 0.0);
+          hgemm(T.data(), p.P, da, kv.second.data(), da2, p.my, da2, da, false, 1.0);
+          have_t = true;
+        }
+        auto &o = out[{p.y, q.y}];
+        if (o.empty()) o.assign((size_t)ydim[p.y] * ydim[q.y], 0.0);
+        hgemm(o.data(), T.data(), da2, q.P, da2, p.my, q.my, da2, true, w);
+      }
+    }
+  }
+}
+
+// rho[s][s'] += tr_y(P_{A,s,y} V[(A, A')] P_{A',s',y}^T): the second orbital opened, the rest traced
+static void mi_close(const HostExp &X, const SecMat &V, double rho[4][4]) {
+  for (const auto &kv : V) {
+    const int A = kv.first.first, A2 = kv.first.second;
+    const int da = X.dim[A], da2 = X.dim[A2];
+    for (const auto &p : X.pieces[A])
+      for (const auto &q : X.pieces[A2]) {
+        if (p.y != q.y) continue;
+        std::vector<double> T((size_t)p.my * da2, 0.0);
+        hgemm(T.data(), p.P, da, kv.second.data(), da2, p.my, da2, da, false, 1.0);
+        double t = 0.0;
+        for (int r = 0; r < p.my; ++r)
+          for (int c2 = 0; c2 < da2; ++c2) t += T[(size_t)r * da2 + c2] * q.P[(int64_t)r * da2 + c2];
+        rho[p.s][q.s] += t;
+      }
+  }
+}
+
+static int site_n(int s) { return SITE_NU[s] + SITE_ND[s]; }
+
+static void mutual_information(dmrg_ctx *c, double *I, double *s1, double *rho_all) {
+  const int L = c->L;
+  if (c->k != 0) throw Fail{DMRG_ESTATE, "mutual information needs the wave function at position 0"};
+  if (!c->psi_valid) throw Fail{DMRG_ESTATE, "no wave function at position 0 (run dmrg_davidson)"};
+  require_blocks(c);
+  for (int n = 1; n <= L - 2; ++n)
+    if (n >= (int)c->right.size() || !c->right[n] || c->right[n]->parent.empty())
+      throw Fail{DMRG_ESTATE, "mutual information needs the right blocks of every length (one backward pass)"};
+  const Psi Y = psi_layout(lblock(c)->lay, rblock(c)->lay, c->nu, c->nd);
+  std::vector<double> h((size_t)std::max<int64_t>(Y.dim, 1));
+  CK(cudaMemcpyAsync(h.data(), c->psi.p, Y.dim * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  CK(cudaStreamSynchronize(c->stream));
+  // R_m = right block of sites m..L-1 = c->right[L - m]
+  std::vector<HostExp> X((size_t)L + 1);
+  std::vector<std::vector<int>> dims((size_t)L + 1);
+  for (int m = 2; m <= L; ++m) {
+    const DevBlock &b = *c->right[L - m];
+    for (const auto &sec : b.lay.sec) dims[m].push_back(sec.dim);
+    if (m < L) host_expansion(b, c->stream, X[m]);
+  }
+  std::vector<double> R((size_t)L * L * 256, 0.0);  // rho of pair (i, j), i < j
+  auto pair_rho = [&](int i, int j) { return R.data() + ((size_t)i * L + j) * 256; };
+  // pair (0, 1): the two sites of position 0
+  {
+    std::vector<PsiBlockRef> blocks;
+    for (const PsiBlock &b : Y.blk) blocks.push_back({b.a, b.b, b.c, b.d, b.off, (int64_t)b.ma * b.md});
+    pair_rdm(blocks, h.data(), pair_rho(0, 1));
+  }
+  // carry V (first orbital i open) from R_m to the right end
+  auto run = [&](int i, int m, std::array<SecMat, 16> V) {
+    for (int j = m; j <= L - 1; ++j) {
+      for (int sg = 0; sg < 16; ++sg) {
+        double rr[4][4] = {};
+        mi_close(X[j], V[sg], rr);
+        for (int a = 0; a < 4; ++a)
+          for (int b = 0; b < 4; ++b) pair_rho(i, j)[(4 * (sg / 4) + a) * 16 + 4 * (sg % 4) + b] += rr[a][b];
+      }
+      if (j == L - 1) break;
+      for (int sg = 0; sg < 16; ++sg) {
+        const bool odd = (site_n(sg / 4) + site_n(sg % 4)) & 1;
+        SecMat nv;
+        mi_expand(X[j], V[sg], nv, dims[j + 1], [&](int s, int s2, double &w) {
+          w = (odd && (site_n(s) & 1)) ? -1.0 : 1.0;
+          return s == s2;
+        });
+        V[sg].swap(nv);
+      }
+    }
+  };
+  auto vec = [&](const PsiBlock &b) { return h.data() + b.off; };
+  // first orbital 0 (site 1 traced, with the string sign) and 1 (site 0 traced)
+  for (int i = 0; i < 2 && L > 2; ++i) {
+    std::array<SecMat, 16> V;
+    for (const PsiBlock &p : Y.blk)
+      for (const PsiBlock &q : Y.blk) {
+        const int sp = i == 0 ? p.b : p.c, sq = i == 0 ? q.b : q.c;  // open states
+        const int tp = i == 0 ? p.c : p.b, tq = i == 0 ? q.c : q.b;  // traced states
+        if (tp != tq) continue;
+        const bool odd = (site_n(sp) + site_n(sq)) & 1;
+        const double w = (i == 0 && odd && (site_n(tp) & 1)) ? -1.0 : 1.0;
+        auto &o = V[4 * sp + sq][{p.d, q.d}];
+        if (o.empty()) o.assign((size_t)p.md * q.md, 0.0);
+        hgemm(o.data(), vec(p), 1, vec(q), q.md, p.md, q.md, 1, false, w);
+      }
+    run(i, 2, V);
+  }
+  // first orbital m >= 2: W (everything left of m traced) over R_m, opened at m
+  SecMat W;
+  for (const PsiBlock &p : Y.blk)
+    for (const PsiBlock &q : Y.blk) {
+      if (p.b != q.b || p.c != q.c || p.d != q.d) continue;
+      auto &o = W[{p.d, q.d}];
+      if (o.empty()) o.assign((size_t)p.md * q.md, 0.0);
+      hgemm(o.data(), vec(p), 1, vec(q), q.md, p.md, q.md, 1, false, 1.0);
+    }
+  for (int m = 2; m <= L - 2; ++m) {
+    std::array<SecMat, 16> V;
+    for (int sg = 0; sg < 16; ++sg)
+      mi_expand(X[m], W, V[sg], dims[m + 1], [&](int s, int s2, double &w) {
+        w = 1.0;
+        return s == sg / 4 && s2 == sg % 4;
+      });
+    run(m, m + 1, V);
+    SecMat nw;
+    mi_expand(X[m], W, nw, dims[m + 1], [&](int s, int s2, double &w) {
+      w = 1.0;
+      return s == s2;
+    });
+    W.swap(nw);
+  }
+  // entropies from the pair matrices
+  std::vector<double> s1v((size_t)L, 0.0);
+  if (I) std::fill(I, I + (size_t)L * L, 0.0);
+  for (int i = 0; i < L; ++i)
+    for (int j = i + 1; j < L; ++j) {
+      double s3[3];
+      orbital_entropies(pair_rho(i, j), s3);
+      s1v[i] = s3[0];
+      s1v[j] = s3[1];
+      if (I) I[(size_t)i * L + j] = I[(size_t)j * L + i] = s3[0] + s3[1] - s3[2];
+    }
+  if (s1) std::copy(s1v.begin(), s1v.end(), s1);
+  if (rho_all) std::copy(R.begin(), R.end(), rho_all);
+}
+
+extern "C" int dmrg_mutual_information(dmrg_ctx *c, double *I, double *s1, double *rho_pairs) {
+  API_BEGIN
+  if (!c || (!I && !s1 && !rho_pairs)) throw Fail{DMRG_EINVAL, "NULL argument"};
+  if (c->L < 2) throw Fail{DMRG_EINVAL, "mutual information needs L >= 2"};
+  mutual_information(c, I, s1, rho_pairs);
+  API_END
 }
 
 extern "C" int dmrg_orbital_entropies(dmrg_ctx *c, double *s3, double *rho2) {

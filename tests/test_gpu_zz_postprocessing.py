@@ -58,3 +58,29 @@ def test_sweep_record_matches_sweep_and_full_ci():
         ref = fock.orbital_entropies(fock.pair_rdm_dets(x_fci, D, k))
         got = rec["entropies"][(nsw - 1) * steps + j]
         assert np.max(np.abs(got - np.array(ref))) < 1e-6, (k, got, ref)
+
+
+def test_mutual_information_matrix_matches_full_ci():
+    """dmrg_mutual_information once the sweeps are exact (L=6, M covering every Schmidt
+    rank): every two-orbital matrix, adjacent or not, equals the oracle's from the full-CI
+    vector (pair_rdm_dets_ij, Jordan-Wigner strings across the orbitals between), and the
+    entropies and mutual information follow."""
+    L, N = 6, 6
+    h, v = workloads.integrals(L, seed=12)
+    e_fci, x, D = fock.fci_ground(h, v, 3, 3)
+    ctx = binding.DMRG(h, v, N, 0, 4096)
+    ctx.sweep(4, tol=1e-11)
+    assert ctx.position()[0] == 0
+    e, _ = ctx.davidson(tol=1e-12, max_iter=400, allow_noconv=True)
+    assert abs(e - e_fci) < 1e-9
+    mi = ctx.mutual_information(pair_matrices=True)
+    ctx.close()
+    for i in range(L):
+        for j in range(i + 1, L):
+            ref = fock.pair_rdm_dets_ij(x, D, i, j)
+            got = mi["rho"][i, j]
+            assert np.max(np.abs(got / np.trace(got) - ref)) < 1e-8, (i, j)
+            si, sj, sij = fock.orbital_entropies(ref)
+            assert abs(mi["s1"][i] - si) < 1e-6 and abs(mi["s1"][j] - sj) < 1e-6
+            assert abs(mi["I"][i, j] - (si + sj - sij)) < 1e-6 and mi["I"][i, j] == mi["I"][j, i]
+    assert np.all(np.diag(mi["I"]) == 0.0)

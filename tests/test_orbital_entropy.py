@@ -143,3 +143,53 @@ def test_basis_export_format_rebuilds_the_blocks():
         assert a.sectors == b.sectors and a.dims == b.dims
         for E in a.sectors:
             assert np.array_equal(a.V[E], b.V[E])
+
+
+def _pair_operator(ops):
+    """16 x 16 matrix of a mode-operator string on the pair space alone (modes 0, 1 =
+    first orbital up, dn; 2, 3 = second orbital up, dn; index 4 b + c)."""
+    D = np.arange(16, dtype=np.int64)
+    D2, sign, ok = fock.apply_string(D, ops)
+    M = np.zeros((16, 16))
+    idx = lambda d: 4 * ((d & 1) + 2 * ((d >> 1) & 1)) + (((d >> 2) & 1) + 2 * ((d >> 3) & 1))  # noqa: E731
+    for d, d2, sg, k in zip(D, D2, sign, ok):
+        if k:
+            M[idx(int(d2)), idx(int(d))] = sg
+    return M
+
+
+def test_oracle_nonadjacent_pair_matrix_reproduces_expectation_values():
+    """For every orbital pair of a random L=5 state, tr(rho_ij O) equals <x|O|x> evaluated
+    on the whole determinant basis (Jordan-Wigner strings across the orbitals between
+    included) for hopping, pair-hopping and number operators between the two orbitals;
+    adjacent pairs equal pair_rdm_dets."""
+    rng = np.random.default_rng(11)
+    L = 5
+    D = fock.determinants(L, 3, 2)
+    x = rng.normal(size=len(D))
+    x /= np.linalg.norm(x)
+    lookup = {int(d): k for k, d in enumerate(D)}
+
+    def expect(ops):
+        D2, sign, ok = fock.apply_string(D, ops)
+        return sum(x[lookup[int(d2)]] * sg * x[k] for k, (d2, sg, o) in enumerate(zip(D2, sign, ok)) if o)
+
+    for i in range(L):
+        for j in range(i + 1, L):
+            rho = fock.pair_rdm_dets_ij(x, D, i, j)
+            assert abs(np.trace(rho) - 1.0) < 1e-12 and np.allclose(rho, rho.T, atol=1e-14)
+            if j == i + 1:
+                assert np.allclose(rho, fock.pair_rdm_dets(x, D, i), atol=1e-14)
+            for ops_full, ops_pair in [
+                ([(2 * i, True), (2 * j, False)], [(0, True), (2, False)]),          # c+_i,up c_j,up
+                ([(2 * j + 1, True), (2 * i + 1, False)], [(3, True), (1, False)]),  # c+_j,dn c_i,dn
+                ([(2 * i, True), (2 * i + 1, True), (2 * j + 1, False), (2 * j, False)],
+                 [(0, True), (1, True), (3, False), (2, False)]),                    # pair hopping
+                ([(2 * i, True), (2 * i, False), (2 * j + 1, True), (2 * j + 1, False)],
+                 [(0, True), (0, False), (3, True), (3, False)]),                    # n_i,up n_j,dn
+                ([(2 * i + 1, True), (2 * j, True), (2 * j + 1, False), (2 * i, False)],
+                 [(1, True), (2, True), (3, False), (0, False)]),                    # spin exchange
+            ]:
+                want = expect(ops_full)
+                got = np.trace(rho @ _pair_operator(ops_pair))
+                assert abs(got - want) < 1e-12, (i, j, ops_full, got, want)
