@@ -549,19 +549,24 @@ int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, 
 
 /*
  * dmrg_debug_validate -- host-only bounds check of the execution plan that
- * dmrg_debug_exec describes (default launch shape).  The four operand arenas
+ * dmrg_debug_exec describes (tune: NULL for the default launch shape, or 4
+ * doubles as in dmrg_debug_exec).  The four operand arenas
  * (stored operators and pre-summed temporaries of both blocks) are given
  * distinct element bases, so every operand address names its arena.  Every
  * operand view of every chunk (rows x columns with its strides) must lie
  * inside its arena, every psi view inside psi, every chunk slot and every
- * reduction inside the scratch array, identity sides must be square.
+ * reduction inside the scratch array, identity sides must be square; with
+ * tensor_cores, every operator and psi tile's source view inside its arena or
+ * psi, every tile inside the tile arenas, every task's X, Y^T and Z^T tile
+ * reads and its stack inside their bounds, every output slot inside the
+ * scratch array.
  * *checked receives the number of views and slots checked, *bad the number
  * of violations (the first one is described in dmrg_last_error).  No GPU is
  * used.
  */
 int dmrg_debug_validate(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
-                        const int *sec_l, int nr, const int *sec_r, int tensor_cores, long long *checked,
-                        long long *bad);
+                        const int *sec_l, int nr, const int *sec_r, int tensor_cores, const double *tune,
+                        long long *checked, long long *bad);
 
 /*
  * dmrg_debug_tc -- host-only dump of the tensor-core launch plan for the same

@@ -93,7 +93,7 @@ def lib():
         "dmrg_debug_exec": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
                                       C.c_int, dp, llp, llp, llp, llp]),
         "dmrg_debug_validate": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip,
-                                          C.c_int, llp, llp]),
+                                          C.c_int, dp, llp, llp]),
         "dmrg_debug_tc": (C.c_int, [C.c_int, C.c_int, C.c_int, dp, dp, C.c_int, C.c_int, ip, C.c_int, ip, dp,
                                     llp, llp, llp, llp, llp]),
         "dmrg_debug_newops": (C.c_int, [C.c_int, dp, dp, C.c_int, C.c_int, C.c_int,
@@ -172,14 +172,18 @@ def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
     return dict(zip(keys, (int(x) for x in cnt))), xs, ch, red
 
 
-def debug_validate(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False):
-    """Host-only bounds check of the execution plan: (views checked, violations, first violation)."""
+def debug_validate(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
+    """Host-only bounds check of the execution plan (and, with tensor_cores, of the
+    tensor-core tile plan) for the default or a given launch shape (4 doubles:
+    target_chunks, min_chunk, tc_min, by_work): (views checked, violations, first violation)."""
     h, v = _f64(h), _f64(v)
     tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
     tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
+    tune_arr = None if tune is None else np.ascontiguousarray(tune, dtype=np.float64)
     chk, bad = C.c_longlong(), C.c_longlong()
     _check(lib().dmrg_debug_validate(h.shape[0], N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr),
-                                     _iptr(tr), int(tensor_cores), C.byref(chk), C.byref(bad)))
+                                     _iptr(tr), int(tensor_cores), None if tune_arr is None else _dptr(tune_arr),
+                                     C.byref(chk), C.byref(bad)))
     return chk.value, bad.value, (lib().dmrg_last_error().decode() if bad.value else "")
 
 

@@ -2859,10 +2859,19 @@ extern "C" int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const 
 
 extern "C" int dmrg_debug_validate(int L, int N, int two_sz, const double *h, const double *v, int k, int nl,
                                    const int *sec_l, int nr, const int *sec_r, int tensor_cores,
-                                   long long *checked, long long *bad) {
+                                   const double *tune, long long *checked, long long *bad) {
   API_BEGIN
   if (L < 2 || k < 0 || k > L - 2 || !h || !v || nl < 1 || nr < 1 || !sec_l || !sec_r || !checked || !bad)
     throw Fail{DMRG_EINVAL, "dmrg_debug_validate: bad arguments"};
+  ChainTune T;
+  if (tune) {
+    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1))
+      throw Fail{DMRG_EINVAL, "dmrg_debug_validate: bad tune"};
+    T.target_chunks = tune[0];
+    T.min_chunk = tune[1];
+    T.tc_min = (int)tune[2];
+    T.by_work = (int)tune[3];
+  }
   if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
   Integrals I;
   I.L = L;
@@ -2895,7 +2904,7 @@ extern "C" int dmrg_debug_validate(int L, int N, int two_sz, const double *h, co
   double f = 0.0;
   expand_hpsi_grouped(rps, A, Y, lb, CL, f);
   ExecPlan X;
-  plan_exec(CL, tensor_cores != 0, true, ChainTune(), X);
+  plan_exec(CL, tensor_cores != 0, true, T, X);
   long long nchk = 0, nbad = 0;
   std::string first;
   auto view = [&](const char *what, uint64_t at, int rows, int cols, int rst, int cst, bool op) {
@@ -2946,6 +2955,38 @@ extern "C" int dmrg_debug_validate(int L, int N, int two_sz, const double *h, co
     view("output block", r.d, r.m, r.q, r.drs, r.dcs, false);
     ++nchk;
     if (r.soff + (int64_t)r.nsplit * r.m * r.q > X.soff && !nbad++) first = "reduction slots leave the scratch array";
+  }
+  if (tensor_cores && !X.vt.empty()) {
+    // the tensor-core plan: every tile's source view inside its arena (the plan keeps
+    // FP32-element addresses times 4, here the synthetic arena bases above), every
+    // tile and every task's tile reads inside the tile arenas
+    TcPlan P;
+    plan_tc(X.xs, X.vt, P);
+    auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
+    for (const TileSpec &t : P.ts) {
+      ++nchk;
+      if (t.dst + c16(t.R) * c16(t.K) * 4 > P.opbytes && !nbad++) first = "operator tile leaves the tile arena";
+      if (t.src != ~0ull) view("operator tile source", t.src / 4, t.R, t.K, t.rs, t.cs, true);
+    }
+    for (const PsiTileSpec &t : P.ps) {
+      ++nchk;
+      if (t.dst + c16(t.p) * c16(t.n) * 4 > P.psibytes && !nbad++) first = "psi tile leaves the tile arena";
+      view("psi tile source", (uint64_t)t.src, t.n, t.p, t.p, 1, false);
+    }
+    for (size_t g = 0; g < P.tg.size(); ++g) {
+      const TcGroup &G = P.tg[g];
+      for (int i = G.first; i < G.first + G.count; ++i) {
+        const TcEntry &e = P.te[(size_t)i];
+        ++nchk;
+        if ((e.xt + c16(G.m) * c16(e.n) * 4 > P.opbytes || e.zt + c16(G.q) * c16(e.p) * 4 > P.opbytes ||
+             e.yt + c16(e.p) * c16(e.n) * 4 > P.psibytes || e.stack > 8 || i + e.stack > G.first + G.count) &&
+            !nbad++)
+          first = "tensor-core task reads outside its tiles or stack";
+      }
+      ++nchk;
+      const uint64_t slot_last = G.d + (uint64_t)(G.m - 1) * G.drs + (uint64_t)(G.q - 1) * G.dcs;
+      if (slot_last >= (uint64_t)X.soff && !nbad++) first = "tensor-core output slot leaves the scratch array";
+    }
   }
   *checked = nchk;
   *bad = nbad;

@@ -208,6 +208,10 @@ def test_operand_views_in_bounds_on_random_layouts(seed):
         return out or [(0, 0, 1)]
     sl, sr = table(k), table(L - k - 2)
     h, v = workloads.integrals(L, seed=seed)
+    # the default launch shape and shapes the autotuner can pick (split granularity,
+    # tensor-core routing threshold, group order); with tensor cores, the tile plan too
+    tunes = [None, [1.0, 0.0, 1, 1], [32768.0, 5.0e4, 17, 0], [8192.0, 2.0e5, 1, 1], [64.0, 1.0e7, 65, 1]]
     for tc in (False, True):
-        checked, bad, first = binding.debug_validate(h, v, N, tsz, k, sl, sr, tensor_cores=tc)
-        assert bad == 0, first
+        for tune in tunes:
+            checked, bad, first = binding.debug_validate(h, v, N, tsz, k, sl, sr, tensor_cores=tc, tune=tune)
+            assert checked > 0 and bad == 0, (tune, first)
