@@ -371,8 +371,10 @@ int dmrg_set_bond_dims(dmrg_ctx *ctx, int m_forward, int m_backward);
 /*
  * dmrg_set_precision -- change the working precision of the Davidson matvecs
  * (DMRG_PREC_*) of an existing context; blocks and the wave function are kept,
- * the H.psi task lists and low-precision operator copies are rebuilt on next
- * use.  DMRG_EINVAL for an unknown precision.  Synchronizes the stream.
+ * the old precision's low-precision operator copies, tensor-core tiles and task
+ * list are released at once (so the largest workloads can switch without
+ * holding both), and the H.psi task lists are rebuilt on next use.
+ * DMRG_EINVAL for an unknown precision.  Synchronizes the stream.
  */
 int dmrg_set_precision(dmrg_ctx *ctx, int precision);
 
@@ -413,7 +415,11 @@ int dmrg_block_op(dmrg_ctx *ctx, int side, int kind, int i, int j, double *out, 
  * out); sigma is written, not accumulated.  The batch does not own the
  * contexts: free the batch first.  Errors: DMRG_EINVAL (n < 1, NULL
  * arguments, contexts on different streams or precision classes),
- * DMRG_ESTATE (a context without the blocks of its position),
+ * DMRG_ESTATE (a context without the blocks of its position; from
+ * dmrg_batch_hpsi: a context whose H.psi task list was rebuilt or released
+ * since the batch was built, by a move, a precision or launch-shape change:
+ * the batch addresses that context's operator copies and must be created
+ * again),
  * DMRG_ETIMEOUT (a bounded tensor-core wait ran out; that call's sigma is
  * invalid), DMRG_ENOMEM / DMRG_ECUDA.
  */

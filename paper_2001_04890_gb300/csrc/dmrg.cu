@@ -901,6 +901,26 @@ struct DevChain {
     CK(cudaStreamSynchronize(s));  // tsd is released on return
   }
 
+  // device memory of the task list back to the allocator
+  void release() {
+    ent.release();
+    xent.release();
+    all.release();
+    big.release();
+    flat.release();
+    red.release();
+    scratch.release();
+    tce.release();
+    tcg.release();
+    pts.release();
+    optiles.release();
+    psitiles.release();
+    tc_counter.release();
+    nall = nbig = nflat = ntc = ntiles = nred = npts = 0;
+    ntc_shape[0] = ntc_shape[1] = ntc_shape[2] = 0;
+    nent = red_total = scratch_n = 0;
+  }
+
   void launch_tc(uint64_t yb, uint64_t tb, int *status, cudaStream_t s) const {
     if (ntc == 0) return;
     if (!status) throw Fail{DMRG_EINVAL, "tensor-core task list launched without a status word"};
@@ -1069,6 +1089,7 @@ struct dmrg_ctx {
   int refine_keep = 0;       // Ritz vectors carried between refinement steps (dmrg_set_davidson)
   int sweep_max_iter = 200;  // matvec cap of each Davidson step of a sweep
   int renorm_prec = DMRG_PREC_FP64;  // renormalization products: FP64 or FP32 O (dmrg_set_renorm_precision)
+  long long plan_gen = 0;  // count of H.psi plan builds and releases (a batch's record of its members)
   double cut_gap = std::numeric_limits<double>::infinity();
   double min_cut_gap = std::numeric_limits<double>::infinity();
   long long truncations = 0, straddled = 0;
@@ -1321,6 +1342,7 @@ static void build_hplan(dmrg_ctx *c) {
   DevBlock *lb = lblock(c), *rb = rblock(c);
   if (P.valid && P.k == c->k && P.lb == lb && P.rb == rb) return;
   P.valid = false;
+  ++c->plan_gen;
   P.k = c->k;
   P.lb = lb;
   P.rb = rb;
@@ -2396,6 +2418,9 @@ extern "C" int dmrg_set_precision(dmrg_ctx *c, int precision) {
     CK(cudaStreamSynchronize(c->stream));
     c->prec = precision;
     c->plan.valid = false;  // task lists and low-precision copies are rebuilt on next use
+    c->plan.chain32.release();  // the old working precision's copies, tiles and task list
+    for (auto &f : c->plan.f32) f.release();
+    ++c->plan_gen;
   }
   API_END
 }
@@ -3188,6 +3213,7 @@ extern "C" int dmrg_hpsi_noalloc(dmrg_ctx *c, const double *psi, double *sigma) 
 // ---------------------------------------------------------------------------
 struct dmrg_batch {
   std::vector<dmrg_ctx *> ctx;
+  std::vector<long long> gen;  // each context's plan generation when the batch was built
   std::vector<long long> off;  // n + 1 offsets into the concatenated vectors
   cudaStream_t stream = nullptr;
   bool lowp = false, tc = false;
@@ -3257,6 +3283,7 @@ extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out)
   }
   ChainList CL;
   batch_chainlist(b->ctx, CL, b->off, b->flops);
+  for (dmrg_ctx *c : b->ctx) b->gen.push_back(c->plan_gen);
   b->lowp = ctxs[0]->prec != DMRG_PREC_FP64;
   b->tc = ctxs[0]->prec == DMRG_PREC_BF16X3;
   b->chain.upload(CL, b->stream, b->tc, true, b->tune);
@@ -3288,6 +3315,11 @@ extern "C" int dmrg_batch_layout(dmrg_batch *b, long long *offsets, double *flop
 extern "C" int dmrg_batch_hpsi(dmrg_batch *b, const double *psi, double *sigma, int device_ptrs) {
   API_BEGIN
   if (!b || !psi || !sigma) throw Fail{DMRG_EINVAL, "NULL argument"};
+  // the batch's task list addresses its contexts' operator copies: refuse if any was rebuilt
+  for (size_t i = 0; i < b->ctx.size(); ++i)
+    if (!b->ctx[i]->plan.valid || b->ctx[i]->plan_gen != b->gen[i])
+      throw Fail{DMRG_ESTATE, "a batched context changed position, precision or launch shape since "
+                              "dmrg_batch_create (create the batch again)"};
   const int64_t n = b->off.back();
   cudaStream_t cs = b->stream, s = b->own;
   CK(cudaMemcpyAsync(b->psi.p, psi, n * sizeof(double),
@@ -3776,6 +3808,8 @@ extern "C" int dmrg_batch_autotune(dmrg_batch *b, int reps, double *best_ms, dou
   double fl = 0.0;
   batch_chainlist(b->ctx, CL, off, fl);
   if (off != b->off) throw Fail{DMRG_ESTATE, "a batched context changed position since dmrg_batch_create"};
+  b->gen.clear();
+  for (dmrg_ctx *c : b->ctx) b->gen.push_back(c->plan_gen);
   const int64_t n = b->off.back();
   CK(launch_fill_guess(b->psi.p, n, 0x5eedull, b->stream));
   double ms = 0.0;

@@ -53,3 +53,28 @@ def test_batched_hpsi_equals_per_instance(prec):
     batch.close()
     for c in ctxs:
         c.close()
+
+
+def test_batch_refuses_after_a_member_rebuilds_its_task_list():
+    """A batch addresses its contexts' operator copies: after one of them switches
+    precision (its copies are released), dmrg_batch_hpsi refuses instead of reading them."""
+    ctxs = []
+    for seed, (L, M) in enumerate([(8, 40), (10, 64)]):
+        h, v = workloads.integrals(L, seed=seed)
+        c = binding.DMRG(h, v, L, 0, M, precision=binding.PREC_FP32)
+        workloads.grow_middle_bond(c, L, L // 2, L // 2, M, (L - 2) // 2, seed=seed)
+        ctxs.append(c)
+    batch = binding.Batch(ctxs)
+    x = workloads.gaussian(batch.offsets[-1], seed=5)
+    y = batch.hpsi(x)
+    ctxs[1].set_precision(binding.PREC_BF16X3)
+    with pytest.raises(binding.DMRGError) as err:
+        batch.hpsi(x)
+    assert err.value.code == binding.DMRG_ESTATE
+    batch.close()
+    ctxs[1].set_precision(binding.PREC_FP32)
+    batch = binding.Batch(ctxs)  # created again: same result
+    assert np.max(np.abs(batch.hpsi(x) - y)) <= 1e-12 * np.max(np.abs(y))
+    batch.close()
+    for c in ctxs:
+        c.close()
