@@ -50,12 +50,15 @@ enum {
 
 /* FP64: every operation in FP64.  FP32: FP64 block operators, renormalization and
  * density matrices; FP32 copies of the operators for the Davidson matvecs (FP32
- * CUDA-core arithmetic).  BF16X3: as FP32, but H.psi output blocks with both
- * sides <= 128 and one side >= tc_min (33 by default; see dmrg_set_tune) run on
+ * CUDA-core arithmetic).  BF16X3: FP64 block operators, renormalization and
+ * density matrices; H.psi output blocks with both sides <= 128 and one side >=
+ * tc_min (33 by default, 1 routes every such block; see dmrg_set_tune) run on
  * the tcgen05 tensor cores as three-pass split-BF16 products with FP32
- * accumulation in tensor memory.  In both mixed modes Davidson finishes with a
- * defect-corrected refinement that applies H in FP64 to the current vector
- * (see dmrg_davidson), so energies are FP64 quality. */
+ * accumulation in tensor memory, their operand tiles split straight from the
+ * FP64 operators (no FP32 copies are held), and the remaining blocks run in
+ * FP64.  In both mixed modes Davidson finishes with a defect-corrected
+ * refinement that applies H in FP64 to the current vector (see dmrg_davidson),
+ * so energies are FP64 quality. */
 enum { DMRG_PREC_FP64 = 0, DMRG_PREC_FP32 = 1, DMRG_PREC_BF16X3 = 2 };
 
 typedef struct dmrg_ctx dmrg_ctx; /* opaque, library-owned */

@@ -705,7 +705,7 @@ struct TcPlan {
 };
 
 static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
-                    TcPlan &P, std::vector<int> *entry_of = nullptr) {
+                    TcPlan &P, std::vector<int> *entry_of = nullptr, uint64_t elem_bytes = 4) {
   auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
   const size_t nv = vt.size();
   // kernel shape per block: 2 (m <= 64, q, p <= 32), 1 (m, q, p <= 64), 0 (the rest);
@@ -779,8 +779,8 @@ static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, 
     const ChainEntry &e = xs[(size_t)src[i]];
     const TcGroup &g = P.tg[(size_t)blk[i]];
     if ((o & 1) == 0)
-      return e.x == ~0ull ? ViewKey{~0ull, 0, 0, e.n, e.n} : ViewKey{e.x * 4ull, e.xrs, e.xcs, g.m, e.n};
-    return e.z == ~0ull ? ViewKey{~0ull, 0, 0, e.p, e.p} : ViewKey{e.z * 4ull, e.zcs, e.zrs, g.q, e.p};
+      return e.x == ~0ull ? ViewKey{~0ull, 0, 0, e.n, e.n} : ViewKey{e.x * elem_bytes, e.xrs, e.xcs, g.m, e.n};
+    return e.z == ~0ull ? ViewKey{~0ull, 0, 0, e.p, e.p} : ViewKey{e.z * elem_bytes, e.zcs, e.zrs, g.q, e.p};
   };
   std::vector<uint32_t> vid;
   std::vector<size_t> vfirst;
@@ -842,12 +842,14 @@ struct DevChain {
   int64_t nent = 0;
   int64_t red_total = 0, scratch_n = 0;
   bool split = false;
+  bool ops32 = false;  // X and Z operands are FP32 copies (else the FP64 masters)
 
   void upload(const ChainList &CL, cudaStream_t s, bool tensor_cores = false, bool split_tasks = false,
-              const ChainTune &tune = ChainTune()) {
+              const ChainTune &tune = ChainTune(), bool ops32_in = false) {
     ExecPlan X;
     plan_exec(CL, tensor_cores, split_tasks, tune, X);
     split = split_tasks;
+    ops32 = ops32_in;
     flat_wide = tune.flat_wide;
     const auto &xs = X.xs;
     const std::vector<ChainGroup> &vb = X.vb, &vf = X.vf, &vt = X.vt;
@@ -878,7 +880,7 @@ struct DevChain {
   void build_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
                 cudaStream_t s) {
     TcPlan P;
-    plan_tc(xs, vt, P);
+    plan_tc(xs, vt, P, nullptr, ops32 ? 4 : 8);
     std::vector<TcEntry> &te = P.te;
     std::vector<TcGroup> &tg = P.tg;
     std::vector<TileSpec> &ts = P.ts;
@@ -897,7 +899,7 @@ struct DevChain {
     tc_counter.alloc(3);
     DBuf<TileSpec> tsd;
     tsd.upload(ts, s);
-    CK(launch_build_tiles(tsd.p, (int)ts.size(), optiles.p, s));
+    CK(launch_build_tiles(tsd.p, (int)ts.size(), optiles.p, !ops32, s));
     CK(cudaStreamSynchronize(s));  // tsd is released on return
   }
 
@@ -936,19 +938,19 @@ struct DevChain {
   // The launch sequence.  The chunk partials of a split task list go to the
   // list's own scratch array, or to ext (at least scratch_n doubles, cleared
   // here) when the caller provides one; nothing is allocated here.
-  void launch(bool f32ops, uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s,
-              int *status = nullptr, double *ext = nullptr) const {
+  void launch(uint64_t xb, uint64_t yb, uint64_t zb, uint64_t db, cudaStream_t s, int *status = nullptr,
+              double *ext = nullptr) const {
     double *part = ext ? ext : scratch.p;
     const uint64_t tb = split ? (uint64_t)(uintptr_t)part : db;
     if (split && scratch_n > 0) CK(cudaMemsetAsync(part, 0, scratch_n * sizeof(double), s));
-    if (f32ops) {
+    if (ops32) {
       CK(launch_chain_f32ops(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_f32ops(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 12 : 8));
-      launch_tc(yb, tb, status, s);
     } else {
       CK(launch_chain_fp64(xent.p, big.p, nbig, ntiles, xb, yb, zb, tb, s));
       CK(launch_chain_flat_fp64(xent.p, flat.p, nflat, xb, yb, zb, tb, s, flat_wide ? 6 : 4));
     }
+    launch_tc(yb, tb, status, s);
     if (split) CK(launch_reduce_partials(red.p, nred, red_total, part, (double *)(uintptr_t)db, s));
   }
 };
@@ -1366,7 +1368,7 @@ static void build_hplan(dmrg_ctx *c) {
   CK(cudaMemsetAsync(P.diag.p, 0, Y.dim * sizeof(double), c->stream));
   CK(launch_diag_fp64(P.chain.ent.p, P.chain.all.p, P.chain.nall, 0, 0, P.diag.p, c->stream));
   P.lowp = c->prec != DMRG_PREC_FP64;
-  if (P.lowp) {
+  if (c->prec == DMRG_PREC_FP32) {
     // FP32 working copies of every operand of the H.psi task list (Davidson matvecs)
     const double *src[4] = {lb->arena(), rb->arena(), P.temps.arena[0].p, P.temps.arena[1].p};
     const int64_t cnt[4] = {lb->lay.total, rb->lay.total, P.temps.set.total[0], P.temps.set.total[1]};
@@ -1377,7 +1379,15 @@ static void build_hplan(dmrg_ctx *c) {
     ChainList CL32;
     double fl32 = 0.0;
     hpsi_chainlist(c, true, CL32, fl32);
-    P.chain32.upload(CL32, c->stream, c->prec == DMRG_PREC_BF16X3, true, c->tune);
+    P.chain32.upload(CL32, c->stream, false, true, c->tune, true);
+    CK(cudaStreamSynchronize(c->stream));
+  } else if (c->prec == DMRG_PREC_BF16X3) {
+    // the tensor-core list reads the FP64 masters: tiles are split straight from them, and
+    // blocks the tensor cores do not take run in FP64 (no FP32 copies are held)
+    ChainList CLt;
+    double flt = 0.0;
+    hpsi_chainlist(c, false, CLt, flt);
+    P.chain32.upload(CLt, c->stream, true, true, c->tune, false);
     CK(cudaStreamSynchronize(c->stream));
   }
   CK(cudaStreamSynchronize(c->stream));
@@ -1420,8 +1430,8 @@ static void hpsi_dev(dmrg_ctx *c, const double *psi, double *sigma, bool fp64 = 
     c->ev.push_back(e);
   }
   CK(cudaEventRecord(c->ev[c->ev_used], c->stream));
-  (lowp ? P.chain32 : P.chain).launch(lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma,
-                                      c->stream, c->dstatus.p);
+  (lowp ? P.chain32 : P.chain).launch(0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream,
+                                      c->dstatus.p);
   CK(cudaEventRecord(c->ev[c->ev_used + 1], c->stream));
   c->ev_used += 2;
   c->hpsi_calls += 1;
@@ -1578,12 +1588,12 @@ static std::unique_ptr<DevBlock> renormalize_block(dmrg_ctx *c, int direction, c
       ce.x = f32b + (ce.x - d64);
       ce.z = f32b + (ce.z - d64);
     }
-    dc.upload(CL, c->stream);
-    dc.launch(true, 0, 0, 0, 0, c->stream);
+    dc.upload(CL, c->stream, false, false, ChainTune(), true);
+    dc.launch(0, 0, 0, 0, c->stream);
     CK(cudaStreamSynchronize(c->stream));
   } else {
     dc.upload(CL, c->stream);
-    dc.launch(false, 0, 0, 0, 0, c->stream);
+    dc.launch(0, 0, 0, 0, c->stream);
     CK(cudaStreamSynchronize(c->stream));
   }
   nb->parent = enl;
@@ -1678,7 +1688,7 @@ static void rdm_truncate(dmrg_ctx *c, int direction, const Enlarged &enl, std::v
   DevChain dc;
   dc.upload(CL, c->stream);
   const uint64_t pb = (uint64_t)(uintptr_t)c->psi.p;
-  dc.launch(false, 0, pb, pb, 0, c->stream);
+  dc.launch(0, pb, pb, 0, c->stream);
 
   // per-sector eigendecomposition (LAPACK-style syevd, eigenvalues ascending)
   int maxn = 0;
@@ -1850,7 +1860,7 @@ static void predict_psi(dmrg_ctx *c, const Psi &old, const DBuf<double> &oldpsi,
   CK(cudaMemsetAsync(c->psi.p, 0, Y.dim * sizeof(double), c->stream));
   DevChain dc;
   dc.upload(CL, c->stream);
-  dc.launch(false, 0, 0, 0, (uint64_t)(uintptr_t)c->psi.p, c->stream);
+  dc.launch(0, 0, 0, (uint64_t)(uintptr_t)c->psi.p, c->stream);
   CK(cudaStreamSynchronize(c->stream));
   c->psi_valid = !CL.flat.empty();
 }
@@ -3200,7 +3210,7 @@ extern "C" int dmrg_hpsi_noalloc(dmrg_ctx *c, const double *psi, double *sigma) 
   // (a time-out of this call is read by dmrg_check_status or the next synchronizing call)
   CK(cudaMemsetAsync(c->dstatus.p, 0, 8 * sizeof(int), c->stream));
   CK(cudaMemsetAsync(sigma, 0, P.psi.dim * sizeof(double), c->stream));
-  ch.launch(lowp, 0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream, c->dstatus.p, scratch);
+  ch.launch(0, (uint64_t)(uintptr_t)psi, 0, (uint64_t)(uintptr_t)sigma, c->stream, c->dstatus.p, scratch);
   API_END
 }
 
@@ -3286,7 +3296,7 @@ extern "C" int dmrg_batch_create(int n, dmrg_ctx *const *ctxs, dmrg_batch **out)
   for (dmrg_ctx *c : b->ctx) b->gen.push_back(c->plan_gen);
   b->lowp = ctxs[0]->prec != DMRG_PREC_FP64;
   b->tc = ctxs[0]->prec == DMRG_PREC_BF16X3;
-  b->chain.upload(CL, b->stream, b->tc, true, b->tune);
+  b->chain.upload(CL, b->stream, b->tc, true, b->tune, ctxs[0]->prec == DMRG_PREC_FP32);
   b->psi.alloc((size_t)std::max<long long>(b->off.back(), 1));
   b->sigma.alloc((size_t)std::max<long long>(b->off.back(), 1));
   CK(cudaStreamCreateWithFlags(&b->own, cudaStreamNonBlocking));
@@ -3329,7 +3339,7 @@ extern "C" int dmrg_batch_hpsi(dmrg_batch *b, const double *psi, double *sigma, 
   int *status = b->ctx[0]->dstatus.p;
   auto body = [&]() {
     CK(cudaMemsetAsync(b->sigma.p, 0, n * sizeof(double), s));
-    b->chain.launch(b->lowp, 0, (uint64_t)(uintptr_t)b->psi.p, 0, (uint64_t)(uintptr_t)b->sigma.p, s, status);
+    b->chain.launch(0, (uint64_t)(uintptr_t)b->psi.p, 0, (uint64_t)(uintptr_t)b->sigma.p, s, status);
   };
   if (!b->exec) {
     body();  // first call runs directly (and sets kernel attributes), then captures the sequence
@@ -3375,12 +3385,12 @@ struct EventPair {
   }
 };
 
-static double time_chain(const DevChain &ch, bool lowp, const double *x, double *y, int64_t n,
+static double time_chain(const DevChain &ch, const double *x, double *y, int64_t n,
                          cudaStream_t s, int *status, int reps) {
   EventPair ev;
   auto once = [&]() {
     CK(cudaMemsetAsync(y, 0, (size_t)n * sizeof(double), s));
-    ch.launch(lowp, 0, (uint64_t)(uintptr_t)x, 0, (uint64_t)(uintptr_t)y, s, status);
+    ch.launch(0, (uint64_t)(uintptr_t)x, 0, (uint64_t)(uintptr_t)y, s, status);
   };
   once();
   CK(cudaEventRecord(ev.a, s));
@@ -3394,12 +3404,12 @@ static double time_chain(const DevChain &ch, bool lowp, const double *x, double 
 
 // Coordinate search: split granularity first, then (tensor cores only) the
 // smallest output-block side routed to the tensor-core kernel.
-static ChainTune autotune_chain(const ChainList &CL, bool tc, bool lowp, const double *x, double *y, int64_t n,
+static ChainTune autotune_chain(const ChainList &CL, bool tc, bool ops32, const double *x, double *y, int64_t n,
                                 cudaStream_t s, int *status, int reps, ChainTune start, double &best_ms) {
   auto run = [&](const ChainTune &t) {
     DevChain ch;
-    ch.upload(CL, s, tc, true, t);
-    return time_chain(ch, lowp, x, y, n, s, status, reps);
+    ch.upload(CL, s, tc, true, t, ops32);
+    return time_chain(ch, x, y, n, s, status, reps);
   };
   ChainTune best = start;
   best_ms = run(best);
@@ -3466,12 +3476,13 @@ extern "C" int dmrg_autotune(dmrg_ctx *c, int reps, double *best_ms, double *par
   {
     ChainList CL;
     double fl = 0.0;
-    hpsi_chainlist(c, lowp, CL, fl);
+    hpsi_chainlist(c, c->prec == DMRG_PREC_FP32, CL, fl);
     DBuf<double> x, y;
     x.alloc((size_t)std::max<int64_t>(n, 1));
     y.alloc((size_t)std::max<int64_t>(n, 1));
     CK(launch_fill_guess(x.p, n, 0x5eedull, c->stream));
-    best = autotune_chain(CL, tc, lowp, x.p, y.p, n, c->stream, c->dstatus.p, reps, c->tune, ms);
+    best = autotune_chain(CL, tc, c->prec == DMRG_PREC_FP32, x.p, y.p, n, c->stream, c->dstatus.p, reps, c->tune,
+                          ms);
     CK(cudaStreamSynchronize(c->stream));
   }
   check_status(c);
@@ -3813,11 +3824,11 @@ extern "C" int dmrg_batch_autotune(dmrg_batch *b, int reps, double *best_ms, dou
   const int64_t n = b->off.back();
   CK(launch_fill_guess(b->psi.p, n, 0x5eedull, b->stream));
   double ms = 0.0;
-  ChainTune best = autotune_chain(CL, b->tc, b->lowp, b->psi.p, b->sigma.p, n, b->stream,
+  ChainTune best = autotune_chain(CL, b->tc, b->ctx[0]->prec == DMRG_PREC_FP32, b->psi.p, b->sigma.p, n, b->stream,
                                   b->ctx[0]->dstatus.p, reps, b->tune, ms);
   check_status(b->ctx[0]);
   b->tune = best;
-  b->chain.upload(CL, b->stream, b->tc, true, best);
+  b->chain.upload(CL, b->stream, b->tc, true, best, b->ctx[0]->prec == DMRG_PREC_FP32);
   if (b->exec) cudaGraphExecDestroy(b->exec);
   if (b->graph) cudaGraphDestroy(b->graph);
   b->exec = nullptr;

@@ -90,7 +90,7 @@ namespace dmrg {
 // (rg, kg) at byte (rg * K16/8 + kg) * 128), rows padded to R8 = ceil8(R),
 // K to K16 = ceil16(K) with zeros; the lo part follows the hi part.
 struct TileSpec {
-  uint64_t src;     // element address of the FP32 source view (element (r, k) at src + r*rs + k*cs)
+  uint64_t src;     // byte address of the source view (FP32 or FP64; element (r, k) at element r*rs + k*cs)
   uint64_t dst;     // byte offset of the tile in the tile arena
   int rs, cs, R, K;
 };
@@ -122,8 +122,8 @@ struct TcGroup {
   int first, count;
 };
 
-// operator tiles from FP32 sources (src == ~0: exact identity tile)
-cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, cudaStream_t s);
+// operator tiles from FP32 (src_f64 false) or FP64 sources (src == ~0: exact identity tile)
+cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, bool src_f64, cudaStream_t s);
 // Y^T tiles of FP64 psi blocks
 cudaError_t launch_psi_tiles(const PsiTileSpec *t, int ntiles, const double *psi, uint8_t *arena,
                              cudaStream_t s);

@@ -132,6 +132,8 @@ __device__ __forceinline__ void write_tile(uint8_t *img, int R, int K, Load load
   }
 }
 
+// Tiles of operator views; the sources are FP32 copies or the FP64 masters (SRC).
+template <typename SRC>
 __global__ void __launch_bounds__(256) build_tiles_kernel(const TileSpec *__restrict__ T, int ntiles,
                                                           uint8_t *arena) {
   for (int t = blockIdx.x; t < ntiles; t += gridDim.x) {
@@ -140,9 +142,10 @@ __global__ void __launch_bounds__(256) build_tiles_kernel(const TileSpec *__rest
     if (s.src == ~0ull) {
       write_tile(img, s.R, s.K, [](int r, int k) { return r == k ? 1.f : 0.f; }, threadIdx.x, blockDim.x);
     } else {
-      const float *X = reinterpret_cast<const float *>(s.src);
+      const SRC *X = reinterpret_cast<const SRC *>(s.src);
       const int64_t rs = s.rs, cs = s.cs;
-      write_tile(img, s.R, s.K, [&](int r, int k) { return X[r * rs + k * cs]; }, threadIdx.x, blockDim.x);
+      write_tile(img, s.R, s.K, [&](int r, int k) { return (float)X[r * rs + k * cs]; }, threadIdx.x,
+                 blockDim.x);
     }
   }
 }
@@ -159,10 +162,13 @@ __global__ void __launch_bounds__(256) psi_tiles_kernel(const PsiTileSpec *__res
   }
 }
 
-cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, cudaStream_t s) {
+cudaError_t launch_build_tiles(const TileSpec *t, int ntiles, uint8_t *arena, bool src_f64, cudaStream_t s) {
   if (ntiles <= 0) return cudaSuccess;
   add_kernel_launches(1);
-  build_tiles_kernel<<<std::min(ntiles, 152 * 16), 256, 0, s>>>(t, ntiles, arena);
+  if (src_f64)
+    build_tiles_kernel<double><<<std::min(ntiles, 152 * 16), 256, 0, s>>>(t, ntiles, arena);
+  else
+    build_tiles_kernel<float><<<std::min(ntiles, 152 * 16), 256, 0, s>>>(t, ntiles, arena);
   return cudaGetLastError();
 }
 
