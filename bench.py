@@ -71,6 +71,17 @@ TRAFFIC_PER_LAUNCH = {
     ("c2", 0, 512, (32768.0, 200000.0, 33, 0, 0)): 1.0293e9 + 0.1472e9,
     ("c2", 0, 512, (131072.0, 50000.0, 33, 0, 0)): 1.8010e9 + 0.7325e9,
     ("c2", 0, 512, (131072.0, 200000.0, 33, 0, 0)): 1.4767e9 + 0.4892e9,
+    # split-BF16x3 H.psi, every block on the tensor cores: DRAM read + write of the
+    # chain_tc2 launches of one H.psi (one shape at M=3000, two at M=6000)
+    ("c5a", 2, 3000, (8192.0, 200000.0, 1, 1, 1)): 434.8e9 + 0.175e9,
+    ("c5b", 2, 6000, (8192.0, 200000.0, 1, 1, 1)): 1282.5e9 + 0.536e9,
+}
+# Algorithmic bytes of one split-BF16x3 H.psi: the distinct pre-split operator tiles
+# (4 bytes per padded element, each read once), the psi tiles, psi and sigma
+# (host task dump of the same launch plan).
+ALG_BYTES = {
+    "c5a": 30.7e9 + 10e6 + 2 * 10.6e6,
+    "c5b": 88.655e9 + 27.8e6 + 2 * 40.6e6,
 }
 
 
@@ -800,6 +811,9 @@ def davidson_line(args, wl, rank, world, prec):
                 "peak_source": "unit counts x 2.07 GHz (no measured SIMT peak)", "unit": "TFLOP/s"}
     roof["frac"] = (kernel_tflops / roof["peak"]) if (kernel_tflops and roof["peak"]) else None
     roof["traffic"] = TRAFFIC_PER_LAUNCH.get((args.workload, prec, wl["M"], _shape_key(r["tune"])))
+    if prec == 2 and args.workload in ALG_BYTES and wl["M"] == WORKLOADS[args.workload]["M"]:
+        roof["traffic_scope"] = "DRAM bytes of the chain_tc2 launches of one H.psi (ncu, one capture)"
+        roof["algorithmic_bytes"] = ALG_BYTES[args.workload]
     hps = st["hpsi_calls"] / K
     line = {
         "metric": METRIC,
