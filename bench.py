@@ -67,14 +67,14 @@ FP32_SIMT_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12  # FP32 FMA units x 2 FLOP x ma
 # DRAM bytes (read + write) per launch of the dominant H.psi kernel, from one ncu
 # capture of the unchanged kernel at that workload and precision (else null)
 TRAFFIC_PER_LAUNCH = {
-    ("c2", 0, 512, (32768.0, 50000.0, 33, 0, 0)): 1.034e9 + 0.147e9,
-    ("c2", 0, 512, (32768.0, 200000.0, 33, 0, 0)): 1.0293e9 + 0.1472e9,
-    ("c2", 0, 512, (131072.0, 50000.0, 33, 0, 0)): 1.8010e9 + 0.7325e9,
-    ("c2", 0, 512, (131072.0, 200000.0, 33, 0, 0)): 1.4767e9 + 0.4892e9,
+    ("c2", 0, 512, (32768.0, 50000.0, 33, 0, 0, 0)): 1.034e9 + 0.147e9,
+    ("c2", 0, 512, (32768.0, 200000.0, 33, 0, 0, 0)): 1.0293e9 + 0.1472e9,
+    ("c2", 0, 512, (131072.0, 50000.0, 33, 0, 0, 0)): 1.8010e9 + 0.7325e9,
+    ("c2", 0, 512, (131072.0, 200000.0, 33, 0, 0, 0)): 1.4767e9 + 0.4892e9,
     # split-BF16x3 H.psi, every block on the tensor cores: DRAM read + write of the
     # chain_tc2 launches of one H.psi (one shape at M=3000, two at M=6000)
-    ("c5a", 2, 3000, (8192.0, 200000.0, 1, 1, 1)): 434.8e9 + 0.175e9,
-    ("c5b", 2, 6000, (8192.0, 200000.0, 1, 1, 1)): 1282.5e9 + 0.536e9,
+    ("c5a", 2, 3000, (8192.0, 200000.0, 1, 1, 1, 0)): 434.8e9 + 0.175e9,
+    ("c5b", 2, 6000, (8192.0, 200000.0, 1, 1, 1, 0)): 1282.5e9 + 0.536e9,
 }
 # Algorithmic bytes of one split-BF16x3 H.psi: the distinct pre-split operator tiles
 # (4 bytes per padded element, each read once), the psi tiles, psi and sigma
@@ -386,12 +386,14 @@ def _precision_extras(ctx, psi_dev, k):
 def _shape_key(tune):
     if not tune:
         return None
-    return (tune["target_chunks"], tune["min_chunk"], tune["tc_min"], tune["by_work"], tune["flat_wide"])
+    return (tune["target_chunks"], tune["min_chunk"], tune["tc_min"], tune["by_work"], tune["flat_wide"],
+            tune.get("tc_tiny", 0))
 
 
 def _fixed_tune(spec):
     t = [float(x) for x in spec.split(",")]
-    return dict(target_chunks=t[0], min_chunk=t[1], tc_min=int(t[2]), by_work=int(t[3]), flat_wide=int(t[4]))
+    return dict(target_chunks=t[0], min_chunk=t[1], tc_min=int(t[2]), by_work=int(t[3]), flat_wide=int(t[4]),
+                tc_tiny=int(t[5]) if len(t) > 5 else 0)
 
 
 def profile_hpsi(wl, precision, ncalls, autotune=False, tune_spec=""):
@@ -720,7 +722,7 @@ def main():
     ap.add_argument("--sweeps", type=int, default=0, metavar="S",
                     help="time S full sweeps from the start state per precision (instead of the step)")
     ap.add_argument("--tune", default="", metavar="T,MIN,TC,ORDER,WIDE",
-                    help="fixed launch shape (target_chunks,min_chunk,tc_min,by_work,flat_wide); no autotuning")
+                    help="fixed launch shape (target_chunks,min_chunk,tc_min,by_work,flat_wide[,tc_tiny]); no autotuning")
     ap.add_argument("--M", type=int, default=0, help="override the workload's bond dimension (profiling)")
     ap.add_argument("--refine-keep", type=int, default=0,
                     help="sweeps: Ritz vectors carried between mixed-precision refinement steps")

@@ -435,36 +435,40 @@ int dmrg_batch_free(dmrg_batch *batch);
 /*
  * Launch-shape autotuning of the H.psi task list (the grouped launch of the
  * sector-pair products of Sec. 2.2.1, Eq. dgemm; the paper has no counterpart:
- * its task sizes are fixed by the MPI distribution).  Five parameters shape a
+ * its task sizes are fixed by the MPI distribution).  Six parameters shape a
  * task list: target_chunks (the work of all output blocks is cut into about
  * this many equal-work chunks), min_chunk (no chunk lighter than this many
  * FLOPs), tc_min (output blocks with a side >= tc_min and both sides <= 128
  * run on the tensor-core kernel in DMRG_PREC_BF16X3), by_work (1: chunks
- * launched heaviest first; 0: in output-block order) and flat_wide (1: the
+ * launched heaviest first; 0: in output-block order), flat_wide (1: the
  * kernel for blocks of at most 32 x 32 runs one wide CTA per SM, 0: two
- * narrower CTAs per SM).  Defaults: 8192, 2e5, 33, 0, 1.
+ * narrower CTAs per SM) and tc_tiny (the tensor-core kernel's shape: 1 = every
+ * block with m <= 64 and q and every task's p <= 32 runs on the 32-column
+ * shape, five CTAs per SM, in a launch of its own; 0 = that shape only when
+ * every block fits it, else the 64- and 128-row shapes).  Defaults: 8192, 2e5,
+ * 33, 0, 1, 0.
  *
  * dmrg_autotune builds candidate task lists for the current position, times
  * `reps` complete H.psi launch sequences of each (CUDA events, on a seeded
  * vector; synchronizes the stream), keeps the fastest for this and later
  * positions and rebuilds the position's task lists with it.  best_ms (may be
  * NULL) receives the time of one H.psi with the chosen shape; params (may be
- * NULL, 5 doubles) the chosen target_chunks, min_chunk, tc_min, by_work,
- * flat_wide.  Results of
+ * NULL, 6 doubles) the chosen target_chunks, min_chunk, tc_min, by_work,
+ * flat_wide, tc_tiny.  Results of
  * H.psi differ between shapes only by floating-point summation order.
  * Errors: DMRG_EINVAL (NULL context, reps < 1), DMRG_ESTATE (blocks of the
  * position not built), DMRG_ETIMEOUT, DMRG_ECUDA.
  * dmrg_set_tune sets the parameters without timing (DMRG_EINVAL unless
- * target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, by_work and
- * flat_wide 0 or 1); the task lists are rebuilt on next use.  dmrg_get_tune
- * writes the current five parameters.
+ * target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, by_work,
+ * flat_wide and tc_tiny 0 or 1); the task lists are rebuilt on next use.
+ * dmrg_get_tune writes the current six parameters.
  * dmrg_batch_autotune does the same for a batch (every context still at the
  * position it had at dmrg_batch_create, else DMRG_ESTATE); the CUDA graph of
  * the batch is captured again on the next dmrg_batch_hpsi.
  */
 int dmrg_autotune(dmrg_ctx *ctx, int reps, double *best_ms, double *params);
 int dmrg_set_tune(dmrg_ctx *ctx, double target_chunks, double min_chunk, int tc_min, int by_work,
-                  int flat_wide);
+                  int flat_wide, int tc_tiny);
 int dmrg_get_tune(dmrg_ctx *ctx, double *params);
 int dmrg_batch_autotune(dmrg_batch *batch, int reps, double *best_ms, double *params);
 
@@ -540,8 +544,9 @@ int dmrg_debug_tasks(int L, int N, int two_sz, const double *h, const double *v,
  * Sec. 2.2.1): each output block's tasks in their cheaper association, cut
  * into chunks of about equal work that accumulate into scratch slots, then an
  * ordered reduction of the slots into sigma.  tensor_cores: 1 routes blocks to
- * the tensor-core kernel as DMRG_PREC_BF16X3 does; tune: NULL (defaults) or 4
- * doubles target_chunks, min_chunk, tc_min, by_work as in dmrg_set_tune.
+ * the tensor-core kernel as DMRG_PREC_BF16X3 does; tune: NULL (defaults) or 5
+ * doubles target_chunks, min_chunk, tc_min, by_work, tc_tiny as in
+ * dmrg_set_tune.
  * counts (8): execution entries, chunks of the 32 x 32 tile kernel, of the
  * flattened-lane kernel, of the tensor-core kernel, reduction groups, tiles,
  * scratch elements, reduced elements.  Optional arrays (NULL to skip; sizes
@@ -558,7 +563,7 @@ int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const double *v, 
 
 /*
  * dmrg_debug_validate -- host-only bounds check of the execution plan that
- * dmrg_debug_exec describes (tune: NULL for the default launch shape, or 4
+ * dmrg_debug_exec describes (tune: NULL for the default launch shape, or 5
  * doubles as in dmrg_debug_exec).  The four operand arenas
  * (stored operators and pre-summed temporaries of both blocks) are given
  * distinct element bases, so every operand address names its arena.  Every
@@ -582,7 +587,7 @@ int dmrg_debug_validate(int L, int N, int two_sz, const double *h, const double 
  * task list as dmrg_debug_exec with tensor_cores = 1 (FP32 operand addresses):
  * the blocks routed to the tensor cores, ordered by kernel shape, their tasks
  * grouped into stacks that share a psi block, and the operator and psi tiles
- * in order of first use.  tune: NULL or 4 doubles as in dmrg_debug_exec.
+ * in order of first use.  tune: NULL or 5 doubles as in dmrg_debug_exec.
  * counts (9): tasks, blocks, operator tiles, psi tiles, operator tile bytes,
  * psi tile bytes, blocks of the 64 x 32, 64 x 64 and 128 x 128 shapes.
  * Optional arrays (NULL to skip): te_out 14 per task (X tile, Y^T tile, Z^T

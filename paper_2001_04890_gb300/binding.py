@@ -74,7 +74,7 @@ def lib():
         "dmrg_batch_hpsi": (C.c_int, [vp, vp, vp, C.c_int]),
         "dmrg_batch_free": (C.c_int, [vp]),
         "dmrg_autotune": (C.c_int, [vp, C.c_int, dp, dp]),
-        "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int]),
+        "dmrg_set_tune": (C.c_int, [vp, C.c_double, C.c_double, C.c_int, C.c_int, C.c_int, C.c_int]),
         "dmrg_get_tune": (C.c_int, [vp, dp]),
         "dmrg_truncation_stats": (C.c_int, [vp, dp, dp, llp, llp]),
         "dmrg_orbital_entropies": (C.c_int, [vp, dp, dp]),
@@ -150,6 +150,19 @@ def debug_tasks(h, v, N, two_sz, k, sec_l, sec_r, grouped=False):
     return out
 
 
+def _debug_tune(tune):
+    """Launch shape of the host-only plan dumps: target_chunks, min_chunk, tc_min, by_work and
+    optionally tc_tiny (0 when omitted), as the 5 doubles the library reads."""
+    if tune is None:
+        return None
+    t = [float(x) for x in tune]
+    if len(t) == 4:
+        t.append(0.0)
+    if len(t) != 5:
+        raise ValueError("tune: target_chunks, min_chunk, tc_min, by_work[, tc_tiny]")
+    return np.ascontiguousarray(t, dtype=np.float64)
+
+
 def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
     """Host-only execution plan of the H.psi task list: dict of counts and the arrays
     xs (n, 8), chunks (n, 8) and reduce (n, 8) described in the header."""
@@ -157,7 +170,7 @@ def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
     L = h.shape[0]
     tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
     tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
-    tune_arr = None if tune is None else np.ascontiguousarray(tune, dtype=np.float64)
+    tune_arr = _debug_tune(tune)
     tp = None if tune_arr is None else _dptr(tune_arr)
     cnt = np.zeros(8, dtype=np.int64)
     llp = C.POINTER(C.c_longlong)
@@ -174,12 +187,12 @@ def debug_exec(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
 
 def debug_validate(h, v, N, two_sz, k, sec_l, sec_r, tensor_cores=False, tune=None):
     """Host-only bounds check of the execution plan (and, with tensor_cores, of the
-    tensor-core tile plan) for the default or a given launch shape (4 doubles:
-    target_chunks, min_chunk, tc_min, by_work): (views checked, violations, first violation)."""
+    tensor-core tile plan) for the default or a given launch shape (target_chunks, min_chunk,
+    tc_min, by_work[, tc_tiny]): (views checked, violations, first violation)."""
     h, v = _f64(h), _f64(v)
     tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
     tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
-    tune_arr = None if tune is None else np.ascontiguousarray(tune, dtype=np.float64)
+    tune_arr = _debug_tune(tune)
     chk, bad = C.c_longlong(), C.c_longlong()
     _check(lib().dmrg_debug_validate(h.shape[0], N, two_sz, _dptr(h), _dptr(v), k, len(tl), _iptr(tl), len(tr),
                                      _iptr(tr), int(tensor_cores), None if tune_arr is None else _dptr(tune_arr),
@@ -194,7 +207,7 @@ def debug_tc(h, v, N, two_sz, k, sec_l, sec_r, tune=None):
     L = h.shape[0]
     tl = np.ascontiguousarray(np.asarray(sec_l, dtype=np.int32).reshape(-1, 3))
     tr = np.ascontiguousarray(np.asarray(sec_r, dtype=np.int32).reshape(-1, 3))
-    tune_arr = None if tune is None else np.ascontiguousarray(tune, dtype=np.float64)
+    tune_arr = _debug_tune(tune)
     tp = None if tune_arr is None else _dptr(tune_arr)
     llp = C.POINTER(C.c_longlong)
     cnt = np.zeros(9, dtype=np.int64)
@@ -453,18 +466,18 @@ class DMRG:
         """Time candidate launch shapes of this position's H.psi task list; keep the fastest.
 
         Returns (ms per H.psi with the chosen shape, {target_chunks, min_chunk, tc_min, by_work,
-        flat_wide})."""
+        flat_wide, tc_tiny})."""
         ms = C.c_double()
-        par = np.zeros(5)
+        par = np.zeros(6)
         _check(lib().dmrg_autotune(self.ctx, reps, C.byref(ms), _dptr(par)))
         return ms.value, _tune_dict(par)
 
-    def set_tune(self, target_chunks=8192.0, min_chunk=2.0e5, tc_min=33, by_work=0, flat_wide=1):
+    def set_tune(self, target_chunks=8192.0, min_chunk=2.0e5, tc_min=33, by_work=0, flat_wide=1, tc_tiny=0):
         _check(lib().dmrg_set_tune(self.ctx, float(target_chunks), float(min_chunk), int(tc_min), int(by_work),
-                                   int(flat_wide)))
+                                   int(flat_wide), int(tc_tiny)))
 
     def get_tune(self):
-        par = np.zeros(5)
+        par = np.zeros(6)
         _check(lib().dmrg_get_tune(self.ctx, _dptr(par)))
         return _tune_dict(par)
 
@@ -541,7 +554,7 @@ class DMRG:
 
 def _tune_dict(par):
     return {"target_chunks": float(par[0]), "min_chunk": float(par[1]), "tc_min": int(par[2]),
-            "by_work": int(par[3]), "flat_wide": int(par[4])}
+            "by_work": int(par[3]), "flat_wide": int(par[4]), "tc_tiny": int(par[5])}
 
 
 class Batch:
@@ -576,7 +589,7 @@ class Batch:
 
         Returns (ms per batched H.psi with the chosen shape, parameters)."""
         ms = C.c_double()
-        par = np.zeros(5)
+        par = np.zeros(6)
         _check(lib().dmrg_batch_autotune(self.h, reps, C.byref(ms), _dptr(par)))
         return ms.value, _tune_dict(par)
 

@@ -361,6 +361,8 @@ struct ChainTune {
   int orient = 1;      // run each entry in its cheaper association (split task lists)
   int flat_wide = 1;   // flat kernel CTAs: 1 = one wide CTA per SM (6 FP64 / 12 FP32 warps),
                        // 0 = two narrower CTAs per SM (4 / 8 warps each)
+  int tc_tiny = 0;     // tensor-core kernel shapes: 1 = every block that fits the 32-column
+                       // shape runs on it (a launch of its own), 0 = only when all blocks fit
 };
 // Host half of a task list's upload: the execution list (entries in their
 // cheaper association, cut into equal-work chunks when split_tasks), the launch
@@ -705,13 +707,14 @@ struct TcPlan {
 };
 
 static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
-                    TcPlan &P, std::vector<int> *entry_of = nullptr, uint64_t elem_bytes = 4) {
+                    TcPlan &P, std::vector<int> *entry_of = nullptr, uint64_t elem_bytes = 4, int tc_tiny = 0) {
   auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
   const size_t nv = vt.size();
   // kernel shape per block: 2 (m <= 64, q, p <= 32), 1 (m, q, p <= 64), 0 (the rest);
-  // blocks ordered by shape.  Shape 2 is used only when every block fits it: each
-  // shape is its own launch with its own last-wave tail, and a third launch costs
-  // more than the extra resident CTAs gain when larger blocks are present.
+  // blocks ordered by shape.  Shape 2 is used when every block fits it, or for every
+  // block that fits it with tc_tiny: each shape is its own launch with its own
+  // last-wave tail, and whether a third launch costs more than its extra resident
+  // CTAs gain depends on the mix of block sizes (an autotuner candidate).
   std::vector<int> pmax(nv, 0);
   parallel_for(nv, [&](size_t i) {
     const ChainGroup &g = vt[i];
@@ -723,7 +726,7 @@ static void plan_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, 
   bool all_tiny = true;
   for (size_t i = 0; i < nv; ++i) all_tiny = all_tiny && fits(i, 32);
   auto shape_of = [&](size_t i) {
-    if (all_tiny) return 2;
+    if (all_tiny || (tc_tiny && fits(i, 32))) return 2;
     return fits(i, 64) ? 1 : 0;
   };
   std::vector<size_t> order;
@@ -838,6 +841,7 @@ struct DevChain {
   DBuf<int> tc_counter;  // work counters of the persistent tensor-core kernels (two shapes)
   int npts = 0, ntc_shape[3] = {0, 0, 0};
   int flat_wide = 1;
+  int tc_tiny = 0;
   int nall = 0, nbig = 0, nflat = 0, ntc = 0, ntiles = 0, nred = 0;
   int64_t nent = 0;
   int64_t red_total = 0, scratch_n = 0;
@@ -851,6 +855,7 @@ struct DevChain {
     split = split_tasks;
     ops32 = ops32_in;
     flat_wide = tune.flat_wide;
+    tc_tiny = tune.tc_tiny;
     const auto &xs = X.xs;
     const std::vector<ChainGroup> &vb = X.vb, &vf = X.vf, &vt = X.vt;
     const std::vector<ReduceGroup> &vr = X.vr;
@@ -880,7 +885,7 @@ struct DevChain {
   void build_tc(const std::vector<ChainEntry, NoInitAlloc<ChainEntry>> &xs, const std::vector<ChainGroup> &vt,
                 cudaStream_t s) {
     TcPlan P;
-    plan_tc(xs, vt, P, nullptr, ops32 ? 4 : 8);
+    plan_tc(xs, vt, P, nullptr, ops32 ? 4 : 8, tc_tiny);
     std::vector<TcEntry> &te = P.te;
     std::vector<TcGroup> &tg = P.tg;
     std::vector<TileSpec> &ts = P.ts;
@@ -2806,12 +2811,14 @@ extern "C" int dmrg_debug_exec(int L, int N, int two_sz, const double *h, const 
   if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
   ChainTune T;
   if (tune) {
-    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1))
+    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1) ||
+        (tune[4] != 0 && tune[4] != 1))
       throw Fail{DMRG_EINVAL, "dmrg_debug_exec: bad launch-shape parameters"};
     T.target_chunks = tune[0];
     T.min_chunk = tune[1];
     T.tc_min = (int)tune[2];
     T.by_work = (int)tune[3];
+    T.tc_tiny = (int)tune[4];
   }
   Integrals I;
   I.L = L;
@@ -2900,12 +2907,14 @@ extern "C" int dmrg_debug_validate(int L, int N, int two_sz, const double *h, co
     throw Fail{DMRG_EINVAL, "dmrg_debug_validate: bad arguments"};
   ChainTune T;
   if (tune) {
-    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1))
+    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1) ||
+        (tune[4] != 0 && tune[4] != 1))
       throw Fail{DMRG_EINVAL, "dmrg_debug_validate: bad tune"};
     T.target_chunks = tune[0];
     T.min_chunk = tune[1];
     T.tc_min = (int)tune[2];
     T.by_work = (int)tune[3];
+    T.tc_tiny = (int)tune[4];
   }
   if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
   Integrals I;
@@ -2996,7 +3005,7 @@ extern "C" int dmrg_debug_validate(int L, int N, int two_sz, const double *h, co
     // FP32-element addresses times 4, here the synthetic arena bases above), every
     // tile and every task's tile reads inside the tile arenas
     TcPlan P;
-    plan_tc(X.xs, X.vt, P);
+    plan_tc(X.xs, X.vt, P, nullptr, 4, T.tc_tiny);
     auto c16 = [](int x) { return (uint64_t)((x + 15) & ~15); };
     for (const TileSpec &t : P.ts) {
       ++nchk;
@@ -3038,12 +3047,14 @@ extern "C" int dmrg_debug_tc(int L, int N, int two_sz, const double *h, const do
   if (std::abs(two_sz) > N || ((N - two_sz) & 1)) throw Fail{DMRG_EINVAL, "two_sz incompatible with N"};
   ChainTune T;
   if (tune) {
-    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1))
+    if (!(tune[0] >= 1.0) || !(tune[1] >= 0.0) || tune[2] < 1 || tune[2] > 129 || (tune[3] != 0 && tune[3] != 1) ||
+        (tune[4] != 0 && tune[4] != 1))
       throw Fail{DMRG_EINVAL, "dmrg_debug_tc: bad launch-shape parameters"};
     T.target_chunks = tune[0];
     T.min_chunk = tune[1];
     T.tc_min = (int)tune[2];
     T.by_work = (int)tune[3];
+    T.tc_tiny = (int)tune[4];
   }
   Integrals I;
   I.L = L;
@@ -3073,7 +3084,7 @@ extern "C" int dmrg_debug_tc(int L, int N, int two_sz, const double *h, const do
   plan_exec(CL, true, true, T, X);
   TcPlan P;
   std::vector<int> src;
-  plan_tc(X.xs, X.vt, P, &src);
+  plan_tc(X.xs, X.vt, P, &src, 4, T.tc_tiny);
   counts[0] = (long long)P.te.size();
   counts[1] = (long long)P.tg.size();
   counts[2] = (long long)P.ts.size();
@@ -3438,6 +3449,13 @@ static ChainTune autotune_chain(const ChainList &CL, bool tc, bool ops32, const 
     }
   }
   if (tc) {
+    ChainTune t = best;
+    t.tc_tiny = 1 - best.tc_tiny;
+    const double ms = run(t);
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = t;
+    }
     const int tcs[] = {1, 9, 17, 33, 49, 65};
     for (int v : tcs) {
       if (v == best.tc_min) continue;
@@ -3460,6 +3478,7 @@ static void tune_out(const ChainTune &t, double *params) {
   params[2] = t.tc_min;
   params[3] = t.by_work;
   params[4] = t.flat_wide;
+  params[5] = t.tc_tiny;
 }
 
 }  // namespace dmrg
@@ -3495,13 +3514,14 @@ extern "C" int dmrg_autotune(dmrg_ctx *c, int reps, double *best_ms, double *par
 }
 
 extern "C" int dmrg_set_tune(dmrg_ctx *c, double target_chunks, double min_chunk, int tc_min, int by_work,
-                             int flat_wide) {
+                             int flat_wide, int tc_tiny) {
   API_BEGIN
   if (!c || !(target_chunks >= 1.0) || !(min_chunk >= 0.0) || tc_min < 1 || tc_min > 129 ||
-      (by_work != 0 && by_work != 1) || (flat_wide != 0 && flat_wide != 1))
+      (by_work != 0 && by_work != 1) || (flat_wide != 0 && flat_wide != 1) || (tc_tiny != 0 && tc_tiny != 1))
     throw Fail{DMRG_EINVAL, "dmrg_set_tune: target_chunks >= 1, min_chunk >= 0, 1 <= tc_min <= 129, "
-                            "by_work and flat_wide 0 or 1"};
+                            "by_work, flat_wide and tc_tiny 0 or 1"};
   c->tune.flat_wide = flat_wide;
+  c->tune.tc_tiny = tc_tiny;
   c->tune.target_chunks = target_chunks;
   c->tune.min_chunk = min_chunk;
   c->tune.tc_min = tc_min;

@@ -48,7 +48,7 @@ def test_tune_calls_reject_bad_arguments_without_a_gpu():
     import ctypes as C
     lib = binding.lib()
     par = (C.c_double * 5)()
-    assert lib.dmrg_set_tune(None, 8192.0, 2e5, 33, 0, 1) == binding.DMRG_EINVAL
+    assert lib.dmrg_set_tune(None, 8192.0, 2e5, 33, 0, 1, 0) == binding.DMRG_EINVAL
     assert lib.dmrg_get_tune(None, par) == binding.DMRG_EINVAL
     assert lib.dmrg_autotune(None, 1, None, None) == binding.DMRG_EINVAL
     assert lib.dmrg_batch_autotune(None, 1, None, None) == binding.DMRG_EINVAL

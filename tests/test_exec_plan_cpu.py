@@ -210,7 +210,8 @@ def test_operand_views_in_bounds_on_random_layouts(seed):
     h, v = workloads.integrals(L, seed=seed)
     # the default launch shape and shapes the autotuner can pick (split granularity,
     # tensor-core routing threshold, group order); with tensor cores, the tile plan too
-    tunes = [None, [1.0, 0.0, 1, 1], [32768.0, 5.0e4, 17, 0], [8192.0, 2.0e5, 1, 1], [64.0, 1.0e7, 65, 1]]
+    tunes = [None, [1.0, 0.0, 1, 1], [32768.0, 5.0e4, 17, 0], [8192.0, 2.0e5, 1, 1], [64.0, 1.0e7, 65, 1],
+             [8192.0, 2.0e5, 1, 1, 1]]
     for tc in (False, True):
         for tune in tunes:
             checked, bad, first = binding.debug_validate(h, v, N, tsz, k, sl, sr, tensor_cores=tc, tune=tune)

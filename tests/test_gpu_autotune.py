@@ -33,6 +33,7 @@ def test_autotune_keeps_hpsi(prec, tol):
     assert par["min_chunk"] in (5.0e4, 2.0e5)
     assert par["tc_min"] in ((1, 9, 17, 33, 49, 65) if prec == binding.PREC_BF16X3 else (33,))
     assert par["by_work"] in (0, 1) and par["flat_wide"] in (0, 1)
+    assert par["tc_tiny"] in ((0, 1) if prec == binding.PREC_BF16X3 else (0,))
     assert ctx.get_tune() == par
     after = ctx.hpsi(psi)
     scale = np.max(np.abs(ref))
@@ -42,6 +43,11 @@ def test_autotune_keeps_hpsi(prec, tol):
     ctx.set_tune(target_chunks=32768, min_chunk=5e4, tc_min=1, by_work=1, flat_wide=0)
     again = ctx.hpsi(psi)
     assert np.max(np.abs(again - ref)) <= tol * scale
+    # the same with the small blocks on the 32-column tensor-core shape (a launch of its own)
+    ctx.set_tune(target_chunks=32768, min_chunk=5e4, tc_min=1, by_work=1, flat_wide=0, tc_tiny=1)
+    assert ctx.get_tune()["tc_tiny"] == 1
+    tiny = ctx.hpsi(psi)
+    assert np.max(np.abs(tiny - ref)) <= tol * scale
     ctx.close()
 
 

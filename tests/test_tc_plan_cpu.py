@@ -9,7 +9,8 @@ import pytest
 from paper_2001_04890_gb300 import binding, workloads
 
 CASES = [(12, 12, 0, 200, 5), (13, 13, 1, 150, 5), (10, 10, 0, 256, 4), (12, 12, 0, 1024, 5)]
-TUNES = [[8192.0, 2e5, 1, 0], [64.0, 0.0, 9, 1], [4096.0, 5e4, 17, 0]]
+# target_chunks, min_chunk, tc_min, by_work[, tc_tiny]
+TUNES = [[8192.0, 2e5, 1, 0], [64.0, 0.0, 9, 1], [4096.0, 5e4, 17, 0], [8192.0, 2e5, 1, 1, 1]]
 
 
 def _c16(x):
@@ -47,7 +48,7 @@ def test_tensor_core_plan_on_random_layouts(seed):
         return out or [(0, 0, 1)]
     sl, sr = table(k), table(L - k - 2)
     h, v = workloads.integrals(L, seed=seed)
-    for tune in ([8192.0, 2e5, 1, 0], [64.0, 0.0, 17, 1]):
+    for tune in ([8192.0, 2e5, 1, 0], [64.0, 0.0, 17, 1], [64.0, 0.0, 1, 0, 1]):
         _check_tc(h, v, N, tsz, k, sl, sr, tune)
 
 
@@ -65,8 +66,10 @@ def _check_tc(h, v, N, tsz, k, sl, sr, tune):
     for c in tc_chunks:
         pmax[int(c[1])] = int(xs[c[6]:c[6] + c[7], 2].max())
     fits = lambda g, lim: g[3] <= 64 and g[4] <= lim and pmax[int(g[0])] <= lim
+    # the 32-column shape: when every block fits it, or (tc_tiny) for each block that fits it
     all_tiny = all(fits(g, 32) for g in tg)
-    shapes = [2 if all_tiny else (1 if fits(g, 64) else 0) for g in tg]
+    tiny = len(tune) > 4 and tune[4] == 1
+    shapes = [2 if (all_tiny or (tiny and fits(g, 32))) else (1 if fits(g, 64) else 0) for g in tg]
     assert shapes == sorted(shapes, reverse=True)
     assert shapes.count(2) == cnt["shape64x32"] and shapes.count(1) == cnt["shape64x64"]
     want = {}
