@@ -31,8 +31,12 @@ def grow_both(h, v, k, M, seed):
     return I, lb, rb, lo, ro
 
 
+# L = 8: blocks of up to five sites on either side, so both halves hold several
+# orbitals when the complementary operators are formed on the larger one (k = 1:
+# the right block is larger, k = 5: the left one, k = 3: equal halves)
 @pytest.mark.parametrize("L,N,two_sz,M,k", [(5, 4, 0, 16, 1), (6, 6, 0, 40, 2), (6, 5, 1, 24, 3),
-                                            (6, 6, 0, 30, 0), (6, 6, 0, 30, 4)])
+                                            (6, 6, 0, 30, 0), (6, 6, 0, 30, 4), (8, 8, 0, 40, 1),
+                                            (8, 8, 0, 40, 3), (8, 8, 0, 40, 5)])
 def test_operator_oracle_hpsi_equals_explicit_projection(L, N, two_sz, M, k):
     h, v = workloads.integrals(L, seed=200 + k)
     nu, nd = (N + two_sz) // 2, (N - two_sz) // 2
