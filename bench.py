@@ -509,9 +509,17 @@ def batched_workload(args, wl):
         e, _ = c.davidson(tol=wl["tol"], max_iter=400, allow_noconv=True)
         e64.append(e)
         c.close()
+    peaks = _peaks()
     for name in res:
         res[name]["max_abs_dE_vs_fp64_first16"] = float(np.max(np.abs(np.array(res[name]["energies_head"]) - e64)))
         del res[name]["energies_head"]
+        if name == "bf16x3" and peaks.get("bf16_tflops"):
+            peak = peaks["bf16_tflops"] / 3.0
+            res[name]["roofline"] = {
+                "bound": "tensor", "kernel": "chain_tc2_kernel (batched H.psi, split-BF16 x3 on tcgen05)",
+                "achieved": res[name]["batched_hpsi_tflops"], "peak": peak,
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops (burst) / 3 (of measured)", "unit": "TFLOP/s",
+                "frac": res[name]["batched_hpsi_tflops"] / peak}
     out.update(res)
     return out
 
