@@ -82,3 +82,18 @@ def test_sweep_summary_takes_every_site_once():
         positions = list(range(0, L - 2)) + list(range(L - 2, 0, -1))   # one sweep, both directions
         rec = {"entropies": np.array([[k, k + 1, -1.0] for k in positions], dtype=float)}
         assert bench._site_entropies(rec, L) == [float(s) for s in range(L)]
+
+
+def test_launch_shape_keys_match_the_recorded_traffic():
+    """A fixed launch shape given on the command line (five or six numbers) maps to
+    the key of the recorded DRAM traffic, and every workload with recorded
+    tensor-core traffic also has its algorithmic bytes."""
+    import bench
+    t5 = bench._fixed_tune("8192,200000,1,1,1")
+    t6 = bench._fixed_tune("8192,200000,1,1,1,0")
+    assert t5 == t6 and t6["tc_tiny"] == 0 and bench._fixed_tune("8192,200000,1,1,1,1")["tc_tiny"] == 1
+    assert ("c5b", 2, 6000, bench._shape_key(t5)) in bench.TRAFFIC_PER_LAUNCH
+    for (wl, prec, M, shape) in bench.TRAFFIC_PER_LAUNCH:
+        assert len(shape) == 6 and M == bench.WORKLOADS[wl]["M"]
+        if prec == 2:
+            assert wl in bench.ALG_BYTES and bench.ALG_BYTES[wl] < bench.TRAFFIC_PER_LAUNCH[(wl, prec, M, shape)]

@@ -112,6 +112,25 @@ def test_sweeps_match_stored_oracle_energies(L, M, nsw):
     assert_sweep_minima_monotone(E, DW, nsw)
 
 
+@pytest.mark.parametrize("prec", [binding.PREC_FP32, binding.PREC_BF16X3])
+def test_mixed_precision_sweeps_match_stored_oracle_energies(prec):
+    """The mixed modes (FP32 operator copies, or every block on the tensor cores in
+    split-BF16 x3, for the Davidson matvecs; FP64 refinement, truncation and
+    renormalization) follow the FP64 oracle's sweeps within the 1e-6 Eh the mixed
+    modes promise, step by step."""
+    L, M, nsw = 12, 128, 4
+    ref = read_golden(f"oracle_sweeps_L{L}_N{L}_2Sz0_M{M}_S{nsw}.txt")
+    h, v = workloads.integrals(L, seed=0)
+    ctx = binding.DMRG(h, v, L, 0, M, precision=prec)
+    if prec == binding.PREC_BF16X3:
+        ctx.set_tune(tc_min=1)
+    E, DW, _ = stepped_sweeps(ctx, nsw, tol=1e-11)
+    ctx.close()
+    assert len(E) == len(ref)
+    assert np.max(np.abs(E - ref)) < 1e-6, np.max(np.abs(E - ref))
+    assert_sweep_minima_monotone(E, DW, nsw)
+
+
 def test_predicted_psi_is_the_converged_state_once_exact():
     """White's prediction (Sec. 2.1 sweep, psi carried through O): once the sweeps
     have reached the full-CI state (every step at the FCI energy), the state
