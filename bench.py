@@ -306,6 +306,7 @@ def run_davidson_bench(args, wl, rank, world, precision):
     sampler, clk_path = _clock_sampler()
     time.sleep(0.3)
     ev, energy = [], None
+    torch.cuda.nvtx.range_push("step")  # lets ncu --nvtx-include "step/" capture the timed steps only
     for _ in range(args.steps):
         with torch.cuda.stream(stream):
             flush.fill_(1.0)  # L2 flush between timed steps (256 MB > 129 MB L2)
@@ -315,6 +316,7 @@ def run_davidson_bench(args, wl, rank, world, precision):
         b.record(stream)
         ev.append((a, b))
     stream.synchronize()
+    torch.cuda.nvtx.range_pop()
     st = ctx.stats(reset=True)
     step_ms = sum(a.elapsed_time(b) for a, b in ev)
     # end to end through the C ABI with HOST buffers: H2D of the start vector and D2H of
