@@ -598,19 +598,44 @@ static void plan_exec(const ChainList &CL, bool tensor_cores, bool split_tasks, 
   }
 }
 
-// First-use numbering of keys: occurrence i (0 <= i < n) has key key_of(i);
-// uid[i] receives the number of its key, keys numbered in order of first
-// occurrence, and first[u] the first occurrence of key u.  Parallel: the keys
-// are split into hash shards, each numbered by one thread scanning all
-// occurrences in order, so the numbering is that of a serial pass.
+// First-use numbering of keys: occurrence i (0 <= i < n < 2^32) has key
+// key_of(i); uid[i] receives the number of its key, keys numbered in order of
+// first occurrence, and first[u] the first occurrence of key u.  Parallel: the
+// keys are split into hash shards; the occurrences of each shard are listed in
+// increasing order (a counting pass per chunk of occurrences, then a scatter),
+// each shard is numbered by one thread, and the shards' first occurrences are
+// merged into one increasing list, so the numbering is that of a serial pass.
 template <class Key, class Hash, class KeyOf>
 static void first_use_numbering(size_t n, KeyOf key_of, Hash hash, std::vector<uint32_t> &uid,
                                 std::vector<size_t> &first) {
   const size_t S = 16, B = 1 << 16;
+  if (n >= (size_t(1) << 32)) throw Fail{DMRG_EINVAL, "too many occurrences to number"};
+  const size_t nc = (n + B - 1) / B;
   std::vector<uint8_t> shard(n);
-  parallel_for((n + B - 1) / B, [&](size_t c) {
-    for (size_t i = c * B; i < std::min(n, (c + 1) * B); ++i)
-      shard[i] = (uint8_t)((hash(key_of(i)) >> 40) % S);
+  std::vector<uint32_t> ccount(nc * S, 0);  // occurrences of each shard in each chunk
+  parallel_for(nc, [&](size_t c) {
+    uint32_t *cnt = &ccount[c * S];
+    for (size_t i = c * B; i < std::min(n, (c + 1) * B); ++i) {
+      const uint8_t sh = (uint8_t)((hash(key_of(i)) >> 40) % S);
+      shard[i] = sh;
+      ++cnt[sh];
+    }
+  });
+  // occ[sstart[sh] ..] lists shard sh's occurrences in increasing order (chunk by chunk)
+  std::vector<size_t> sstart(S + 1, 0), coff(nc * S);
+  for (size_t sh = 0; sh < S; ++sh) {
+    size_t acc = 0;
+    for (size_t c = 0; c < nc; ++c) {
+      coff[c * S + sh] = acc;
+      acc += ccount[c * S + sh];
+    }
+    sstart[sh + 1] = sstart[sh] + acc;
+  }
+  std::vector<uint32_t> occ(n);
+  parallel_for(nc, [&](size_t c) {
+    size_t w[S];
+    for (size_t sh = 0; sh < S; ++sh) w[sh] = sstart[sh] + coff[c * S + sh];
+    for (size_t i = c * B; i < std::min(n, (c + 1) * B); ++i) occ[w[shard[i]]++] = (uint32_t)i;
   });
   std::vector<uint32_t> lid(n);
   std::vector<std::vector<size_t>> lfirst(S);
@@ -629,8 +654,8 @@ static void first_use_numbering(size_t n, KeyOf key_of, Hash hash, std::vector<u
       while (t[at].id != EMPTY) at = (at + 1) & (t.size() - 1);
       t[at] = x;
     };
-    for (size_t i = 0; i < n; ++i) {
-      if (shard[i] != sh) continue;
+    for (size_t qi = sstart[sh]; qi < sstart[sh + 1]; ++qi) {
+      const size_t i = occ[qi];
       const Key k = key_of(i);
       const uint64_t h = (uint64_t)hash(k);
       size_t at = (size_t)h & (tab.size() - 1);
@@ -651,17 +676,25 @@ static void first_use_numbering(size_t n, KeyOf key_of, Hash hash, std::vector<u
       }
     }
   });
-  // global numbers in order of first occurrence
+  // global numbers in order of first occurrence: merge the shards' increasing lists
   std::vector<std::vector<uint32_t>> gnum(S);
   std::vector<size_t> pos(S, 0);
-  for (size_t sh = 0; sh < S; ++sh) gnum[sh].resize(lfirst[sh].size());
+  size_t keys = 0;
+  for (size_t sh = 0; sh < S; ++sh) {
+    gnum[sh].resize(lfirst[sh].size());
+    keys += lfirst[sh].size();
+  }
   first.clear();
-  for (size_t i = 0; i < n; ++i) {
-    const size_t sh = shard[i];
-    if (pos[sh] < lfirst[sh].size() && lfirst[sh][pos[sh]] == i) {
-      gnum[sh][pos[sh]++] = (uint32_t)first.size();
-      first.push_back(i);
-    }
+  first.reserve(keys);
+  for (size_t u = 0; u < keys; ++u) {
+    size_t bsh = S, best = n;
+    for (size_t sh = 0; sh < S; ++sh)
+      if (pos[sh] < lfirst[sh].size() && lfirst[sh][pos[sh]] < best) {
+        best = lfirst[sh][pos[sh]];
+        bsh = sh;
+      }
+    gnum[bsh][pos[bsh]++] = (uint32_t)first.size();
+    first.push_back(best);
   }
   uid.resize(n);
   parallel_for((n + B - 1) / B, [&](size_t c) {
