@@ -133,7 +133,7 @@ def test_sweep_reaches_fci_small():
     ctx.close()
 
 
-def test_config1_l8_m256_exact():
+def test_l8_m256_exact():
     """M=256 keeps every Schmidt rank of L=8: from sweep 3 on every step is the FCI energy."""
     L, N, M, nsw = 8, 8, 256, 5
     h, v = workloads.integrals(L, seed=0)

@@ -69,7 +69,7 @@ def read_golden(name):
     return np.loadtxt(os.path.join(GOLDEN, name), comments="#")
 
 
-def test_config1_l8_m64_sweeps_match_oracle():
+def test_l8_m64_sweeps_match_oracle():
     """L=8, N=8, Sz=0, M=64, six sweeps: every step equals the oracle's (1e-10 Eh)."""
     L, N, M, nsw = 8, 8, 64, 6
     h, v = workloads.integrals(L, seed=0)
